@@ -1,0 +1,325 @@
+"""Throughput of the CNSF fan-beam projector: forward + back projection (pixel*view updates/s).
+
+Workload (one step): a 512 x 512 FP32 random-ellipse phantom (20 ellipses, values in
+[0, 2], seed 2), fan beam with source-to-isocentre 500 mm and source-to-detector
+1000 mm, 888 flat-detector cells of 1 mm, 720 views over 360 deg; one forward projection
+y = A c and one back projection A^T y.  value = 512^2 * 720 * steps * ranks / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cnsf|reference]
+
+Under torchrun each rank projects its own copy of the workload (independent problems,
+no collective on the data path: weak scaling).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of views instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+back pixel·view updates/s at 512²×720 views; p50/p99 recon latency"
+UNIT = "pixel·view updates/s"
+WORKLOAD = ("512x512 FP32 random-ellipse phantom (20 ellipses, values [0,2], seed 2); fan beam "
+            "D_po 500 mm, D_ps 1000 mm, 888 flat cells x 1 mm (tau = 1 mm), 720 views over 360 deg; "
+            "one forward + one back projection per step, batch 1")
+# FP32 operations of one non-zero entry as the formula is evaluated: s' (2), tau'/2 (1),
+# the window difference of the trapezoid antiderivatives (13), the division by tau' (2) and
+# the accumulation (1).  An FMA counts as one operation.
+ALG_OPS_PER_ENTRY = 19
+FP32_LANES_PER_SM = 128
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        rows = []
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1907_10526_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(kernel)
+    if not ent or ent.get("source_hash") != _kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------- oracle leg
+def oracle_sample_rate(n_views_sample: int = 180):
+    """The FP64 CPU oracle on host cores: FP + BP of the workload restricted to a sample of
+    its views (every (720/n)-th view).  Returns (updates/s, seconds, threads, description)."""
+    import oracle
+    from synth import config_geometry, phantom_for_config
+    g = config_geometry(2)
+    stride = max(1, g.n_views // n_views_sample)
+    ang = g.view_angles()[::stride]
+    gs = g.with_(n_views=len(ang), angles=tuple(float(a) for a in ang))
+    img = phantom_for_config(2)
+    t0 = time.perf_counter()
+    y = oracle.forward(gs, img)
+    oracle.back(gs, y)
+    dt = time.perf_counter() - t0
+    upd = g.nx * g.ny * len(ang)
+    return upd / dt, dt, oracle.num_threads(), f"{len(ang)} of 720 views (every {stride}th), FP+BP, FP64"
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    per_step_views = 12
+    for _ in range(args.warmup):
+        oracle_sample_rate(per_step_views)
+    times, upd = [], 0
+    for _ in range(args.steps):
+        r, dt, thr, desc = oracle_sample_rate(per_step_views)
+        times.append(dt)
+        upd += 512 * 512 * per_step_views
+    tot = sum(times)
+    val = upd / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{per_step_views} views per step"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": f"{per_step_views} of 720 views per step (every 60th), FP+BP, FP64"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU leg
+def run_cnsf(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1907_10526_gb300 as cnsf
+    from synth import config_geometry, phantom_for_config
+
+    g = config_geometry(2)
+    geom = cnsf.Geometry(g)
+    img_np = phantom_for_config(2)
+    img = torch.tensor(img_np, dtype=torch.float32, device=dev)
+    sino = torch.empty((g.n_views, g.n_det), dtype=torch.float32, device=dev)
+    back = torch.empty((g.ny, g.nx), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+    nnz = cnsf.count_nonzeros(geom)
+
+    def step():
+        cnsf.forward_project(geom, img, out=sino)
+        cnsf.back_project(geom, sino, out=back)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)   # let the sampler start
+        for k in range(args.steps):
+            flush.fill_(float(k))                  # evict L2 between steps (outside the events)
+            ev[k][0].record(stream)
+            cnsf.forward_project(geom, img, out=sino)
+            ev[k][1].record(stream)
+            cnsf.back_project(geom, sino, out=back)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_fp = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_bp = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    total_ms = sum(t_fp) + sum(t_bp)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    upd_per_step = g.nx * g.ny * g.n_views
+    value = upd_per_step * args.steps * world / (total_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed
+    img_host = torch.tensor(img_np, dtype=torch.float32).pin_memory()
+    sino_host = torch.empty((g.n_views, g.n_det), dtype=torch.float32).pin_memory()
+    back_host = torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory()
+    img_dev = torch.empty_like(img)
+
+    def e2e_step():
+        img_dev.copy_(img_host, non_blocking=True)
+        cnsf.forward_project(geom, img_dev, out=sino)
+        cnsf.back_project(geom, sino, out=back)
+        sino_host.copy_(sino, non_blocking=True)
+        back_host.copy_(back, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize()
+        e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = sum(e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = upd_per_step * args.steps * world / (e2e_total * 1e-3)
+
+    # ---- roofline of the dominant kernel (FP32 issue throughput)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = _measured_peaks()
+    clocks = clk.summary()
+    sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+    fp_ms, bp_ms = statistics.mean(t_fp), statistics.mean(t_bp)
+    dom, dom_ms = ("fp_f32_kernel", fp_ms) if fp_ms >= bp_ms else ("bp_f32_kernel", bp_ms)
+    achieved = ALG_OPS_PER_ENTRY * nnz / (dom_ms * 1e-3)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
+            "frac": achieved / peak_ops, "traffic": _recorded_traffic(dom), "kernel": dom,
+            "ops_per_entry": ALG_OPS_PER_ENTRY, "entries_per_launch": nnz,
+            "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
+                          "(max SM clock of MEASURED_PEAKS.json); an FMA counts as one op",
+            "fp_ms": fp_ms, "bp_ms": bp_ms,
+            "fp_frac": ALG_OPS_PER_ENTRY * nnz / (fp_ms * 1e-3) / peak_ops,
+            "bp_frac": ALG_OPS_PER_ENTRY * nnz / (bp_ms * 1e-3) / peak_ops}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MiB write, outside the events)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(img_host.numel() * 4),
+                "d2h_bytes_per_step": int(sino_host.numel() * 4 + back_host.numel() * 4)},
+        "roofline": roof,
+        "clocks": clocks,
+        "gpu_launches": 4 * args.steps,
+        "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "bp_f32_kernel"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, thr, desc = oracle_sample_rate(180)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
+                                "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cnsf", choices=["cnsf", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_cnsf(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

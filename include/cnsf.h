@@ -1,0 +1,132 @@
+/*
+ * cnsf.h -- C ABI of the GB300 (sm_103a) CNSF fan-beam projector.
+ *
+ * The library computes the matrix-free forward projection y = A c and its
+ * adjoint A^T y of Zhang & Entezari, "A Convolutional Forward and
+ * Back-Projection Model for Fan-Beam Geometry" (arXiv 1907.10526).  Each entry
+ * of A is the convolutional non-separable footprint of Eq. (18): the pixel
+ * basis (first-order box spline, Sec. III.A) projected along the ray through
+ * the centre of a detector cell (Eq. 16, Theorem 2) and convolved with the
+ * effective detector blur tau' of Eq. (17), evaluated on the fly; no system
+ * matrix is stored.
+ *
+ * Conventions (the paper's Sec. II.A leaves them open):
+ *   view k:   theta_k = angles_rad[k] (or 2*pi*k/n_views), u = (cos, sin),
+ *             source p = d_po * u, flat detector perpendicular to u at distance
+ *             d_ps from the source, detector axis w = (-sin, cos);
+ *   cell j:   centre s_j = (j - (n_det-1)/2) * det_spacing + det_offset_mm,
+ *             width det_width_mm (tau); a cell value is the mean of the line
+ *             integrals over the cell (Eq. 2 with a normalised box blur);
+ *   pixel:    pixel (i, r) of an n_x x n_y image of side pixel_mm is centred at
+ *             (center_x + (i - (n_x-1)/2) h, center_y + (r - (n_y-1)/2) h).
+ *
+ * Memory layouts (all buffers contiguous, owned by the caller):
+ *   image     [batch][n_y][n_x]      (column index i fastest)
+ *   sinogram  [batch][n_views][n_det] (cell index j fastest)
+ *   element type float (CNSF_F32) or double (CNSF_F64).
+ *
+ * Device pointers, unless a function says otherwise, live on the device that
+ * was current when the geometry was created; that device must be current
+ * when any call is made.  Calls that take a stream are asynchronous on it
+ * (a NULL stream is the legacy default stream) and overwrite their outputs.
+ * No function throws; each returns a cnsf_status.  One geometry may be used
+ * from several host threads and streams at once: it is immutable after
+ * creation, and every call keeps its scratch memory private to that call.
+ */
+#ifndef CNSF_H
+#define CNSF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CNSF_API __attribute__((visibility("default")))
+#else
+#define CNSF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CNSF_OK = 0,
+    CNSF_ERR_INVALID = 1,     /* bad argument or geometry, nothing launched          */
+    CNSF_ERR_CUDA = 2,        /* a CUDA runtime call failed (see cnsf_last_cuda_error) */
+    CNSF_ERR_NOMEM = 3,       /* device or host allocation failed                    */
+    CNSF_ERR_UNSUPPORTED = 4, /* valid request the library does not implement        */
+    CNSF_ERR_INTERNAL = 5     /* a consistency check of the library failed           */
+} cnsf_status;
+
+typedef enum { CNSF_F32 = 0, CNSF_F64 = 1 } cnsf_dtype;
+
+typedef enum { CNSF_DETECTOR_FLAT = 0 } cnsf_detector;
+
+typedef struct cnsf_geometry cnsf_geometry; /* opaque, immutable after creation */
+
+/* Fan-beam acquisition (Sec. II.A, Fig. 1). */
+typedef struct {
+    int32_t n_x, n_y;          /* image columns and rows (>= 1)                      */
+    double pixel_mm;           /* h, side of the square pixel (> 0)                  */
+    double center_x_mm;        /* image centre relative to the rotation centre       */
+    double center_y_mm;
+    int32_t n_views;           /* >= 1                                               */
+    const double *angles_rad;  /* host array of n_views angles, copied; NULL selects
+                                  theta_k = 2*pi*k/n_views                           */
+    int32_t n_det;             /* detector cells (>= 1)                              */
+    double det_spacing_mm;     /* Delta_s, pitch of the cell centres (> 0)           */
+    double det_width_mm;       /* tau, cell width (> 0)                              */
+    double det_offset_mm;      /* shift of the detector centre along w               */
+    double d_po_mm;            /* source to rotation centre (D_po)                   */
+    double d_ps_mm;            /* source to detector line (D_ps > D_po)              */
+    int32_t detector;          /* CNSF_DETECTOR_FLAT                                 */
+} cnsf_geometry_desc;
+
+/* Build a geometry and its device tables on the current device (Sec. II.A and
+ * Eq. 17: per-view rotations, per-cell effective-blur slopes, per-ray walk
+ * tables).  Synchronous.  Rejects (CNSF_ERR_INVALID): non-positive sizes or
+ * lengths, d_ps <= d_po, and images that reach within two pixels of the source
+ * circle (the footprint model needs every pixel in front of the source).
+ * On success *out owns device memory until cnsf_geometry_destroy. */
+CNSF_API int cnsf_geometry_create(const cnsf_geometry_desc *desc, cnsf_geometry **out);
+
+/* Release a geometry (NULL is allowed).  The caller must first make sure that no
+ * work launched with it is still pending. */
+CNSF_API void cnsf_geometry_destroy(cnsf_geometry *geom);
+
+/* Sizes of a geometry: any output pointer may be NULL. */
+CNSF_API int cnsf_geometry_shape(const cnsf_geometry *geom, int32_t *n_x, int32_t *n_y, int32_t *n_views,
+                        int32_t *n_det);
+
+/* Forward projection y = A c (Eq. 6 with the entries of Eq. 18), detector-driven
+ * gather without atomics.  image: device [batch][n_y][n_x]; sino: device
+ * [batch][n_views][n_det], overwritten.  batch >= 0 (0 launches nothing).
+ * Allocates its scratch (zero-padded copies of the image) stream-ordered on
+ * `stream` and frees it the same way. */
+CNSF_API int cnsf_forward_project(const cnsf_geometry *geom, const void *image, void *sino, int32_t batch,
+                         int32_t dtype, void *stream);
+
+/* Back projection c = A^T y, the exact adjoint of cnsf_forward_project (same
+ * entries), pixel-driven gather without atomics.  sino: device
+ * [batch][n_views][n_det]; image: device [batch][n_y][n_x], overwritten.  Uses no
+ * scratch memory. */
+CNSF_API int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch,
+                      int32_t dtype, void *stream);
+
+/* Number of non-zero entries of A: pairs (view, cell, pixel) whose pixel centre lies
+ * strictly inside the support of the footprint, |s'| < (zeta_1 + zeta_2 + tau')/2
+ * (Eq. 18), decided in FP32 along the forward kernel's enumeration.
+ * Synchronous; *count is a host pointer. */
+CNSF_API int cnsf_count_nonzeros(const cnsf_geometry *geom, uint64_t *count, void *stream);
+
+/* Status code to a static English string. */
+CNSF_API const char *cnsf_status_string(int status);
+
+/* Text of the last CUDA error seen by this host thread (static storage). */
+CNSF_API const char *cnsf_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CNSF_H */

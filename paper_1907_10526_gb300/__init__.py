@@ -1,0 +1,173 @@
+"""GB300-native CNSF fan-beam projector: Python binding over the C ABI of ``_cnsf.so``.
+
+Zhang & Entezari, "A Convolutional Forward and Back-Projection Model for Fan-Beam
+Geometry": y = A c with the entries of Eq. (18), and its adjoint A^T y, computed by
+hand-written sm_103a kernels.  This module only marshals arguments: PyTorch supplies
+device memory and the current stream; every step of the projection runs in the CUDA
+library.  The functions have the names of the C entry points without the ``cnsf_``
+prefix.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from typing import Optional
+
+import torch
+
+from ._lib import CNSF_F32, CNSF_F64, CnsfError, GeometryDesc, check, lib  # noqa: F401
+
+__all__ = ["Geometry", "forward_project", "back_project", "count_nonzeros", "Projector", "CnsfError"]
+
+
+def _dtype_code(t: torch.dtype) -> int:
+    if t == torch.float32:
+        return CNSF_F32
+    if t == torch.float64:
+        return CNSF_F64
+    raise TypeError(f"unsupported dtype {t}: float32 or float64")
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream], device) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return int(s.cuda_stream)
+
+
+class Geometry:
+    """A fan-beam acquisition (Sec. II.A) with its device tables.
+
+    Built from any object with the fields of ``synth.FanGeometry`` (nx, ny, n_views,
+    n_det, pixel, det_spacing, det_width, d_po, d_ps, center_x, center_y, det_offset,
+    angles) or from the same names as keyword arguments.  The tables live on
+    ``device`` (default: the current CUDA device).
+    """
+
+    def __init__(self, desc=None, device=None, **kw):
+        if desc is None:
+            from types import SimpleNamespace
+            base = dict(pixel=1.0, det_spacing=1.0, det_width=1.0, d_po=500.0, d_ps=1000.0,
+                        center_x=0.0, center_y=0.0, det_offset=0.0, angles=None)
+            base.update(kw)
+            desc = SimpleNamespace(**base)
+        self.desc = desc
+        self.nx, self.ny = int(desc.nx), int(desc.ny)
+        self.n_views, self.n_det = int(desc.n_views), int(desc.n_det)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        ang = getattr(desc, "angles", None)
+        self._angles = None
+        if ang is not None:
+            self._angles = (ctypes.c_double * self.n_views)(*[float(a) for a in ang])
+        d = GeometryDesc(self.nx, self.ny, float(desc.pixel), float(desc.center_x), float(desc.center_y),
+                         self.n_views,
+                         ctypes.cast(self._angles, ctypes.POINTER(ctypes.c_double)) if self._angles else None,
+                         self.n_det, float(desc.det_spacing), float(desc.det_width), float(desc.det_offset),
+                         float(desc.d_po), float(desc.d_ps), 0)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(self._h)), "cnsf_geometry_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def image_shape(self):
+        return (self.ny, self.nx)
+
+    @property
+    def sino_shape(self):
+        return (self.n_views, self.n_det)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.cnsf_geometry_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _prep(x: torch.Tensor, inner: tuple, what: str):
+    if x.shape[-2:] != inner:
+        raise ValueError(f"{what}: expected trailing shape {inner}, got {tuple(x.shape)}")
+    lead = x.shape[:-2]
+    batch = int(math.prod(lead)) if lead else 1
+    return lead, batch
+
+
+def _run(fn, name, geom: Geometry, x: torch.Tensor, in_shape, out_shape, out, stream):
+    lead, batch = _prep(x, in_shape, name)
+    host_in = x.device.type != "cuda"
+    dev = geom.device
+    xd = x.to(dev, non_blocking=True) if host_in else x
+    if xd.device != dev:
+        raise ValueError(f"{name}: tensor on {xd.device}, geometry on {dev}")
+    xd = xd.contiguous()
+    code = _dtype_code(xd.dtype)
+    if out is None or host_in:
+        yd = torch.empty(lead + out_shape, dtype=xd.dtype, device=dev)
+    else:
+        yd = out
+        if yd.shape != lead + out_shape or yd.dtype != xd.dtype or not yd.is_contiguous() or yd.device != dev:
+            raise ValueError(f"{name}: bad output tensor")
+    with torch.cuda.device(dev):
+        check(fn(geom.handle, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()), batch, code,
+                 ctypes.c_void_p(_stream_ptr(stream, dev))), name)
+    if host_in:
+        res = yd.to("cpu")
+        if out is not None:
+            out.copy_(res)
+            return out
+        return res
+    return yd
+
+
+def forward_project(geom: Geometry, image: torch.Tensor, out: Optional[torch.Tensor] = None,
+                    stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """y = A c.  image [..., ny, nx] float32/float64 -> sinogram [..., n_views, n_det].
+
+    A CUDA tensor runs asynchronously on ``stream`` (default: current stream).  A CPU
+    tensor is copied to the geometry's device, projected there and copied back.
+    """
+    return _run(lib.cnsf_forward_project, "cnsf_forward_project", geom, image, geom.image_shape,
+                geom.sino_shape, out, stream)
+
+
+def back_project(geom: Geometry, sino: torch.Tensor, out: Optional[torch.Tensor] = None,
+                 stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """c = A^T y.  sinogram [..., n_views, n_det] -> image [..., ny, nx]."""
+    return _run(lib.cnsf_back_project, "cnsf_back_project", geom, sino, geom.sino_shape, geom.image_shape,
+                out, stream)
+
+
+def count_nonzeros(geom: Geometry, stream: Optional[torch.cuda.Stream] = None) -> int:
+    """Number of non-zero entries of A (synchronous)."""
+    n = ctypes.c_uint64()
+    with torch.cuda.device(geom.device):
+        check(lib.cnsf_count_nonzeros(geom.handle, ctypes.byref(n),
+                                      ctypes.c_void_p(_stream_ptr(stream, geom.device))),
+              "cnsf_count_nonzeros")
+    return int(n.value)
+
+
+class Projector(torch.autograd.Function):
+    """y = A c as a differentiable op: forward runs the forward kernel, backward runs the
+    back-projection kernel (grad_c = A^T grad_y, A^T being the exact adjoint)."""
+
+    @staticmethod
+    def forward(ctx, image, geom):
+        ctx.geom = geom
+        return forward_project(geom, image)
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        return back_project(ctx.geom, grad_y.contiguous()), None
+
+
+def project(geom: Geometry, image: torch.Tensor) -> torch.Tensor:
+    """Differentiable forward projection (see Projector)."""
+    return Projector.apply(image, geom)

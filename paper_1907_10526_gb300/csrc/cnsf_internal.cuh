@@ -1,0 +1,192 @@
+// cnsf_internal.cuh -- geometry constants, table layouts and the per-ray /
+// per-tile parameter derivations shared by the host table builder and the
+// device kernels of the CNSF projector.
+//
+// Notation (Zhang & Entezari, Sec. II.A, III.B-C):
+//   u = (cos t, sin t), w = (-sin t, cos t); source p = D_po u;
+//   cell j centre s_j on the detector line at distance D_ps from the source;
+//   central ray direction v_j = (-D_ps u + s_j w)/L_j, L_j = sqrt(D_ps^2 + s_j^2);
+//   its unit normal n_j = (s_j u + D_ps w)/L_j spans v(s)perp;
+//   zeta_1 = h n_x, zeta_2 = h n_y (Eq. 16); s' = n_j . (k - p);
+//   t = v_j . (k - p) the depth of pixel centre k along the central ray;
+//   tau' = t * dtan_j (Eq. 17, reading: perspective-divided edge coordinates
+//   scaled to the pixel depth), dtan_j = tan(phi+) - tan(phi-), phi+- the angles
+//   of the two cell edges from the central ray.
+#pragma once
+
+#include <cstdint>
+#include <cmath>
+
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#define __forceinline__ inline
+#endif
+
+namespace cnsf {
+
+// Plain numbers of a geometry, passed by value to every kernel.
+struct GeomConsts {
+    int nx, ny, nv, nd;
+    double h, cx, cy;
+    double ds, tau, doff;
+    double dpo, dps;
+    double rimg;      // distance from the rotation centre to the farthest image corner
+    double s0;        // centre of cell 0
+};
+
+// Per-cell quantities that do not depend on the view.
+__host__ __device__ inline double cell_centre(const GeomConsts &g, int j)
+{
+    return (j - 0.5 * (g.nd - 1)) * g.ds + g.doff;
+}
+
+// tan(phi+) - tan(phi-) for cell j: the two cell edges seen from the source in the frame of
+// the central ray (the perspective division of Eq. 17 at unit depth).
+__host__ __device__ inline double cell_dtan(const GeomConsts &g, double sj)
+{
+    double d2 = g.dps * g.dps + sj * sj, ht = 0.5 * g.tau;
+    return ht * g.dps * (1.0 / (d2 + sj * ht) + 1.0 / (d2 - sj * ht));
+}
+
+// Ray parameters of one (view, cell) in the walk frame.  The walk runs over the image
+// axis "b" that the ray crosses most steeply (rows when |v_y| >= |v_x|, otherwise columns of
+// the transposed image); along each crossed line the candidate pixels are indexed by the
+// other axis "a".  For a pixel at a-index ia on the line b = rb, with crossing f(rb):
+//   s'  = sign * B * (ia - f(rb))            (B = h |n_a| >= h/sqrt 2)
+//   t   = lambda(rb) + va h (ia - f(rb))      (depth along the central ray)
+//   e   = tau'/2 = e(rb) + kap (ia - f(rb)),  e(rb) = e0 + rb de
+template <typename T>
+struct RayParams {
+    T f0, g;          // f(rb) = f0 + rb g, a-index of the crossing of line rb
+    T e0, de, kap;    // half effective blur along the walk (mm)
+    T B, C;           // h|n_a| >= h|n_b|: the two footprint widths (Eq. 16)
+    T dtan;           // tan(phi+) - tan(phi-)
+    int transposed;   // 0: walk rows (b = y); 1: walk columns (b = x)
+    int na, nb;       // image extent across / along the walk
+};
+
+template <typename T>
+__host__ __device__ inline RayParams<T> make_ray_params(const GeomConsts &g, double c, double s, int j)
+{
+    double sj = cell_centre(g, j);
+    double L = sqrt(g.dps * g.dps + sj * sj);
+    double vx = (-g.dps * c - sj * s) / L, vy = (-g.dps * s + sj * c) / L;
+    double nxv = (sj * c - g.dps * s) / L, nyv = (sj * s + g.dps * c) / L;
+    double px = g.dpo * c, py = g.dpo * s;
+    double dtan = cell_dtan(g, sj);
+    RayParams<T> R;
+    int tr = fabs(vy) >= fabs(vx) ? 0 : 1;
+    double va, vb, na_, nb_, pa, pb, ca, cb;
+    int Na, Nb;
+    if (!tr) {
+        va = vx; vb = vy; na_ = nxv; nb_ = nyv; pa = px; pb = py; ca = g.cx; cb = g.cy; Na = g.nx; Nb = g.ny;
+    } else {
+        va = vy; vb = vx; na_ = nyv; nb_ = nxv; pa = py; pb = px; ca = g.cy; cb = g.cx; Na = g.ny; Nb = g.nx;
+    }
+    // source in index units of the walk frame
+    double PA = (pa - ca) / g.h + 0.5 * (Na - 1);
+    double PB = (pb - cb) / g.h + 0.5 * (Nb - 1);
+    double gg = va / vb;
+    R.f0 = (T)(PA - PB * gg);
+    R.g = (T)gg;
+    // lambda(rb) = (rb - PB) h / vb
+    R.e0 = (T)((-PB * g.h / vb) * 0.5 * dtan);
+    R.de = (T)((g.h / vb) * 0.5 * dtan);
+    R.kap = (T)(va * g.h * 0.5 * dtan);
+    R.B = (T)(g.h * fabs(na_));
+    R.C = (T)(g.h * fabs(nb_));
+    R.dtan = (T)dtan;
+    R.transposed = tr;
+    R.na = Na;
+    R.nb = Nb;
+    return R;
+}
+
+// Box-spline constants of one ray: trapezoid box_B * box_C with plateau half-width p and
+// outer half-width q, the reciprocal of C (clamped so that C = 0 stays finite) and the
+// normalisation h^2 / (2B) of the blurred footprint (Eq. 18 with the pixel area).
+template <typename T>
+struct BoxConsts {
+    T p, q, iC, nrm;
+};
+
+template <typename T>
+__host__ __device__ inline BoxConsts<T> make_box_consts(double B, double C, double h)
+{
+    BoxConsts<T> b;
+    b.p = (T)(0.5 * (B - C));
+    b.q = (T)(0.5 * (B + C));
+    double Cc = C > 1e-30 * h ? C : 1e-30 * h;
+    b.iC = (T)(1.0 / Cc);
+    b.nrm = (T)(h * h / (2.0 * B));
+    return b;
+}
+
+// Per (pixel tile, view) coefficients of the back projector.  For the pixel at offset
+// (di, dr) from the tile origin:
+//   D_n   = Dt + aD di + bD dr            (depth of the pixel centre along u from the source)
+//   y'    = yt + ay di + by dr            (coordinate along w)
+//   sigma = J + phi + (rho + a1 di + b1 dr) / D_n
+// where sigma is the continuous cell coordinate of the pixel centre's perspective
+// projection (Eq. 4), split into an integer J and a small remainder so that FP32 keeps it
+// to ~1e-6 cells.
+template <typename T>
+struct TileView {
+    T Dt, yt, a1, b1, rho, phi;
+    int J;
+};
+
+__host__ __device__ inline void tile_view_double(const GeomConsts &g, double c, double s, int it, int rt,
+                                                 double *Dt, double *yt, double *a1, double *b1,
+                                                 double *rho, double *phi, int *J)
+{
+    double kx = g.cx + (it - 0.5 * (g.nx - 1)) * g.h;
+    double ky = g.cy + (rt - 0.5 * (g.ny - 1)) * g.h;
+    double xu = kx * c + ky * s, yw = -kx * s + ky * c;
+    double D = g.dpo - xu;
+    double aD = -g.h * c, bD = -g.h * s, ay = -g.h * s, by = g.h * c;
+    double Nt = (g.dps * yw - g.s0 * D) / g.ds;
+    double aN = (g.dps * ay - g.s0 * aD) / g.ds;
+    double bN = (g.dps * by - g.s0 * bD) / g.ds;
+    double sig = Nt / D;
+    double Jd = floor(sig);
+    *Dt = D;
+    *yt = yw;
+    *a1 = aN - sig * aD;
+    *b1 = bN - sig * bD;
+    *rho = Nt - sig * D;
+    *phi = sig - Jd;
+    *J = (int)Jd;
+}
+
+// Fixed-point (32.32) form of the forward walk used by the FP32 kernel.
+struct RayF {
+    long long A0;     // fixed point of f(r0) - hw at the first walked line
+    long long G;      // fixed point of the per-line slope g
+    float e0, de;     // half blur at the first walked line and per line
+    float kap;        // half blur per unit a-offset within a line
+    float hw;         // candidate half-window (a-index units)
+    int r0, nrows;    // first walked line and number of lines
+    int kc;           // candidates per line
+    int flags;        // bit 0: transposed walk
+};
+static_assert(sizeof(RayF) == 48, "RayF layout");
+
+}  // namespace cnsf
+
+// Host-side geometry object behind the opaque handle.
+struct cnsf_geometry {
+    cnsf::GeomConsts gc;
+    int device;
+    int pad;                  // zero columns on each side of the padded image copies
+    int kc_max;               // largest candidate count per walked line
+    double kr;                // back projector: cell half-window = kr / D_n (cells)
+    // device tables
+    double *d_view_cs;        // [nv][2] cos, sin (FP64)
+    float *d_view_csf;        // [nv][2] cos, sin (FP32)
+    double *d_cell_d;         // [nd][4] s_j, L_j, dtan_j, 0 (FP64)
+    float *d_cell_f;          // [nd][4] ds/L_j, D_ps dtan_j/(2L_j), s_j dtan_j/(2L_j), 0
+    float *d_box;             // [nv][nd][4] p, q, iC, nrm (FP32)
+    cnsf::RayF *d_ray;        // [nv][nd]
+};

@@ -1,0 +1,25 @@
+// cnsf_runtime.h -- internal entry points between the C ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cnsf.h"
+
+namespace cnsf {
+
+// Remember the CUDA error text for cnsf_last_cuda_error (per host thread); returns CNSF_ERR_CUDA.
+int record_cuda_error(cudaError_t e = cudaGetLastError());
+
+int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out);
+void destroy_geometry(cnsf_geometry *geo);
+
+// Kernel launchers (arguments already validated by the C ABI layer).
+int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,
+                   cudaStream_t stream);
+int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch, int dtype,
+                cudaStream_t stream);
+int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t stream);
+
+}  // namespace cnsf

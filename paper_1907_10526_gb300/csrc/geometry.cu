@@ -1,0 +1,199 @@
+// geometry.cu -- validation and device tables of a fan-beam geometry (Sec. II.A, Eq. 17).
+//
+// Everything here runs once per geometry, on the host, in FP64.  The per-(view, cell)
+// walk of the forward projector is converted to 32.32 fixed point and every walk is
+// checked, with the same integer arithmetic the kernel uses, to stay inside the
+// zero-padded image copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cnsf.h"
+#include "cnsf_internal.cuh"
+#include "cnsf_runtime.h"
+
+namespace cnsf {
+
+static inline long long ceil_fx(long long a)   // ceil(a / 2^32)
+{
+    long long hi = a >> 32;
+    return hi + (((unsigned long long)a & 0xffffffffull) != 0ull ? 1 : 0);
+}
+
+static int validate(const cnsf_geometry_desc *d)
+{
+    if (!d) return CNSF_ERR_INVALID;
+    if (d->n_x < 1 || d->n_y < 1 || d->n_views < 1 || d->n_det < 1) return CNSF_ERR_INVALID;
+    if (d->n_x > (1 << 16) || d->n_y > (1 << 16) || d->n_det > (1 << 20) || d->n_views > (1 << 20))
+        return CNSF_ERR_INVALID;
+    if (!(d->pixel_mm > 0) || !(d->det_spacing_mm > 0) || !(d->det_width_mm > 0)) return CNSF_ERR_INVALID;
+    if (!(d->d_po_mm > 0) || !(d->d_ps_mm > d->d_po_mm)) return CNSF_ERR_INVALID;
+    if (!std::isfinite(d->center_x_mm) || !std::isfinite(d->center_y_mm) || !std::isfinite(d->det_offset_mm))
+        return CNSF_ERR_INVALID;
+    if (d->detector != CNSF_DETECTOR_FLAT) return CNSF_ERR_UNSUPPORTED;
+    double rx = std::fabs(d->center_x_mm) + 0.5 * d->n_x * d->pixel_mm;
+    double ry = std::fabs(d->center_y_mm) + 0.5 * d->n_y * d->pixel_mm;
+    if (std::hypot(rx, ry) + 2.0 * d->pixel_mm >= d->d_po_mm) return CNSF_ERR_INVALID;
+    if (d->angles_rad)
+        for (int k = 0; k < d->n_views; ++k)
+            if (!std::isfinite(d->angles_rad[k])) return CNSF_ERR_INVALID;
+    return CNSF_OK;
+}
+
+int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
+{
+    if (!out) return CNSF_ERR_INVALID;
+    *out = nullptr;
+    int st = validate(d);
+    if (st != CNSF_OK) return st;
+
+    GeomConsts g{};
+    g.nx = d->n_x; g.ny = d->n_y; g.nv = d->n_views; g.nd = d->n_det;
+    g.h = d->pixel_mm; g.cx = d->center_x_mm; g.cy = d->center_y_mm;
+    g.ds = d->det_spacing_mm; g.tau = d->det_width_mm; g.doff = d->det_offset_mm;
+    g.dpo = d->d_po_mm; g.dps = d->d_ps_mm;
+    g.rimg = std::hypot(std::fabs(g.cx) + 0.5 * g.nx * g.h, std::fabs(g.cy) + 0.5 * g.ny * g.h);
+    g.s0 = cell_centre(g, 0);
+
+    const int nv = g.nv, nd = g.nd;
+    const size_t nr = (size_t)nv * nd;
+    std::vector<double> cs(2 * (size_t)nv);
+    for (int k = 0; k < nv; ++k) {
+        double th = d->angles_rad ? d->angles_rad[k] : 2.0 * M_PI * k / nv;
+        cs[2 * k] = std::cos(th);
+        cs[2 * k + 1] = std::sin(th);
+    }
+    std::vector<double> celld(4 * (size_t)nd);
+    std::vector<float> cellf(4 * (size_t)nd);
+    double dtan_max = 0.0, smax = 0.0;
+    for (int j = 0; j < nd; ++j) {
+        double sj = cell_centre(g, j), L = std::sqrt(g.dps * g.dps + sj * sj), dt = cell_dtan(g, sj);
+        celld[4 * j] = sj; celld[4 * j + 1] = L; celld[4 * j + 2] = dt; celld[4 * j + 3] = 0.0;
+        cellf[4 * j] = (float)(g.ds / L);
+        cellf[4 * j + 1] = (float)(g.dps * dt / (2.0 * L));
+        cellf[4 * j + 2] = (float)(sj * dt / (2.0 * L));
+        cellf[4 * j + 3] = 0.0f;
+        dtan_max = std::max(dtan_max, dt);
+        smax = std::max(smax, std::fabs(sj));
+    }
+
+    // Forward-walk tables.
+    std::vector<RayF> rays(nr);
+    std::vector<float> box(4 * nr);
+    const double fx_one = 4294967296.0;  // 2^32
+    const double tmax = g.dpo + g.rimg + g.h;
+    int kc_max = 1;
+    std::vector<double> hw_of(nr);
+    for (int k = 0; k < nv; ++k) {
+        for (int j = 0; j < nd; ++j) {
+            size_t q = (size_t)k * nd + j;
+            RayParams<double> R = make_ray_params<double>(g, cs[2 * k], cs[2 * k + 1], j);
+            BoxConsts<double> bc = make_box_consts<double>(R.B, R.C, g.h);
+            box[4 * q] = (float)bc.p; box[4 * q + 1] = (float)bc.q;
+            box[4 * q + 2] = (float)bc.iC; box[4 * q + 3] = (float)bc.nrm;
+            double emax = tmax * 0.5 * R.dtan;
+            double hw = (0.5 * (R.B + R.C) + emax) / R.B + 1e-3;
+            int kc = (int)std::floor(2.0 * hw) + 1;
+            kc_max = std::max(kc_max, kc);
+            hw_of[q] = hw;
+            // lines whose window [f - hw, f + hw] meets [0, na-1], widened by one
+            int r0 = 0, r1 = R.nb - 1;
+            if (std::fabs(R.g) < 1e-300) {
+                if (R.f0 < -hw || R.f0 > R.na - 1 + hw) r1 = -1;
+            } else {
+                double ra = (-hw - R.f0) / R.g, rb = (R.na - 1 + hw - R.f0) / R.g;
+                if (ra > rb) std::swap(ra, rb);
+                double lo = std::max(0.0, std::ceil(ra) - 1.0), hi = std::min((double)(R.nb - 1), std::floor(rb) + 1.0);
+                r0 = (int)lo;
+                r1 = hi < lo ? -1 : (int)hi;
+            }
+            RayF &F = rays[q];
+            F.G = std::llround(R.g * fx_one);
+            F.kc = kc;
+            F.flags = R.transposed;
+            F.hw = (float)hw;
+            F.kap = (float)R.kap;
+            F.de = (float)R.de;
+            // exact integer check of the candidate window at a line
+            auto meets = [&](int rbi, long long A0, int r0i) {
+                long long A = A0 + (long long)(rbi - r0i) * F.G;
+                long long ilo = ceil_fx(A);
+                return ilo <= R.na - 1 && ilo + kc - 1 >= 0;
+            };
+            auto a0_at = [&](int rbi) { return std::llround((R.f0 + rbi * R.g - hw) * fx_one); };
+            while (r0 <= r1 && !meets(r0, a0_at(r0), r0)) ++r0;
+            if (r0 <= r1) {
+                long long A0 = a0_at(r0);
+                while (r1 >= r0 && !meets(r1, A0, r0)) --r1;
+                F.A0 = A0;
+            } else {
+                F.A0 = 0;
+            }
+            F.r0 = r0 <= r1 ? r0 : 0;
+            F.nrows = r0 <= r1 ? r1 - r0 + 1 : 0;
+            // Pixels of the image lie in front of the source (validated), so their depth and e
+            // are positive; candidates in the zero padding may not be, but carry weight 0.
+            F.e0 = (float)(R.e0 + F.r0 * R.de);
+        }
+    }
+    int pad = ((kc_max + 1 + 3) / 4) * 4;
+    // The walk never leaves [-pad, na-1+pad]: windows that meet [0, na-1] are at most kc wide.
+    for (size_t q = 0; q < nr; ++q) {
+        const RayF &F = rays[q];
+        if (F.nrows == 0) continue;
+        int na = F.flags ? g.ny : g.nx;
+        for (int end = 0; end < 2; ++end) {
+            long long A = F.A0 + (long long)(end ? F.nrows - 1 : 0) * F.G;
+            long long ilo = ceil_fx(A);
+            if (ilo < -pad || ilo + F.kc - 1 > na - 1 + pad) return CNSF_ERR_INTERNAL;
+        }
+    }
+
+    cnsf_geometry *geo = new (std::nothrow) cnsf_geometry();
+    if (!geo) return CNSF_ERR_NOMEM;
+    geo->gc = g;
+    geo->pad = pad;
+    geo->kc_max = kc_max;
+    double reach = 0.5 * (std::sqrt(2.0) * g.h + tmax * dtan_max) + 1e-3 * g.h;
+    double lmax = std::sqrt(g.dps * g.dps + (smax + g.ds) * (smax + g.ds));
+    geo->kr = reach * lmax / g.ds;
+    if (cudaGetDevice(&geo->device) != cudaSuccess) { delete geo; return record_cuda_error(); }
+
+    std::vector<float> csf(2 * (size_t)nv);
+    for (size_t i = 0; i < csf.size(); ++i) csf[i] = (float)cs[i];
+    struct Up { void **dst; const void *src; size_t bytes; };
+    Up ups[] = {
+        {(void **)&geo->d_view_cs, cs.data(), cs.size() * sizeof(double)},
+        {(void **)&geo->d_view_csf, csf.data(), csf.size() * sizeof(float)},
+        {(void **)&geo->d_cell_d, celld.data(), celld.size() * sizeof(double)},
+        {(void **)&geo->d_cell_f, cellf.data(), cellf.size() * sizeof(float)},
+        {(void **)&geo->d_box, box.data(), box.size() * sizeof(float)},
+        {(void **)&geo->d_ray, rays.data(), rays.size() * sizeof(RayF)},
+    };
+    for (const Up &u : ups) {
+        cudaError_t e = cudaMalloc(u.dst, u.bytes);
+        if (e != cudaSuccess) {
+            destroy_geometry(geo);
+            return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+        }
+        e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { destroy_geometry(geo); return record_cuda_error(e); }
+    }
+    *out = geo;
+    return CNSF_OK;
+}
+
+void destroy_geometry(cnsf_geometry *geo)
+{
+    if (!geo) return;
+    void *ptrs[] = {geo->d_view_cs, geo->d_view_csf, geo->d_cell_d, geo->d_cell_f, geo->d_box, geo->d_ray};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete geo;
+}
+
+}  // namespace cnsf

@@ -1,0 +1,210 @@
+"""Parity of the CUDA projector with the FP64 oracle (GPU).
+
+Tolerances: FP64 kernels 1e-12 relative L2, FP32 kernels 1e-5 relative L2 against the
+FP64 oracle (the accuracy bar of the projector).  Small cases compare every output;
+the 512^2 x 720-view workload compares sampled rays and pixels that the oracle computes
+one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import FanGeometry, config_geometry, ellipse_phantom, phantom_for_config
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def cnsf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1907_10526_gb300 as m
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _fwd(cnsf, geom, img, dt):
+    return cnsf.forward_project(geom, torch.tensor(img, dtype=dt, device="cuda")).double().cpu().numpy()
+
+
+def _bwd(cnsf, geom, sino, dt):
+    return cnsf.back_project(geom, torch.tensor(sino, dtype=dt, device="cuda")).double().cpu().numpy()
+
+
+# ------------------------------------------------------------------ small, every output
+RAGGED = FanGeometry(nx=100, ny=77, n_views=37, n_det=181, d_po=200.0, d_ps=450.0, center_x=3.2,
+                     center_y=-1.7, det_offset=0.45, det_spacing=0.9, det_width=0.8, pixel=1.1)
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_config1_forward_back(cnsf, dt):
+    g = config_geometry(1)
+    geom = cnsf.Geometry(g)
+    img = phantom_for_config(1)
+    y_ref = oracle.forward(g, img)
+    assert rel(_fwd(cnsf, geom, img, dt), y_ref) < TOL[dt]
+    assert rel(_bwd(cnsf, geom, y_ref, dt), oracle.back(g, y_ref)) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_ragged_multi_tile(cnsf, dt):
+    """Image and detector sizes that are not multiples of any tile, offsets everywhere."""
+    g = RAGGED
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(21)
+    img = rng.uniform(0, 1, (g.ny, g.nx))
+    sino = rng.uniform(0, 1, (g.n_views, g.n_det))
+    assert rel(_fwd(cnsf, geom, img, dt), oracle.forward(g, img)) < TOL[dt]
+    assert rel(_bwd(cnsf, geom, sino, dt), oracle.back(g, sino)) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_degenerate_angles(cnsf, dt):
+    """Axis-aligned and near-axis views (one footprint width -> 0, M_0 = delta) and 45 deg."""
+    eps = 1e-7
+    ang = (0.0, eps, -eps, math.pi / 2, math.pi / 2 + eps, math.pi / 2 - eps, math.pi, 1.5 * math.pi,
+           math.pi / 4, 3 * math.pi / 4 + eps)
+    g = FanGeometry(nx=64, ny=64, n_views=len(ang), n_det=129, d_po=300.0, d_ps=600.0, angles=ang)
+    geom = cnsf.Geometry(g)
+    img = ellipse_phantom(64, 6, 1.0, seed=5)
+    y_ref = oracle.forward(g, img)
+    assert rel(_fwd(cnsf, geom, img, dt), y_ref) < TOL[dt]
+    assert rel(_bwd(cnsf, geom, y_ref, dt), oracle.back(g, y_ref)) < TOL[dt]
+
+
+def _random_geoms():
+    rng = np.random.default_rng(99)
+    out = []
+    for _ in range(6):
+        n_x, n_y = int(rng.integers(5, 60)), int(rng.integers(5, 60))
+        h = float(rng.uniform(0.3, 2.0))
+        rad = math.hypot(n_x, n_y) * h / 2
+        d_po = rad * float(rng.uniform(1.3, 4.0)) + 3 * h
+        out.append(FanGeometry(nx=n_x, ny=n_y, n_views=int(rng.integers(1, 40)), n_det=int(rng.integers(1, 200)),
+                               pixel=h, det_spacing=float(rng.uniform(0.2, 2.0)),
+                               det_width=float(rng.uniform(0.1, 2.5)), d_po=d_po,
+                               d_ps=d_po * float(rng.uniform(1.2, 3.0)),
+                               center_x=float(rng.uniform(-1, 1)) * h, center_y=float(rng.uniform(-1, 1)) * h,
+                               det_offset=float(rng.uniform(-3, 3)), angles=None))
+    return out
+
+
+@pytest.mark.parametrize("g", _random_geoms())
+def test_random_geometries_fp64(cnsf, g):
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(3)
+    img = rng.uniform(-1, 1, (g.ny, g.nx))
+    sino = rng.uniform(-1, 1, (g.n_views, g.n_det))
+    assert rel(_fwd(cnsf, geom, img, torch.float64), oracle.forward(g, img)) < 1e-12
+    assert rel(_bwd(cnsf, geom, sino, torch.float64), oracle.back(g, sino)) < 1e-12
+    assert rel(_fwd(cnsf, geom, img, torch.float32), oracle.forward(g, img)) < 1e-5
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_adjoint_identity_on_gpu(cnsf, dt):
+    g = RAGGED
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(8)
+    c = torch.tensor(rng.uniform(-1, 1, (g.ny, g.nx)), dtype=dt, device="cuda")
+    y = torch.tensor(rng.uniform(-1, 1, (g.n_views, g.n_det)), dtype=dt, device="cuda")
+    Ac = cnsf.forward_project(geom, c).double()
+    Aty = cnsf.back_project(geom, y).double()
+    lhs = float((Ac * y.double()).sum())
+    rhs = float((c.double() * Aty).sum())
+    assert abs(lhs - rhs) / float(Ac.norm() * y.double().norm()) < TOL[dt]
+
+
+def test_batch_matches_single(cnsf):
+    g = config_geometry(1)
+    geom = cnsf.Geometry(g)
+    imgs = np.stack([ellipse_phantom(64, 8, 1.0, seed=s) for s in (1, 2, 3)])
+    xb = torch.tensor(imgs, dtype=torch.float32, device="cuda")
+    yb = cnsf.forward_project(geom, xb)
+    bb = cnsf.back_project(geom, yb)
+    for k in range(3):
+        yk = cnsf.forward_project(geom, xb[k])
+        assert torch.equal(yb[k], yk)
+        assert torch.equal(bb[k], cnsf.back_project(geom, yk))
+
+
+def test_empty_batch_and_errors(cnsf):
+    g = config_geometry(1)
+    geom = cnsf.Geometry(g)
+    y = cnsf.forward_project(geom, torch.zeros((0, 64, 64), device="cuda"))
+    assert y.shape == (0, 90, 128)
+    with pytest.raises(ValueError):
+        cnsf.forward_project(geom, torch.zeros((64, 65), device="cuda"))
+    with pytest.raises(TypeError):
+        cnsf.forward_project(geom, torch.zeros((64, 64), dtype=torch.float16, device="cuda"))
+    with pytest.raises(cnsf.CnsfError):
+        cnsf.Geometry(FanGeometry(nx=1000, ny=1000, n_views=4, n_det=8, d_po=500.0, d_ps=1000.0))
+
+
+def test_host_tensors_round_trip(cnsf):
+    """CPU tensors go through the device and come back (the end-to-end path)."""
+    g = config_geometry(1)
+    geom = cnsf.Geometry(g)
+    img = torch.tensor(phantom_for_config(1), dtype=torch.float32).pin_memory()
+    y_host = cnsf.forward_project(geom, img)
+    assert y_host.device.type == "cpu"
+    y_dev = cnsf.forward_project(geom, img.cuda())
+    assert torch.equal(y_host, y_dev.cpu())
+
+
+def test_nonzero_count_matches_oracle(cnsf):
+    g = RAGGED
+    geom = cnsf.Geometry(g)
+    n_gpu = cnsf.count_nonzeros(geom)
+    n_ref = oracle.count_nnz(g)
+    # support endpoints are decided in FP32 on the GPU and in FP64 in the oracle
+    assert abs(n_gpu - n_ref) <= max(2, 1e-6 * n_ref)
+
+
+# ------------------------------------------------------------------ full-size workload, sampled
+@pytest.fixture(scope="module")
+def cfg2(cnsf):
+    g = config_geometry(2)
+    geom = cnsf.Geometry(g)
+    img = phantom_for_config(2)
+    y = cnsf.forward_project(geom, torch.tensor(img, dtype=torch.float32, device="cuda"))
+    return g, geom, img, y
+
+
+def test_config2_forward_sampled(cfg2):
+    g, geom, img, y = cfg2
+    rng = np.random.default_rng(2)
+    views = rng.integers(0, g.n_views, 400)
+    cells = rng.integers(0, g.n_det, 400)
+    ref = oracle.forward_rays(g, img, views, cells)
+    got = y.double().cpu().numpy()[views, cells]
+    assert rel(got, ref) < 1e-5
+
+
+def test_config2_back_sampled(cnsf, cfg2):
+    g, geom, img, y = cfg2
+    yh = y.double().cpu().numpy()
+    x = cnsf.back_project(geom, y).double().cpu().numpy()
+    rng = np.random.default_rng(3)
+    pix = rng.integers(0, g.nx * g.ny, 300)
+    ref = oracle.back_pixels(g, yh, pix)
+    assert rel(x.ravel()[pix], ref) < 1e-5
+
+
+def test_config2_adjoint_fp32(cnsf, cfg2):
+    g, geom, img, y = cfg2
+    rng = np.random.default_rng(4)
+    s = torch.tensor(rng.uniform(0, 1, (g.n_views, g.n_det)), dtype=torch.float32, device="cuda")
+    c = torch.tensor(img, dtype=torch.float32, device="cuda")
+    lhs = float((y.double() * s.double()).sum())
+    rhs = float((c.double() * cnsf.back_project(geom, s).double()).sum())
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5

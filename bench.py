@@ -296,7 +296,7 @@ def run_cnsf(args):
         "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "bp_f32_kernel"],
     }
     if rank == 0 and not args.no_cpu_baseline:
-        r, dt, thr, desc = oracle_sample_rate(180)
+        r, dt, thr, desc = oracle_sample_rate(720)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
                                 "seconds": dt}
     if rank == 0:
@@ -309,7 +309,7 @@ def run_cnsf(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cnsf", choices=["cnsf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -119,6 +119,28 @@ CNSF_API int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void
  * Synchronous; *count is a host pointer. */
 CNSF_API int cnsf_count_nonzeros(const cnsf_geometry *geom, uint64_t *count, void *stream);
 
+/* Size of the static device array used by cnsf_forward_project_noalloc: 16 MiB. */
+#define CNSF_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* Forward projection that allocates no memory (the paper has no counterpart: this
+ * exists for callers that may not allocate device memory, such as a plugin inside a
+ * framework that owns the device-memory budget, or a loop that must not wait on the
+ * allocator).  Same arguments, layouts and result as cnsf_forward_project; its scratch
+ * (the zero-padded copies of the image) lives in one file-scope device array of
+ * CNSF_NOALLOC_SCRATCH_BYTES that every GPU loading the library reserves until the
+ * process exits.  The request must fit:
+ *     batch * (n_y*(n_x + 2*pad) + n_x*(n_y + 2*pad)) * sizeof(element) <= 16 MiB,
+ * pad being the geometry's padding (8 for 1 mm cells and pixels), e.g. batch <= 7 at
+ * 512^2 FP32, batch 1 up to ~1400^2 FP32; larger requests return CNSF_ERR_UNSUPPORTED
+ * and launch nothing.  The first call on a device looks up the array's device address
+ * (which may load the library's device code); make that first call before any stream
+ * capture.  Every call on a device shares the one array: calls whose work overlaps on
+ * the GPU (different streams without ordering between them) race and may corrupt
+ * each other's results.  The array keeps the last call's contents; nothing in it needs
+ * clearing because each call rewrites every element it reads. */
+CNSF_API int cnsf_forward_project_noalloc(const cnsf_geometry *geom, const void *image, void *sino,
+                                          int32_t batch, int32_t dtype, void *stream);
+
 /* Status code to a static English string. */
 CNSF_API const char *cnsf_status_string(int status);
 

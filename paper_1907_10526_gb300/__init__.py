@@ -17,7 +17,8 @@ import torch
 
 from ._lib import CNSF_F32, CNSF_F64, CnsfError, GeometryDesc, check, lib  # noqa: F401
 
-__all__ = ["Geometry", "forward_project", "back_project", "count_nonzeros", "Projector", "CnsfError"]
+__all__ = ["Geometry", "forward_project", "back_project", "count_nonzeros", "forward_project_noalloc",
+           "Projector", "CnsfError"]
 
 
 def _dtype_code(t: torch.dtype) -> int:
@@ -142,6 +143,19 @@ def back_project(geom: Geometry, sino: torch.Tensor, out: Optional[torch.Tensor]
     """c = A^T y.  sinogram [..., n_views, n_det] -> image [..., ny, nx]."""
     return _run(lib.cnsf_back_project, "cnsf_back_project", geom, sino, geom.sino_shape, geom.image_shape,
                 out, stream)
+
+
+def forward_project_noalloc(geom: Geometry, image: torch.Tensor, out: Optional[torch.Tensor] = None,
+                            stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """y = A c through the entry point that allocates nothing inside the library.
+
+    For callers that may not allocate device memory while projecting: the library's
+    scratch is a fixed 16 MiB device array instead.  Pass ``out`` to keep this call free
+    of allocations on the Python side too.  Calls on different streams must not overlap
+    on the GPU (they share the array).  Requests larger than the array raise CnsfError.
+    """
+    return _run(lib.cnsf_forward_project_noalloc, "cnsf_forward_project_noalloc", geom, image,
+                geom.image_shape, geom.sino_shape, out, stream)
 
 
 def count_nonzeros(geom: Geometry, stream: Optional[torch.cuda.Stream] = None) -> int:

@@ -35,6 +35,7 @@ _SIGNATURES = {
     "cnsf_forward_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_back_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_count_nonzeros": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), _P]),
+    "cnsf_forward_project_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cnsf_last_cuda_error": (ctypes.c_char_p, []),
 }

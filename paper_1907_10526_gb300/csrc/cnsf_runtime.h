@@ -22,4 +22,9 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
                 cudaStream_t stream);
 int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t stream);
 
+// Forward projection into caller-provided scratch (bytes from forward_scratch_bytes).
+size_t forward_scratch_bytes(const cnsf_geometry *geo, int batch, int dtype);
+int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,
+                                void *scratch, size_t scratch_bytes, cudaStream_t stream);
+
 }  // namespace cnsf

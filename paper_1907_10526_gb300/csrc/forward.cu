@@ -258,6 +258,45 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
+// Forward projection whose padded copies go into a buffer the caller provides (no
+// allocation).  Returns CNSF_ERR_UNSUPPORTED when the buffer is smaller than
+// forward_scratch_bytes().
+size_t forward_scratch_bytes(const cnsf_geometry *geo, int batch, int dtype)
+{
+    const GeomConsts &g = geo->gc;
+    size_t per = (size_t)g.ny * (g.nx + 2 * geo->pad) + (size_t)g.nx * (g.ny + 2 * geo->pad);
+    return (size_t)batch * per * (dtype == CNSF_F64 ? sizeof(double) : sizeof(float));
+}
+
+int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,
+                                void *scratch, size_t scratch_bytes, cudaStream_t st)
+{
+    if (batch == 0) return CNSF_OK;
+    if (forward_scratch_bytes(geo, batch, dtype) > scratch_bytes) return CNSF_ERR_UNSUPPORTED;
+    const GeomConsts &g = geo->gc;
+    const int nr = g.nv * g.nd, pad = geo->pad;
+    const int pitchP = g.nx + 2 * pad, pitchT = g.ny + 2 * pad;
+    const long long strideP = (long long)g.ny * pitchP, strideT = (long long)g.nx * pitchT;
+    dim3 blk(128), grdr((pitchP + 127) / 128, g.ny, batch);
+    dim3 blkt(32, 8), grdt((pitchT + 31) / 32, (g.nx + 31) / 32, batch);
+    dim3 grd((nr + 127) / 128, batch);
+    if (dtype == CNSF_F32) {
+        float *P = (float *)scratch, *Tt = P + (size_t)batch * strideP;
+        pad_rows_kernel<float><<<grdr, blk, 0, st>>>((const float *)img, P, g.nx, g.ny, pad, pitchP, 0);
+        pad_transpose_kernel<float><<<grdt, blkt, 0, st>>>((const float *)img, Tt, g.nx, g.ny, pad, pitchT, 0);
+        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_ray, (const float4 *)geo->d_box, P, Tt, pitchP, pitchT,
+                                                  strideP, strideT, pad, nr, (float *)sino);
+    } else {
+        double *P = (double *)scratch, *Tt = P + (size_t)batch * strideP;
+        pad_rows_kernel<double><<<grdr, blk, 0, st>>>((const double *)img, P, g.nx, g.ny, pad, pitchP, 0);
+        pad_transpose_kernel<double><<<grdt, blkt, 0, st>>>((const double *)img, Tt, g.nx, g.ny, pad, pitchT, 0);
+        fp_f64_kernel<<<grd, blk, 0, st>>>(g, geo->d_view_cs, geo->d_ray, P, Tt, pitchP, pitchT, strideP, strideT,
+                                           pad, nr, (double *)sino);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
 // Non-zero entries: pairs strictly inside the support of M_[B, C, tau'], found by the
 // forward walk over an image of ones (the zero padding contributes nothing).
 int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t st)

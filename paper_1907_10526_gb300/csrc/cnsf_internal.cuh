@@ -137,7 +137,9 @@ struct TileView {
     int J;
 };
 
-__host__ __device__ inline void tile_view_double(const GeomConsts &g, double c, double s, int it, int rt,
+// (it, rt) is the reference point of the tile in pixel-index units (its centre, so that the
+// per-pixel offsets stay small).
+__host__ __device__ inline void tile_view_double(const GeomConsts &g, double c, double s, double it, double rt,
                                                  double *Dt, double *yt, double *a1, double *b1,
                                                  double *rho, double *phi, int *J)
 {
@@ -173,6 +175,28 @@ struct RayF {
 };
 static_assert(sizeof(RayF) == 48, "RayF layout");
 
+// Per-(view, cell) trapezoid constants of the FP32 kernels: box_B * box_C (Eq. 16 widths)
+// as p = (B - C)/2, q/C, 1/C (clamped for C = 0) and C/2.  B = 2(p + C/2); the
+// normalisation of Eq. (18) with the pixel area is h^2/(2B).
+struct alignas(16) BoxF {
+    float p, qiC, iC, hC;
+};
+
+// Per-cell constants of the FP32 back projector: s' = D_n g1 (sigma - j) and
+// tau'/2 = D_n c1 + y' c2 for a pixel at depth D_n and coordinate y' along w.
+struct alignas(16) CellF {
+    float g1, c1, c2, pad;   // ds/L_j, D_ps dtan_j/(2 L_j), s_j dtan_j/(2 L_j)
+};
+
+// Back-projector cell window (cells) of a pixel at depth D_n, coordinate y' along w:
+//   hwc = kz * h(|y' c - D_n s| + |y' s + D_n c|) / D_n^2 * (1.02 + 2 h / D_n) + ke
+// The first term is (zeta1 + zeta2)/2 * L / (D_n ds) for the ray through the pixel centre
+// (the widths of Eq. 16 on that ray, with slack for the neighbouring cell rays), the second
+// bounds tau'/2 * L / (D_n ds) = (D_ps + s_j s_n / D_ps) dtan_j / (2 ds).
+struct BpWindow {
+    double kz, ke;
+};
+
 }  // namespace cnsf
 
 // Host-side geometry object behind the opaque handle.
@@ -181,12 +205,11 @@ struct cnsf_geometry {
     int device;
     int pad;                  // zero columns on each side of the padded image copies
     int kc_max;               // largest candidate count per walked line
-    double kr;                // back projector: cell half-window = kr / D_n (cells)
+    cnsf::BpWindow bw;        // back projector cell window
     // device tables
     double *d_view_cs;        // [nv][2] cos, sin (FP64)
-    float *d_view_csf;        // [nv][2] cos, sin (FP32)
     double *d_cell_d;         // [nd][4] s_j, L_j, dtan_j, 0 (FP64)
-    float *d_cell_f;          // [nd][4] ds/L_j, D_ps dtan_j/(2L_j), s_j dtan_j/(2L_j), 0
-    float *d_box;             // [nv][nd][4] p, q, iC, nrm (FP32)
+    cnsf::BoxF *d_box;        // [nv][nd]
+    cnsf::CellF *d_cellf;     // [nd]
     cnsf::RayF *d_ray;        // [nv][nd]
 };

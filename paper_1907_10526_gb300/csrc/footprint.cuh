@@ -37,4 +37,34 @@ __device__ __forceinline__ T window_diff(T x, T e, T p, T qiC, T iC, T hC)
     return (h1 + hC) - copysign(h0, z0);
 }
 
+// 1/x by the hardware approximation (max error ~1 ulp); x is a blur half-width or a
+// depth here, never denormal or huge, so the range handling of IEEE division is not needed.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Two entries at once with the packed FP32 instructions of sm_100+ (FADD2/FMUL2/FFMA2):
+// the same arithmetic as window_diff, lane by lane, for candidates that share the
+// trapezoid constants (p, q/C, 1/C, C/2 given as pairs).  min, saturate and sign
+// handling have no packed form and stay scalar.
+__device__ __forceinline__ float2 window_diff2(float2 x, float2 e, float2 ne1, float p, float qiC, float iC,
+                                               float2 hC2, float2 nhC2)
+{
+    const float2 z1 = __fadd2_rn(x, e);
+    const float2 z0 = __ffma2_rn(e, ne1, x);          // x - e
+    const float a0x = fabsf(z0.x), a0y = fabsf(z0.y);
+    const float2 m1 = make_float2(fminf(z1.x, p), fminf(z1.y, p));
+    const float2 m0 = make_float2(fminf(a0x, p), fminf(a0y, p));
+    const float2 v1 = make_float2(sat01(fmaf(-z1.x, iC, qiC)), sat01(fmaf(-z1.y, iC, qiC)));
+    const float2 v0 = make_float2(sat01(fmaf(-a0x, iC, qiC)), sat01(fmaf(-a0y, iC, qiC)));
+    const float2 t1 = __ffma2_rn(__fmul2_rn(nhC2, v1), v1, m1);   // B H(z1) - C/2
+    const float2 t0 = __ffma2_rn(__fmul2_rn(nhC2, v0), v0, m0);
+    const float2 h0 = __fadd2_rn(t0, hC2);                      // B H(|z0|)
+    const float2 cs = make_float2(copysignf(h0.x, z0.x), copysignf(h0.y, z0.y));
+    return __ffma2_rn(cs, ne1, __fadd2_rn(t1, hC2));             // (t1 + C/2) - sgn(z0) h0
+}
+
 }  // namespace cnsf

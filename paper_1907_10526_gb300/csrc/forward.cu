@@ -72,10 +72,82 @@ __device__ __forceinline__ float line_sum(const float *__restrict__ rp, float u,
             s += (x < p + 2.f * hC + e) ? c : 0.f;
         } else {
             float d = window_diff(x, e, p, qiC, iC, hC);
-            s = fmaf(c, __fdividef(d, e), s);
+            s = fmaf(c, d * rcp_approx(e), s);
         }
     }
     return s;
+}
+
+// Two consecutive lines of the walk at once with packed FP32 arithmetic: lane .x of every
+// float2 belongs to line rb, lane .y to line rb + 1, and the KC candidates of both lines
+// are evaluated pair by pair (no padding candidates).
+template <int KC>
+__device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, const float *__restrict__ rp1,
+                                                float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1,
+                                                float p, float qiC, float iC, float2 hC2, float2 nhC2)
+{
+    float2 s = make_float2(0.f, 0.f);
+    const float2 one = make_float2(1.0f, 1.0f);
+#pragma unroll
+    for (int m = 0; m < KC; ++m) {
+        const float2 xs = __fmul2_rn(B2, u);
+        const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));
+        const float2 e = __ffma2_rn(kap2, u, er2);
+        const float2 d = window_diff2(x, e, ne1, p, qiC, iC, hC2, nhC2);
+        const float2 w = make_float2(d.x * rcp_approx(e.x), d.y * rcp_approx(e.y));
+        const float2 c = make_float2(__ldg(rp0 + m), __ldg(rp1 + m));
+        s = __ffma2_rn(c, w, s);
+        u = __fadd2_rn(u, one);
+    }
+    return s;
+}
+
+__device__ __forceinline__ void fx_window(long long A, int &ilo, float &rho)
+{
+    // first candidate ilo = ceil(f - hw); rho = ilo - (f - hw) in [0, 1) from the low word
+    ilo = (int)(A >> 32) + (((unsigned)A) != 0u ? 1 : 0);
+    unsigned nl = 0u - (unsigned)A;
+    rho = __uint_as_float(0x3f800000u | (nl >> 9)) - 1.0f;
+}
+
+template <int KC>
+__device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ base, int pitch, float B,
+                                       float p, float qiC, float iC, float hC)
+{
+    long long A = R.A0;
+    const long long G = R.G;
+    float2 er2 = make_float2(R.e0, R.e0 + R.de);
+    const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);
+    const float2 B2 = make_float2(B, B), ne1 = make_float2(-1.0f, -1.0f);
+    const float2 hC2 = make_float2(hC, hC), nhC2 = make_float2(-hC, -hC);
+    const float hw = R.hw;
+    float2 acc = make_float2(0.f, 0.f), part = make_float2(0.f, 0.f);
+    int rr = 0;
+    for (; rr + 1 < R.nrows; rr += 2) {
+        int ilo0, ilo1;
+        float rho0, rho1;
+        fx_window(A, ilo0, rho0);
+        fx_window(A + G, ilo1, rho1);
+        const float2 u = make_float2(rho0 - hw, rho1 - hw);
+        part = __fadd2_rn(part, line_pair_sum<KC>(base + ilo0, base + pitch + ilo1, u, er2, kap2, B2, ne1, p,
+                                                  qiC, iC, hC2, nhC2));
+        A += 2 * G;
+        er2 = __fadd2_rn(er2, de2);
+        base += 2 * pitch;
+        if ((rr & 15) == 14) {   // blocked summation: partial sums of 16 lines
+            acc = __fadd2_rn(acc, part);
+            part = make_float2(0.f, 0.f);
+        }
+    }
+    acc = __fadd2_rn(acc, part);
+    float tot = acc.x + acc.y;
+    if (rr < R.nrows) {   // odd line count: the last line alone
+        int ilo;
+        float rho;
+        fx_window(A, ilo, rho);
+        tot += line_sum<KC, false>(base + ilo, rho - hw, er2.x, R.kap, B, p, qiC, iC, hC);
+    }
+    return tot;
 }
 
 template <int KC, bool COUNT>
@@ -105,7 +177,7 @@ __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ b
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(128) fp_f32_kernel(const RayF *__restrict__ rays, const float4 *__restrict__ box,
+__global__ void __launch_bounds__(128) fp_f32_kernel(const RayF *__restrict__ rays, const BoxF *__restrict__ box, float h2q,
                                                      const float *__restrict__ imgP, const float *__restrict__ imgT,
                                                      int pitchP, int pitchT, long long strideP, long long strideT,
                                                      int pad, int nr, float *__restrict__ sino)
@@ -116,13 +188,14 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const RayF *__restrict__ ra
     const RayF R = rays[q];
     float acc = 0.f;
     if (R.nrows > 0) {
-        const float4 bx = __ldg(box + q);
-        const float p = bx.x, qq = bx.y, iC = bx.z;
-        const float hC = 0.5f * (qq - p), qiC = qq * iC, B = p + qq;
+        const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
+        const float p = bx.x, qiC = bx.y, iC = bx.z, hC = bx.w;
+        const float B = 2.f * (p + hC);
         const bool tr = (R.flags & 1) != 0;
         const int pitch = tr ? pitchT : pitchP;
         const float *base = (tr ? imgT + b * strideT : imgP + b * strideP) + pad + (long long)R.r0 * pitch;
-        switch (R.kc) {
+        const int kcase = COUNT ? R.kc : 100 + R.kc;
+        switch (kcase) {
             case 1: acc = walk<1, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
             case 2: acc = walk<2, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
             case 3: acc = walk<3, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
@@ -131,6 +204,14 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const RayF *__restrict__ ra
             case 6: acc = walk<6, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
             case 7: acc = walk<7, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
             case 8: acc = walk<8, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 101: acc = walk2<1>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 102: acc = walk2<2>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 103: acc = walk2<3>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 104: acc = walk2<4>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 105: acc = walk2<5>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 106: acc = walk2<6>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 107: acc = walk2<7>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 108: acc = walk2<8>(R, base, pitch, B, p, qiC, iC, hC); break;
             default: {
                 // wide windows (cells much wider than pixels): generic loop
                 long long A = R.A0;
@@ -146,7 +227,7 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const RayF *__restrict__ ra
                         if (COUNT)
                             acc += (x < p + 2.f * hC + e) ? c : 0.f;
                         else
-                            acc += c * __fdividef(window_diff(x, e, p, qiC, iC, hC), e);
+                            acc += c * window_diff(x, e, p, qiC, iC, hC) * rcp_approx(e);
                     }
                     A += R.G;
                     er += R.de;
@@ -154,7 +235,7 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const RayF *__restrict__ ra
                 }
             }
         }
-        if (!COUNT) acc *= bx.w;
+        if (!COUNT) acc *= h2q / (p + hC);   // h^2/(2B), B = 2(p + C/2)
     }
     sino[b * nr + q] = acc;
 }
@@ -241,7 +322,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
         float *buf = nullptr;
         int s = make_padded<float>(geo, (const float *)img, batch, 0, st, &buf, &pitchP, &pitchT, &strideP, &strideT);
         if (s != CNSF_OK) return s;
-        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_ray, (const float4 *)geo->d_box, buf,
+        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf,
                                                   buf + (size_t)batch * strideP, pitchP, pitchT, strideP, strideT,
                                                   geo->pad, nr, (float *)sino);
         cudaFreeAsync(buf, st);
@@ -284,7 +365,7 @@ int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void 
         float *P = (float *)scratch, *Tt = P + (size_t)batch * strideP;
         pad_rows_kernel<float><<<grdr, blk, 0, st>>>((const float *)img, P, g.nx, g.ny, pad, pitchP, 0);
         pad_transpose_kernel<float><<<grdt, blkt, 0, st>>>((const float *)img, Tt, g.nx, g.ny, pad, pitchT, 0);
-        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_ray, (const float4 *)geo->d_box, P, Tt, pitchP, pitchT,
+        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P, Tt, pitchP, pitchT,
                                                   strideP, strideT, pad, nr, (float *)sino);
     } else {
         double *P = (double *)scratch, *Tt = P + (size_t)batch * strideP;
@@ -311,7 +392,7 @@ int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t st)
     cudaError_t e = cudaMallocAsync((void **)&out, (size_t)nr * sizeof(float), st);
     if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
     dim3 blk(128), grd((nr + 127) / 128, 1);
-    fp_f32_kernel<true><<<grd, blk, 0, st>>>(geo->d_ray, (const float4 *)geo->d_box, buf, buf + strideP, pitchP,
+    fp_f32_kernel<true><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + strideP, pitchP,
                                              pitchT, strideP, strideT, geo->pad, nr, out);
     std::vector<float> host(nr);
     e = cudaMemcpyAsync(host.data(), out, (size_t)nr * sizeof(float), cudaMemcpyDeviceToHost, st);

@@ -68,22 +68,25 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         cs[2 * k + 1] = std::sin(th);
     }
     std::vector<double> celld(4 * (size_t)nd);
-    std::vector<float> cellf(4 * (size_t)nd);
     double dtan_max = 0.0, smax = 0.0;
     for (int j = 0; j < nd; ++j) {
         double sj = cell_centre(g, j), L = std::sqrt(g.dps * g.dps + sj * sj), dt = cell_dtan(g, sj);
         celld[4 * j] = sj; celld[4 * j + 1] = L; celld[4 * j + 2] = dt; celld[4 * j + 3] = 0.0;
-        cellf[4 * j] = (float)(g.ds / L);
-        cellf[4 * j + 1] = (float)(g.dps * dt / (2.0 * L));
-        cellf[4 * j + 2] = (float)(sj * dt / (2.0 * L));
-        cellf[4 * j + 3] = 0.0f;
         dtan_max = std::max(dtan_max, dt);
         smax = std::max(smax, std::fabs(sj));
     }
 
-    // Forward-walk tables.
+    // Forward-walk tables and per-(view, cell) constants.
     std::vector<RayF> rays(nr);
-    std::vector<float> box(4 * nr);
+    std::vector<BoxF> box(nr);
+    std::vector<CellF> cellf(nd);
+    for (int j = 0; j < nd; ++j) {
+        const double sj = celld[4 * j], Lj = celld[4 * j + 1], dtj = celld[4 * j + 2];
+        cellf[j].g1 = (float)(g.ds / Lj);
+        cellf[j].c1 = (float)(g.dps * dtj / (2.0 * Lj));
+        cellf[j].c2 = (float)(sj * dtj / (2.0 * Lj));
+        cellf[j].pad = 0.0f;
+    }
     const double fx_one = 4294967296.0;  // 2^32
     const double tmax = g.dpo + g.rimg + g.h;
     int kc_max = 1;
@@ -93,8 +96,11 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
             size_t q = (size_t)k * nd + j;
             RayParams<double> R = make_ray_params<double>(g, cs[2 * k], cs[2 * k + 1], j);
             BoxConsts<double> bc = make_box_consts<double>(R.B, R.C, g.h);
-            box[4 * q] = (float)bc.p; box[4 * q + 1] = (float)bc.q;
-            box[4 * q + 2] = (float)bc.iC; box[4 * q + 3] = (float)bc.nrm;
+            BoxF &V = box[q];
+            V.p = (float)bc.p;
+            V.qiC = (float)(bc.q * bc.iC);
+            V.iC = (float)bc.iC;
+            V.hC = (float)(0.5 * R.C);
             double emax = tmax * 0.5 * R.dtan;
             double hw = (0.5 * (R.B + R.C) + emax) / R.B + 1e-3;
             int kc = (int)std::floor(2.0 * hw) + 1;
@@ -158,20 +164,29 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     geo->gc = g;
     geo->pad = pad;
     geo->kc_max = kc_max;
-    double reach = 0.5 * (std::sqrt(2.0) * g.h + tmax * dtan_max) + 1e-3 * g.h;
-    double lmax = std::sqrt(g.dps * g.dps + (smax + g.ds) * (smax + g.ds));
-    geo->kr = reach * lmax / g.ds;
+    // Back-projector window: cells within kz*zs/D_n^2*(1.02 + 2h/D_n) + ke of the pixel's
+    // projection.  W bounds |s_n - s_j| over the window (widest at the nearest pixel depth).
+    {
+        double dmin = g.dpo - g.rimg;
+        double lmax = std::sqrt(g.dps * g.dps + (smax + g.ds) * (smax + g.ds));
+        double reach = 0.5 * (std::sqrt(2.0) * g.h + tmax * dtan_max);
+        double W = std::max(64.0 * g.ds, 1.5 * reach * lmax / dmin + 2.0 * g.ds);
+        double ke = 0.0;
+        for (int j = 0; j < nd; ++j) {
+            double sj = celld[4 * j], L = celld[4 * j + 1], dt = celld[4 * j + 2];
+            ke = std::max(ke, (L * L / g.dps) * dt / (2.0 * g.ds) * (1.0 + std::fabs(sj) * W / (L * L)));
+        }
+        geo->bw.kz = g.dps / (2.0 * g.ds);
+        geo->bw.ke = ke * 1.001 + 1e-3;
+    }
     if (cudaGetDevice(&geo->device) != cudaSuccess) { delete geo; return record_cuda_error(); }
 
-    std::vector<float> csf(2 * (size_t)nv);
-    for (size_t i = 0; i < csf.size(); ++i) csf[i] = (float)cs[i];
     struct Up { void **dst; const void *src; size_t bytes; };
     Up ups[] = {
         {(void **)&geo->d_view_cs, cs.data(), cs.size() * sizeof(double)},
-        {(void **)&geo->d_view_csf, csf.data(), csf.size() * sizeof(float)},
         {(void **)&geo->d_cell_d, celld.data(), celld.size() * sizeof(double)},
-        {(void **)&geo->d_cell_f, cellf.data(), cellf.size() * sizeof(float)},
-        {(void **)&geo->d_box, box.data(), box.size() * sizeof(float)},
+        {(void **)&geo->d_box, box.data(), box.size() * sizeof(BoxF)},
+        {(void **)&geo->d_cellf, cellf.data(), cellf.size() * sizeof(CellF)},
         {(void **)&geo->d_ray, rays.data(), rays.size() * sizeof(RayF)},
     };
     for (const Up &u : ups) {
@@ -190,7 +205,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
 void destroy_geometry(cnsf_geometry *geo)
 {
     if (!geo) return;
-    void *ptrs[] = {geo->d_view_cs, geo->d_view_csf, geo->d_cell_d, geo->d_cell_f, geo->d_box, geo->d_ray};
+    void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete geo;

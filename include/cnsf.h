@@ -119,6 +119,27 @@ CNSF_API int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void
  * Synchronous; *count is a host pointer. */
 CNSF_API int cnsf_count_nonzeros(const cnsf_geometry *geom, uint64_t *count, void *stream);
 
+/* Iterative reconstruction drivers.  Neither is in the paper (its experiments use
+ * ASD-POCS); they are the textbook algorithms, built on the projector pair above:
+ *   SIRT  x <- x + relax * C A^T (R (y - A x)),  R = 1/(A 1), C = 1/(A^T 1)
+ *         (0 where a sum is 0);
+ *   CGLS  conjugate gradients on A^T A x = A^T y (Hestenes-Stiefel form).
+ * y: device sinogram [n_views][n_det]; x: device image [n_y][n_x], holding x0 on entry
+ * and the result on exit (batch 1).  ws: device workspace of at least
+ * cnsf_solver_workspace_bytes bytes, 256-byte aligned, owned by the caller and used by
+ * one call at a time.  All iterations are launched asynchronously on `stream`; step
+ * lengths are computed on the device (FP64 dot products with a fixed reduction order, so
+ * results are the same whatever else runs on the GPU).  CGLS with resume != 0 continues
+ * from the state a previous call on the same ws, geometry and sinogram left (x must be
+ * that call's result); resume = 0 starts from x0. */
+CNSF_API size_t cnsf_solver_workspace_bytes(const cnsf_geometry *geom, int32_t dtype);
+
+CNSF_API int cnsf_sirt(const cnsf_geometry *geom, const void *sino, void *image, int32_t iters, double relax,
+                       int32_t dtype, void *ws, size_t ws_bytes, void *stream);
+
+CNSF_API int cnsf_cgls(const cnsf_geometry *geom, const void *sino, void *image, int32_t iters, int32_t resume,
+                       int32_t dtype, void *ws, size_t ws_bytes, void *stream);
+
 /* Size of the static device array used by cnsf_forward_project_noalloc: 16 MiB. */
 #define CNSF_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 

@@ -18,7 +18,7 @@ import torch
 from ._lib import CNSF_F32, CNSF_F64, CnsfError, GeometryDesc, check, lib  # noqa: F401
 
 __all__ = ["Geometry", "forward_project", "back_project", "count_nonzeros", "forward_project_noalloc",
-           "Projector", "CnsfError"]
+           "sirt", "cgls", "SolverWorkspace", "Projector", "project", "CnsfError"]
 
 
 def _dtype_code(t: torch.dtype) -> int:
@@ -166,6 +166,49 @@ def count_nonzeros(geom: Geometry, stream: Optional[torch.cuda.Stream] = None) -
                                       ctypes.c_void_p(_stream_ptr(stream, geom.device))),
               "cnsf_count_nonzeros")
     return int(n.value)
+
+
+class SolverWorkspace:
+    """Device workspace of the SIRT/CGLS drivers (one call at a time).  CGLS keeps its
+    state here between calls, which is what ``resume=True`` continues from."""
+
+    def __init__(self, geom: Geometry, dtype: torch.dtype = torch.float32):
+        self.geom = geom
+        self.dtype = dtype
+        n = int(lib.cnsf_solver_workspace_bytes(geom.handle, _dtype_code(dtype)))
+        self.buf = torch.empty(n + 256, dtype=torch.uint8, device=geom.device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = self.buf.data_ptr() + off
+        self.nbytes = n
+
+
+def _solver(name, fn, geom, sino, iters, x0, ws, stream, extra):
+    if sino.shape != geom.sino_shape:
+        raise ValueError(f"{name}: sinogram shape {tuple(sino.shape)}, expected {geom.sino_shape}")
+    sino = sino.contiguous()
+    code = _dtype_code(sino.dtype)
+    x = torch.zeros(geom.image_shape, dtype=sino.dtype, device=geom.device) if x0 is None else x0
+    if x.shape != geom.image_shape or x.dtype != sino.dtype or not x.is_contiguous() or x.device != sino.device:
+        raise ValueError(f"{name}: bad x0")
+    if ws is None:
+        ws = SolverWorkspace(geom, sino.dtype)
+    with torch.cuda.device(geom.device):
+        check(fn(geom.handle, ctypes.c_void_p(sino.data_ptr()), ctypes.c_void_p(x.data_ptr()), int(iters), *extra,
+                 code, ctypes.c_void_p(ws.ptr), ws.nbytes, ctypes.c_void_p(_stream_ptr(stream, geom.device))), name)
+    return x
+
+
+def sirt(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[torch.Tensor] = None, relax: float = 1.0,
+         ws: Optional[SolverWorkspace] = None, stream=None) -> torch.Tensor:
+    """SIRT iterations (device); x0 (updated in place) or zeros.  Returns the image."""
+    return _solver("cnsf_sirt", lib.cnsf_sirt, geom, sino, iters, x0, ws, stream, (ctypes.c_double(relax),))
+
+
+def cgls(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[torch.Tensor] = None,
+         ws: Optional[SolverWorkspace] = None, resume: bool = False, stream=None) -> torch.Tensor:
+    """CGLS iterations (device); x0 (updated in place) or zeros.  resume=True continues the
+    iteration whose state ``ws`` holds (x0 must be its result)."""
+    return _solver("cnsf_cgls", lib.cnsf_cgls, geom, sino, iters, x0, ws, stream, (1 if resume else 0,))
 
 
 class Projector(torch.autograd.Function):

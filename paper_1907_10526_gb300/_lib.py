@@ -36,6 +36,11 @@ _SIGNATURES = {
     "cnsf_back_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_count_nonzeros": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), _P]),
     "cnsf_forward_project_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "cnsf_solver_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
+    "cnsf_sirt": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P, ctypes.c_size_t,
+                                 _P]),
+    "cnsf_cgls": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t,
+                                 _P]),
     "cnsf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cnsf_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -109,6 +109,37 @@ int cnsf_count_nonzeros(const cnsf_geometry *geom, uint64_t *count, void *stream
     }
 }
 
+size_t cnsf_solver_workspace_bytes(const cnsf_geometry *geom, int32_t dtype)
+{
+    if (!geom || (dtype != CNSF_F32 && dtype != CNSF_F64)) return 0;
+    return solver_workspace_bytes(geom, dtype);
+}
+
+static int solver_call(const cnsf_geometry *geom, int algo, const void *sino, void *image, int32_t iters,
+                       double relax, int32_t resume, int32_t dtype, void *ws, size_t ws_bytes, void *stream)
+{
+    try {
+        int s = check_call(geom, sino, image, 1, dtype);
+        if (s != CNSF_OK) return s;
+        if (iters < 0 || !(relax > 0.0 && relax < 2.0)) return CNSF_ERR_INVALID;
+        return run_solver(geom, algo, sino, image, iters, relax, resume, dtype, ws, ws_bytes, (cudaStream_t)stream);
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
+int cnsf_sirt(const cnsf_geometry *geom, const void *sino, void *image, int32_t iters, double relax, int32_t dtype,
+              void *ws, size_t ws_bytes, void *stream)
+{
+    return solver_call(geom, 0, sino, image, iters, relax, 0, dtype, ws, ws_bytes, stream);
+}
+
+int cnsf_cgls(const cnsf_geometry *geom, const void *sino, void *image, int32_t iters, int32_t resume, int32_t dtype,
+              void *ws, size_t ws_bytes, void *stream)
+{
+    return solver_call(geom, 1, sino, image, iters, 1.0, resume, dtype, ws, ws_bytes, stream);
+}
+
 const char *cnsf_status_string(int status)
 {
     switch (status) {

@@ -27,4 +27,9 @@ size_t forward_scratch_bytes(const cnsf_geometry *geo, int batch, int dtype);
 int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,
                                 void *scratch, size_t scratch_bytes, cudaStream_t stream);
 
+// Iterative drivers (solver.cu): algo 0 = SIRT, 1 = CGLS.
+size_t solver_workspace_bytes(const cnsf_geometry *geo, int dtype);
+int run_solver(const cnsf_geometry *geo, int algo, const void *sino, void *image, int iters, double relax,
+               int resume, int dtype, void *ws, size_t ws_bytes, cudaStream_t stream);
+
 }  // namespace cnsf

@@ -1,0 +1,142 @@
+"""SIRT and CGLS on the GPU against the oracle's textbook drivers (GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from synth import FanGeometry, config_geometry, ellipse_phantom, phantom_for_config, poisson_counts
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = FanGeometry(nx=40, ny=36, n_views=30, n_det=70, d_po=150.0, d_ps=330.0, center_x=0.7, det_offset=0.3)
+
+
+@pytest.fixture(scope="module")
+def cnsf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1907_10526_gb300 as m
+    return m
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _small_problem():
+    img = ellipse_phantom(40, 5, 1.0, seed=4)[:36, :40]
+    y = oracle.forward(SMALL, img)
+    y = y + 0.01 * np.random.default_rng(1).standard_normal(y.shape)
+    return y
+
+
+def test_cgls_fp64_matches_oracle(cnsf):
+    """8 iterations: on this small, noisy problem the CGLS iterate itself amplifies a 1e-15
+    change of y to 2e-14 after 5 iterations, 4e-10 after 10 and 1e-4 after 15 (loss of
+    orthogonality), so later iterates of any two FP64 implementations differ that much."""
+    geom = cnsf.Geometry(SMALL)
+    y = _small_problem()
+    x = cnsf.cgls(geom, torch.tensor(y, device="cuda"), 8)
+    ref = oracle.cgls(SMALL, y, 8)
+    assert rel(x.cpu().numpy(), ref) < 1e-9
+
+
+def test_sirt_fp64_matches_oracle(cnsf):
+    geom = cnsf.Geometry(SMALL)
+    y = _small_problem()
+    x = cnsf.sirt(geom, torch.tensor(y, device="cuda"), 12)
+    ref = oracle.sirt(SMALL, y, 12)
+    assert rel(x.cpu().numpy(), ref) < 1e-10
+    x2 = cnsf.sirt(geom, torch.tensor(y, device="cuda"), 5, relax=1.5)
+    assert rel(x2.cpu().numpy(), oracle.sirt(SMALL, y, 5, relax=1.5)) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def downscale():
+    """256^2 downscale of the 2048^2 reconstruction workload: noisy sinogram (Poisson
+    counts, 1e5 photons) of the ellipse + texture phantom."""
+    g = config_geometry(30)
+    img = phantom_for_config(30)
+    clean = oracle.forward(g, img)
+    noisy, _ = poisson_counts(clean, seed=30)
+    return g, img, noisy
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _cgls_fp32_projections(G, y, iters):
+    """The FP32 driver's arithmetic on the oracle: CG state in FP64, every projector input
+    and output rounded to FP32, the sinogram given in FP32 (oracle.cgls otherwise)."""
+    y = _f32(y)
+    x = np.zeros((G.ny, G.nx))
+    r = y - _f32(oracle.forward(G, _f32(x)))
+    s = _f32(oracle.back(G, _f32(r)))
+    p = s.copy()
+    gam = float(np.sum(s * s))
+    for _ in range(iters):
+        q = _f32(oracle.forward(G, _f32(p)))
+        alpha = gam / float(np.sum(q * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        s = _f32(oracle.back(G, _f32(r)))
+        gnew = float(np.sum(s * s))
+        p = s + (gnew / gam) * p
+        gam = gnew
+    return x
+
+
+def test_cgls_fp32_downscale_matches_oracle(cnsf, downscale):
+    """FP32 projections, FP64 CG state, on the 256^2 downscale, 20 iterations.
+
+    This CGLS run is sensitive to 1e-7 perturbations of the operator (not of the data):
+    rounding the oracle's projector inputs or outputs to FP32 moves its 20th iterate by
+    7e-3 and its residual up by 3 %, while rounding only y moves x by 3e-7.  The FP32
+    driver is therefore compared with the oracle doing the driver's own roundings, and
+    the early iterates with the plain FP64 oracle."""
+    g, img, y = downscale
+    geom = cnsf.Geometry(g)
+    G = oracle.Geometry(g)
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    x5 = cnsf.cgls(geom, yt, 5).double().cpu().numpy()
+    assert rel(x5, oracle.cgls(G, y, 5)) < 1e-4
+    x = cnsf.cgls(geom, yt, 20).double().cpu().numpy()
+    ref = _cgls_fp32_projections(G, y, 20)
+    res = lambda v: np.linalg.norm(oracle.forward(G, v) - y) / np.linalg.norm(y)
+    print(f"cgls fp32: x vs rounded oracle {rel(x, ref):.3e}, residual {res(x):.6e} vs {res(ref):.6e}")
+    assert abs(res(x) - res(ref)) / res(ref) < 1e-4
+    assert rel(x, ref) < 1e-4          # measured 1.0e-5
+
+
+def test_sirt_fp32_downscale_matches_oracle(cnsf, downscale):
+    g, img, y = downscale
+    geom = cnsf.Geometry(g)
+    x = cnsf.sirt(geom, torch.tensor(y, dtype=torch.float32, device="cuda"), 20)
+    ref = oracle.sirt(g, y, 20)
+    assert rel(x.cpu().numpy(), ref) < 1e-5
+
+
+def test_cgls_resume_and_determinism(cnsf):
+    g = config_geometry(1)
+    geom = cnsf.Geometry(g)
+    y = torch.tensor(oracle.forward(g, phantom_for_config(1)), dtype=torch.float32, device="cuda")
+    straight = cnsf.cgls(geom, y, 10)
+    again = cnsf.cgls(geom, y, 10)
+    assert torch.equal(straight, again)
+    ws = cnsf.SolverWorkspace(geom, torch.float32)
+    x = cnsf.cgls(geom, y, 4, ws=ws)
+    x = cnsf.cgls(geom, y, 6, x0=x, ws=ws, resume=True)
+    assert torch.equal(x, straight)
+
+
+def test_cgls_reduces_error(cnsf, downscale):
+    g, img, y = downscale
+    geom = cnsf.Geometry(g)
+    yt = torch.tensor(y, dtype=torch.float32, device="cuda")
+    errs = []
+    for it in (1, 5, 20):
+        x = cnsf.cgls(geom, yt, it).cpu().numpy()
+        errs.append(np.linalg.norm(x - img) / np.linalg.norm(img))
+    assert errs[0] > errs[1] > errs[2]

@@ -23,6 +23,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -175,7 +177,6 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU leg
 def run_cnsf(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -295,6 +296,12 @@ def run_cnsf(args):
         "gpu_launches": 4 * args.steps,
         "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "bp_f32_kernel"],
     }
+    if rank == 0 and not args.no_extras:
+        line["serving"] = bench_serving(args, dev)
+        line["reconstruction_2048"] = bench_solvers(dev)
+        line["batch16_512x360"] = bench_batch16(dev)
+        line["p50_recon_latency_s"] = line["serving"]["continuous"].get("p50_s")
+        line["p99_recon_latency_s"] = line["serving"]["continuous"].get("p99_s")
     if rank == 0 and not args.no_cpu_baseline:
         r, dt, thr, desc = oracle_sample_rate(720)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
@@ -306,6 +313,88 @@ def run_cnsf(args):
     return 0
 
 
+# ---------------------------------------------------------------------------- extras
+def bench_serving(args, dev):
+    """Poisson arrivals (200 req/s) of CGLS reconstructions (20 iterations, FP32) with image
+    sizes in {256, 512, 768, 1024}^2, views in {180, 360, 720, 1440}, 1.75 n cells, admitted
+    by device footprint (64 GiB budget, 8 streams), against one-at-a-time service."""
+    import torch
+    from paper_1907_10526_gb300 import serve
+    from synth import poisson_trace
+    server = serve.ReconServer(64 << 30, max_active=8, device=dev.index or 0)
+    trace = poisson_trace(args.serve_requests, 200.0, seed=5)
+    sinos = serve.synthetic_sinograms(server, sorted({(t.n, t.n_views) for t in trace}))
+    reqs = serve.make_requests(trace, lambda n, v: sinos[(n, v)], iters=20)
+    server.run(reqs[:4], mode="continuous", keep_images=False)        # warm-up
+    out = {"trace": f"{len(reqs)} requests, Poisson arrivals at 200 req/s (seed 5)", "iters": 20}
+    out["sequential"] = serve.summarize(server.run(reqs, mode="sequential", keep_images=False))
+    out["continuous"] = serve.summarize(server.run(reqs, mode="continuous", keep_images=False))
+    out["continuous"]["max_concurrent"] = server.max_concurrent
+    cap = out["continuous"]["recons_per_s"]
+    if cap and cap == cap:
+        slow = poisson_trace(args.serve_requests, 0.7 * cap, seed=6)
+        reqs2 = serve.make_requests(slow, lambda n, v: sinos.get((n, v)) if (n, v) in sinos else
+                                    serve.synthetic_sinograms(server, [(n, v)])[(n, v)], iters=20)
+        out["continuous_at_0.7x_capacity"] = serve.summarize(server.run(reqs2, mode="continuous",
+                                                                         keep_images=False))
+        out["continuous_at_0.7x_capacity"]["rate_req_per_s"] = 0.7 * cap
+    return out
+
+
+def bench_solvers(dev, iters: int = 50):
+    """2048^2 FP32 ellipse + texture phantom, 1536 cells, 1440 views, D 2000/4000 mm, noisy
+    sinogram (Poisson, 1e5 photons): 50 iterations each of SIRT and CGLS, ms per iteration."""
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import config_geometry, phantom_for_config, poisson_counts
+    g = config_geometry(3)
+    geom = cnsf.Geometry(g)
+    img = phantom_for_config(3)
+    clean = cnsf.forward_project(geom, torch.tensor(img, dtype=torch.float32, device=dev))
+    noisy, _ = poisson_counts(clean.double().cpu().numpy(), seed=3)
+    y = torch.tensor(noisy, dtype=torch.float32, device=dev)
+    ws = cnsf.SolverWorkspace(geom, torch.float32)
+    out = {"workload": "2048^2, 1536 cells, 1440 views, 50 iterations, FP32 projections"}
+    for name, fn in (("sirt", lambda x: cnsf.sirt(geom, y, iters, x0=x, ws=ws)),
+                     ("cgls", lambda x: cnsf.cgls(geom, y, iters, x0=x, ws=ws))):
+        x = torch.zeros((g.ny, g.nx), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        fn(x)
+        t1.record()
+        torch.cuda.synchronize()
+        xe = x.double().cpu().numpy()
+        err = float(np.linalg.norm(xe - img) / np.linalg.norm(img))
+        out[name] = {"ms_per_iter": t0.elapsed_time(t1) / iters, "rel_error_to_phantom": err}
+    return out
+
+
+def bench_batch16(dev, steps: int = 5):
+    """16 FP32 512^2 images (seeds 400-415), 888 cells x 360 views: one batched forward and
+    one batched back projection, pixel*view updates/s."""
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import config_geometry, phantom_for_config
+    g = config_geometry(4)
+    geom = cnsf.Geometry(g)
+    x = torch.tensor(np.stack([phantom_for_config(4, b) for b in range(16)]), dtype=torch.float32, device=dev)
+    y = cnsf.forward_project(geom, x)
+    c = cnsf.back_project(geom, y)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        cnsf.forward_project(geom, x, out=y)
+        cnsf.back_project(geom, y, out=c)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    return {"ms_per_fp_bp": ms, "updates_per_s": 16 * g.nx * g.ny * g.n_views / (ms * 1e-3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,6 +402,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cnsf", choices=["cnsf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip serving / reconstruction / batch lines")
+    ap.add_argument("--serve-requests", type=int, default=120)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

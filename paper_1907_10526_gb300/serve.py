@@ -1,0 +1,230 @@
+"""Continuous-batching reconstruction server on one GPU.
+
+Requests (an n x n image, V views, a sinogram, a CGLS iteration count) arrive over time.
+The scheduler admits them in arrival order whenever a stream slot is free and their
+device footprint fits the HBM budget; every admitted request runs on its own CUDA stream
+(sinogram upload, CGLS iterations through the C library, image download), so the work of
+requests that arrive while others run overlaps on the device.  A finished request frees
+its slot and memory for the next one.  Results do not depend on the mix: the kernels use
+no atomics and the solver's reductions have a fixed order.
+
+Latency = completion on the device (CUDA event, same clock as the arrivals) minus arrival.
+``mode="sequential"`` serves the same trace one request at a time (the baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import statistics
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Tuple
+
+import torch
+
+from . import CNSF_F32, Geometry, SolverWorkspace, _lib, cgls
+
+
+@dataclass
+class ReconRequest:
+    rid: int
+    arrival_s: float          # seconds after the start of the run
+    n: int                    # image side (pixels)
+    n_views: int
+    sino: torch.Tensor        # [n_views][n_det] FP32, host (pinned) or device
+    iters: int = 20
+
+
+@dataclass
+class ReconResult:
+    rid: int
+    status: str               # "ok" or "rejected: ..."
+    image: Optional[torch.Tensor] = None   # host FP32 [n][n]
+    arrival_s: float = 0.0
+    admit_s: float = 0.0      # host time of admission
+    done_s: float = 0.0       # device completion time
+    latency_s: float = 0.0
+
+
+def serving_geometry_desc(n: int, n_views: int):
+    """The serving workload's geometry: 1 mm pixels and cells, n_det = round(1.75 n),
+    source distances 500*max(1, n/512) and twice that (source outside the image)."""
+    from types import SimpleNamespace
+    d_po = 500.0 * max(1.0, n / 512.0)
+    return SimpleNamespace(nx=n, ny=n, n_views=n_views, n_det=int(round(1.75 * n)), pixel=1.0, det_spacing=1.0,
+                           det_width=1.0, d_po=d_po, d_ps=2.0 * d_po, center_x=0.0, center_y=0.0,
+                           det_offset=0.0, angles=None)
+
+
+class ReconServer:
+    """Admission by device footprint, one stream per active request."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, device: int = 0):
+        self.device = torch.device("cuda", device)
+        self.budget = int(hbm_budget_bytes)
+        self.max_active = int(max_active)
+        self.geoms: Dict[Tuple[int, int], Geometry] = {}
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_active)]
+
+    # ------------------------------------------------------------------ set-up
+    def geometry(self, n: int, n_views: int) -> Geometry:
+        key = (n, n_views)
+        g = self.geoms.get(key)
+        if g is None:
+            with torch.cuda.device(self.device):
+                g = Geometry(serving_geometry_desc(n, n_views), device=self.device)
+            self.geoms[key] = g
+        return g
+
+    def footprint(self, n: int, n_views: int) -> int:
+        """Device bytes a request holds while active: sinogram, image, solver workspace
+        and the forward projector's padded image copies."""
+        g = self.geometry(n, n_views)
+        ws = int(_lib.lib.cnsf_solver_workspace_bytes(g.handle, CNSF_F32))
+        pad = 16
+        scratch = 2 * n * (n + 2 * pad) * 4
+        return g.n_views * g.n_det * 4 + n * n * 4 + ws + 256 + scratch
+
+    # ------------------------------------------------------------------ serving
+    def run(self, requests: List[ReconRequest], mode: str = "continuous", keep_images: bool = True,
+            poll_s: float = 2e-5) -> List[ReconResult]:
+        dev = self.device
+        reqs = sorted(requests, key=lambda r: (r.arrival_s, r.rid))
+        for r in reqs:
+            self.geometry(r.n, r.n_views)          # geometries are built before the clock starts
+        pending = deque(reqs)
+        queue: deque = deque()
+        active = {}                                # slot -> (request, done event, buffers, bytes)
+        free_slots = list(range(self.max_active if mode == "continuous" else 1))
+        used = 0
+        self.max_used = 0
+        self.max_concurrent = 0
+        results: Dict[int, ReconResult] = {}
+        torch.cuda.synchronize(dev)
+        start_ev = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.device(dev):
+            start_ev.record()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        while pending or queue or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival_s <= now:
+                queue.append(pending.popleft())
+            progressed = False
+            for slot in list(active):
+                r, ev, bufs, nbytes = active[slot]
+                if ev.query():
+                    res = results[r.rid]
+                    res.done_s = start_ev.elapsed_time(ev) * 1e-3
+                    res.latency_s = res.done_s - r.arrival_s
+                    res.image = bufs["out"] if keep_images else None
+                    used -= nbytes
+                    del active[slot]
+                    free_slots.append(slot)
+                    progressed = True
+            while queue and free_slots:
+                r = queue[0]
+                nbytes = self.footprint(r.n, r.n_views)
+                if nbytes > self.budget:
+                    queue.popleft()
+                    results[r.rid] = ReconResult(r.rid, "rejected: exceeds HBM budget", arrival_s=r.arrival_s)
+                    progressed = True
+                    continue
+                if used + nbytes > self.budget:
+                    break                          # wait for memory: keep arrival order
+                queue.popleft()
+                slot = free_slots.pop()
+                stream = self.streams[slot]
+                g = self.geometry(r.n, r.n_views)
+                with torch.cuda.device(dev), torch.cuda.stream(stream):
+                    sino = r.sino.to(dev, non_blocking=True)
+                    x = torch.zeros((r.n, r.n), dtype=torch.float32, device=dev)
+                    ws = SolverWorkspace(g, torch.float32)
+                    cgls(g, sino, r.iters, x0=x, ws=ws, stream=stream)
+                    out = torch.empty((r.n, r.n), dtype=torch.float32, pin_memory=True)
+                    out.copy_(x, non_blocking=True)
+                    ev = torch.cuda.Event(enable_timing=True)
+                    ev.record(stream)
+                results[r.rid] = ReconResult(r.rid, "ok", arrival_s=r.arrival_s, admit_s=time.perf_counter() - t0)
+                active[slot] = (r, ev, {"sino": sino, "x": x, "ws": ws, "out": out}, nbytes)
+                used += nbytes
+                self.max_used = max(self.max_used, used)
+                self.max_concurrent = max(self.max_concurrent, len(active))
+                progressed = True
+                if mode != "continuous":
+                    break
+            if not progressed:
+                if active:
+                    time.sleep(poll_s)
+                elif pending:
+                    time.sleep(max(0.0, min(pending[0].arrival_s - (time.perf_counter() - t0), 1e-3)))
+        torch.cuda.synchronize(dev)
+        return [results[r.rid] for r in reqs]
+
+
+def summarize(results: List[ReconResult]) -> dict:
+    ok = [r for r in results if r.status == "ok"]
+    lat = sorted(r.latency_s for r in ok)
+    if not lat:
+        return {"completed": 0, "rejected": len(results)}
+
+    def pct(q):
+        k = max(0, min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1))
+        return lat[k]
+    span = max(r.done_s for r in ok) - min(r.arrival_s for r in ok)
+    return {"completed": len(ok), "rejected": len(results) - len(ok), "p50_s": pct(0.50), "p99_s": pct(0.99),
+            "mean_s": statistics.fmean(lat), "recons_per_s": len(ok) / span if span > 0 else float("nan"),
+            "makespan_s": span}
+
+
+def make_requests(trace, sino_for, iters: int = 20) -> List[ReconRequest]:
+    """Requests of a synth.poisson_trace; ``sino_for(n, V)`` gives each shape's sinogram."""
+    return [ReconRequest(t.rid, t.arrival_s, t.n, t.n_views, sino_for(t.n, t.n_views), iters) for t in trace]
+
+
+def synthetic_sinograms(server: ReconServer, shapes, seed: int = 5):
+    """One noisy sinogram per (n, V): a random-ellipse phantom (10 ellipses, values in [0, 1])
+    projected by the forward kernel, with Poisson counts (1e5 photons)."""
+    import numpy as np
+
+    from synth import ellipse_phantom, poisson_counts
+    cache = {}
+    phantoms = {}
+    for (n, v) in shapes:
+        if n not in phantoms:
+            phantoms[n] = torch.tensor(ellipse_phantom(n, 10, 1.0, seed=seed + n), dtype=torch.float32,
+                                       device=server.device)
+        g = server.geometry(n, v)
+        from . import forward_project
+        clean = forward_project(g, phantoms[n]).double().cpu().numpy()
+        noisy, _ = poisson_counts(clean, seed=seed + 7 * n + v)
+        cache[(n, v)] = torch.tensor(noisy, dtype=torch.float32).pin_memory()
+    return cache
+
+
+def main():
+    import sys
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--requests", type=int, default=120)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--seed", type=int, default=5)
+    args = ap.parse_args()
+    from synth import poisson_trace
+    server = ReconServer(int(args.budget_gb * 2**30), max_active=args.max_active)
+    trace = poisson_trace(args.requests, args.rate, seed=args.seed)
+    sinos = synthetic_sinograms(server, sorted({(t.n, t.n_views) for t in trace}))
+    reqs = make_requests(trace, lambda n, v: sinos[(n, v)], args.iters)
+    out = {}
+    for mode in ("sequential", "continuous"):
+        out[mode] = summarize(server.run(reqs, mode=mode, keep_images=False))
+    json.dump(out, sys.stdout)
+    print()
+
+
+if __name__ == "__main__":
+    main()

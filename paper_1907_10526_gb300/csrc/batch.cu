@@ -1,0 +1,304 @@
+// batch.cu -- forward and back projection of a batch of images (FP32), each entry of A
+// evaluated once per chunk of up to 16 images.
+//
+// The per-image kernels evaluate the footprint (Eq. 18) once per (view, cell, pixel) and
+// image.  For a batch, the entry is the same for every image, so these kernels evaluate it
+// once and apply it to a chunk of NB = 4, 8 or 16 images.  Both directions read their
+// input from a batch-interleaved copy (the NB values of one pixel, or of one cell, are
+// contiguous), so the chunk costs NB/4 16-byte loads and NB FMAs per entry.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "cnsf_internal.cuh"
+#include "cnsf_runtime.h"
+#include "footprint.cuh"
+
+namespace cnsf {
+
+// ------------------------------------------------------------------ interleaved copies
+// out[row][c][q] (q < NB fastest) = img[b0 + q][row][c - pad], zero outside the image or
+// beyond the batch.  transposed: rows are image columns.
+__global__ void pad_interleave_kernel(const float *__restrict__ img, float *__restrict__ out, int nx, int ny,
+                                      int pad, int pitch, int b0, int nb_used, int NB, int transposed)
+{
+    const long long total = (long long)(transposed ? nx : ny) * pitch * NB;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t % NB);
+        const long long rc = t / NB;
+        const int c = (int)(rc % pitch), row = (int)(rc / pitch);
+        const int a = c - pad;   // index across the line
+        float v = 0.f;
+        if (q < nb_used) {
+            const int i = transposed ? row : a, r = transposed ? a : row;
+            if (a >= 0 && a < (transposed ? ny : nx))
+                v = img[((long long)(b0 + q) * ny + r) * nx + i];
+        }
+        out[t] = v;
+    }
+}
+
+// out[v][j][q] = y[b0 + q][v][j] (0 beyond the batch)
+__global__ void sino_interleave_kernel(const float *__restrict__ y, float *__restrict__ out, long long nvd, int b0,
+                                       int nb_used, int NB)
+{
+    const long long total = nvd * NB;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(t % NB);
+        const long long vj = t / NB;
+        out[t] = q < nb_used ? y[(long long)(b0 + q) * nvd + vj] : 0.f;
+    }
+}
+
+template <int NB4>
+struct Acc {
+    float4 v[NB4];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int k = 0; k < NB4; ++k) v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __device__ __forceinline__ void fma_from(float w, const float4 *__restrict__ p)
+    {
+#pragma unroll
+        for (int k = 0; k < NB4; ++k) {
+            const float4 c = __ldg(p + k);
+            v[k].x = fmaf(w, c.x, v[k].x);
+            v[k].y = fmaf(w, c.y, v[k].y);
+            v[k].z = fmaf(w, c.z, v[k].z);
+            v[k].w = fmaf(w, c.w, v[k].w);
+        }
+    }
+    __device__ __forceinline__ void add(const Acc &o)
+    {
+#pragma unroll
+        for (int k = 0; k < NB4; ++k) {
+            v[k].x += o.v[k].x; v[k].y += o.v[k].y; v[k].z += o.v[k].z; v[k].w += o.v[k].w;
+        }
+    }
+};
+
+// ------------------------------------------------------------------ forward
+template <int KC, int NB4>
+__device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__restrict__ base, int pitch4, float B,
+                                              float p, float qiC, float iC, float hC, Acc<NB4> &acc)
+{
+    long long A = R.A0;
+    float er = R.e0;
+    Acc<NB4> part;
+    part.zero();
+    for (int rr = 0; rr < R.nrows; ++rr) {
+        const int ilo = (int)(A >> 32) + (((unsigned)A) != 0u ? 1 : 0);
+        const unsigned nl = 0u - (unsigned)A;
+        const float u0 = (__uint_as_float(0x3f800000u | (nl >> 9)) - 1.0f) - R.hw;
+        const float4 *rp = base + (long long)ilo * NB4;
+#pragma unroll
+        for (int m = 0; m < KC; ++m) {
+            const float um = u0 + (float)m;
+            const float e = fmaf(R.kap, um, er);
+            const float d = window_diff(fabsf(B * um), e, p, qiC, iC, hC);
+            part.fma_from(d * rcp_approx(e), rp + m * NB4);
+        }
+        A += R.G;
+        er += R.de;
+        base += pitch4;
+        if ((rr & 15) == 15) {
+            acc.add(part);
+            part.zero();
+        }
+    }
+    acc.add(part);
+}
+
+template <int NB4>
+__global__ void __launch_bounds__(128) fp_batch_kernel(const RayF *__restrict__ rays, const BoxF *__restrict__ box,
+                                                       float h2q, const float4 *__restrict__ P,
+                                                       const float4 *__restrict__ Tt, int pitchP, int pitchT,
+                                                       int pad, int nr, float *__restrict__ sino, int b0,
+                                                       int nb_used)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nr) return;
+    const RayF R = rays[q];
+    Acc<NB4> acc;
+    acc.zero();
+    if (R.nrows > 0) {
+        const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
+        const float p = bx.x, qiC = bx.y, iC = bx.z, hC = bx.w;
+        const float B = 2.f * (p + hC);
+        const bool tr = (R.flags & 1) != 0;
+        const int pitch = tr ? pitchT : pitchP;
+        const float4 *base = (tr ? Tt : P) + ((long long)R.r0 * pitch + pad) * NB4;
+        const int p4 = pitch * NB4;
+        switch (R.kc) {
+            case 1: fp_batch_walk<1, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            case 2: fp_batch_walk<2, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            case 3: fp_batch_walk<3, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            case 4: fp_batch_walk<4, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            case 5: fp_batch_walk<5, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            case 6: fp_batch_walk<6, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            case 7: fp_batch_walk<7, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            default: fp_batch_walk<8, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        }
+        const float nrm = h2q / (p + hC);
+#pragma unroll
+        for (int k = 0; k < NB4; ++k) {
+            acc.v[k].x *= nrm; acc.v[k].y *= nrm; acc.v[k].z *= nrm; acc.v[k].w *= nrm;
+        }
+    }
+    const float *a = reinterpret_cast<const float *>(acc.v);
+#pragma unroll
+    for (int k = 0; k < 4 * NB4; ++k)
+        if (k < nb_used) sino[(long long)(b0 + k) * nr + q] = a[k];
+}
+
+// ------------------------------------------------------------------ back
+constexpr int BPB_T = 16;
+constexpr int BPB_CHUNK = 256;
+
+struct alignas(16) TileViewB {
+    float Dt, yt, a1, b1, rho, phi, hc, hs;
+};
+
+template <int NB4>
+__global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const double *__restrict__ view_cs,
+                                                       const float4 *__restrict__ box,
+                                                       const float4 *__restrict__ cell,
+                                                       const float4 *__restrict__ Y, float *__restrict__ img,
+                                                       float kz, float ke, float h2, float h2q, int b0,
+                                                       int nb_used)
+{
+    __shared__ TileViewB tv[BPB_CHUNK];
+    __shared__ int tj[BPB_CHUNK];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
+    const int it = blockIdx.x * BPB_T, rt = blockIdx.y * BPB_T;
+    const int i = it + tx, r = rt + ty;
+    const bool inside = i < g.nx && r < g.ny;
+    const float ctr = 0.5f * (BPB_T - 1);
+    const float di = (float)tx - ctr, dr = (float)ty - ctr;
+    Acc<NB4> acc;
+    acc.zero();
+    for (int v0 = 0; v0 < g.nv; v0 += BPB_CHUNK) {
+        const int nvc = min(BPB_CHUNK, g.nv - v0);
+        __syncthreads();
+        if (tid < nvc) {
+            double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
+            double Dt, yt, a1, b1, rho, phi;
+            int J;
+            tile_view_double(g, c, s, it + (double)ctr, rt + (double)ctr, &Dt, &yt, &a1, &b1, &rho, &phi, &J);
+            TileViewB T;
+            T.Dt = (float)Dt; T.yt = (float)yt; T.a1 = (float)a1; T.b1 = (float)b1;
+            T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)(g.h * c); T.hs = (float)(g.h * s);
+            tv[tid] = T;
+            tj[tid] = J;
+        }
+        __syncthreads();
+        if (!inside) continue;
+        Acc<NB4> part;
+        part.zero();
+        for (int vv = 0; vv < nvc; ++vv) {
+            const TileViewB T = tv[vv];
+            const int J = tj[vv];
+            const long long vrow = (long long)(v0 + vv) * g.nd;
+            const float Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
+            const float yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
+            const float rD = rcp_approx(Dn);
+            const float sig = fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);
+            const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
+            const float hwc = fmaf(kz * (fabsf(za) + fabsf(zb)) * rD * rD, fmaf(h2, rD, 1.02f), ke);
+            const int jlo = max((int)ceilf(sig - hwc), -J);
+            const int jhi = min((int)floorf(sig + hwc), g.nd - 1 - J);
+            float d = sig - (float)jlo;
+            for (int jl = jlo; jl <= jhi; ++jl) {
+                const long long q = vrow + J + jl;
+                const float4 A = __ldg(box + q);
+                const float4 C = __ldg(cell + J + jl);
+                const float x = fabsf(Dn * C.x * d);
+                const float e = fmaf(Dn, C.y, yp * C.z);
+                const float w = window_diff(x, e, A.x, A.y, A.z, A.w);
+                part.fma_from(w * rcp_approx((A.x + A.w) * e), Y + q * NB4);
+                d -= 1.f;
+            }
+            if ((vv & 15) == 15) {
+                acc.add(part);
+                part.zero();
+            }
+        }
+        acc.add(part);
+    }
+    if (inside) {
+        const float *a = reinterpret_cast<const float *>(acc.v);
+#pragma unroll
+        for (int k = 0; k < 4 * NB4; ++k)
+            if (k < nb_used) img[((long long)(b0 + k) * g.ny + r) * g.nx + i] = a[k] * h2q;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+static int chunk_nb4(int left) { return left > 8 ? 4 : (left > 4 ? 2 : 1); }
+
+int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t st)
+{
+    const GeomConsts &g = geo->gc;
+    const int nr = g.nv * g.nd, pad = geo->pad;
+    const int pitchP = g.nx + 2 * pad, pitchT = g.ny + 2 * pad;
+    const size_t per = (size_t)g.ny * pitchP + (size_t)g.nx * pitchT;   // pixels of both copies
+    float *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, per * 16 * sizeof(float), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    for (int b0 = 0; b0 < batch;) {
+        const int nb4 = chunk_nb4(batch - b0), NB = 4 * nb4, used = std::min(NB, batch - b0);
+        float *P = buf, *Tt = buf + (size_t)g.ny * pitchP * NB;
+        const long long nP = (long long)g.ny * pitchP * NB, nT = (long long)g.nx * pitchT * NB;
+        pad_interleave_kernel<<<(unsigned)std::min<long long>((nP + 255) / 256, 8192), 256, 0, st>>>(
+            img, P, g.nx, g.ny, pad, pitchP, b0, used, NB, 0);
+        pad_interleave_kernel<<<(unsigned)std::min<long long>((nT + 255) / 256, 8192), 256, 0, st>>>(
+            img, Tt, g.nx, g.ny, pad, pitchT, b0, used, NB, 1);
+        dim3 blk(128), grd((nr + 127) / 128);
+        const float h2q = (float)(0.25 * g.h * g.h);
+        const float4 *P4 = reinterpret_cast<const float4 *>(P), *T4 = reinterpret_cast<const float4 *>(Tt);
+        if (nb4 == 4)
+            fp_batch_kernel<4><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+        else if (nb4 == 2)
+            fp_batch_kernel<2><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+        else
+            fp_batch_kernel<1><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+        b0 += used;
+    }
+    cudaFreeAsync(buf, st);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
+int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t st)
+{
+    const GeomConsts &g = geo->gc;
+    const long long nvd = (long long)g.nv * g.nd;
+    float *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)nvd * 16 * sizeof(float), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    dim3 blk(BPB_T * BPB_T), grd((g.nx + BPB_T - 1) / BPB_T, (g.ny + BPB_T - 1) / BPB_T);
+    const float kz = (float)geo->bw.kz, ke = (float)geo->bw.ke, h2 = (float)(2.0 * g.h), h2q = (float)(0.25 * g.h * g.h);
+    const float4 *box = reinterpret_cast<const float4 *>(geo->d_box), *cell = reinterpret_cast<const float4 *>(geo->d_cellf);
+    for (int b0 = 0; b0 < batch;) {
+        const int nb4 = chunk_nb4(batch - b0), NB = 4 * nb4, used = std::min(NB, batch - b0);
+        sino_interleave_kernel<<<(unsigned)std::min<long long>((nvd * NB + 255) / 256, 8192), 256, 0, st>>>(
+            sino, buf, nvd, b0, used, NB);
+        const float4 *Y = reinterpret_cast<const float4 *>(buf);
+        if (nb4 == 4)
+            bp_batch_kernel<4><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used);
+        else if (nb4 == 2)
+            bp_batch_kernel<2><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used);
+        else
+            bp_batch_kernel<1><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used);
+        b0 += used;
+    }
+    cudaFreeAsync(buf, st);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
+}  // namespace cnsf

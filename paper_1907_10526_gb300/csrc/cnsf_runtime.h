@@ -27,6 +27,10 @@ size_t forward_scratch_bytes(const cnsf_geometry *geo, int batch, int dtype);
 int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,
                                 void *scratch, size_t scratch_bytes, cudaStream_t stream);
 
+// Batches of FP32 images (batch.cu): each entry evaluated once per chunk of <= 16 images.
+int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t stream);
+int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t stream);
+
 // Iterative drivers (solver.cu): algo 0 = SIRT, 1 = CGLS.
 size_t solver_workspace_bytes(const cnsf_geometry *geo, int dtype);
 int run_solver(const cnsf_geometry *geo, int algo, const void *sino, void *image, int iters, double relax,

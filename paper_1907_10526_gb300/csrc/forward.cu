@@ -313,6 +313,7 @@ static int make_padded(const cnsf_geometry *geo, const T *img, int batch, int on
 int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype, cudaStream_t st)
 {
     if (batch == 0) return CNSF_OK;
+    if (dtype == CNSF_F32 && batch >= 2) return launch_forward_batch(geo, (const float *)img, (float *)sino, batch, st);
     const GeomConsts &g = geo->gc;
     const int nr = g.nv * g.nd;
     int pitchP, pitchT;

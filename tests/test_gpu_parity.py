@@ -124,17 +124,26 @@ def test_adjoint_identity_on_gpu(cnsf, dt):
     assert abs(lhs - rhs) / float(Ac.norm() * y.double().norm()) < TOL[dt]
 
 
-def test_batch_matches_single(cnsf):
-    g = config_geometry(1)
+@pytest.mark.parametrize("nb", [2, 3, 5, 9, 16, 19])
+def test_batch_matches_single_and_oracle(cnsf, nb):
+    """Batches evaluate each entry once per chunk of up to 16 images (chunks of 4, 8, 16
+    and a ragged tail); every image equals its own projection within rounding and the
+    oracle within the FP32 bar."""
+    g = RAGGED
     geom = cnsf.Geometry(g)
-    imgs = np.stack([ellipse_phantom(64, 8, 1.0, seed=s) for s in (1, 2, 3)])
+    rng = np.random.default_rng(nb)
+    imgs = rng.uniform(0, 1, (nb, g.ny, g.nx))
+    sinos = rng.uniform(0, 1, (nb, g.n_views, g.n_det))
     xb = torch.tensor(imgs, dtype=torch.float32, device="cuda")
-    yb = cnsf.forward_project(geom, xb)
-    bb = cnsf.back_project(geom, yb)
-    for k in range(3):
-        yk = cnsf.forward_project(geom, xb[k])
-        assert torch.equal(yb[k], yk)
-        assert torch.equal(bb[k], cnsf.back_project(geom, yk))
+    yb = torch.tensor(sinos, dtype=torch.float32, device="cuda")
+    fb = cnsf.forward_project(geom, xb).double().cpu().numpy()
+    bb = cnsf.back_project(geom, yb).double().cpu().numpy()
+    for k in sorted({0, nb // 2, nb - 1}):
+        fk = cnsf.forward_project(geom, xb[k]).double().cpu().numpy()
+        bk = cnsf.back_project(geom, yb[k]).double().cpu().numpy()
+        assert rel(fb[k], fk) < 1e-6 and rel(bb[k], bk) < 1e-6
+        assert rel(fb[k], oracle.forward(g, imgs[k])) < 1e-5
+        assert rel(bb[k], oracle.back(g, sinos[k])) < 1e-5
 
 
 def test_empty_batch_and_errors(cnsf):

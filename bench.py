@@ -119,6 +119,22 @@ def _recorded_traffic(kernel: str):
     return ent.get("dram_bytes_per_launch")
 
 
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a per-rank number over all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_step_per_rank: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job units/s: every rank processes its own copy (weak scaling)."""
+    return units_per_step_per_rank * steps * world / (max_ms * 1e-3)
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -225,13 +241,9 @@ def run_cnsf(args):
         dist.barrier()
     t_fp = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     t_bp = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
-    total_ms = sum(t_fp) + sum(t_bp)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(t_fp) + sum(t_bp), world, dev)
     upd_per_step = g.nx * g.ny * g.n_views
-    value = upd_per_step * args.steps * world / (total_ms * 1e-3)
+    value = job_throughput(upd_per_step, args.steps, world, total_ms)
 
     # ---- end to end through the public API with host buffers (pinned), copies timed
     img_host = torch.tensor(img_np, dtype=torch.float32).pin_memory()
@@ -257,12 +269,8 @@ def run_cnsf(args):
         e2e_step()
         torch.cuda.synchronize()
         e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_total = sum(e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = upd_per_step * args.steps * world / (e2e_total * 1e-3)
+    e2e_total = reduce_max(sum(e_ms), world, dev)
+    e2e_value = job_throughput(upd_per_step, args.steps, world, e2e_total)
 
     # ---- roofline of the dominant kernel (FP32 issue throughput)
     props = torch.cuda.get_device_properties(dev)

@@ -1,0 +1,58 @@
+"""bench.py's multi-rank path on CPU with gloo, world size 2: the job time is the maximum
+over ranks, the value is the whole-job throughput, and the reference arm prints on rank 0
+only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local_ms = 100.0 + 50.0 * rank                 # rank 1 is the slow one
+    mx = bench.reduce_max(local_ms, world)
+    val = bench.job_throughput(1000.0, 10, world, mx)
+    out.put((rank, mx, val))
+    dist.destroy_process_group()
+
+
+def test_reduce_max_and_job_throughput_gloo():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, mx, val in res:
+        assert mx == 150.0                          # slowest rank
+        assert val == pytest.approx(1000.0 * 10 * 2 / 0.150)
+
+
+def test_reference_arm_silent_on_other_ranks():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, env=env, timeout=120)
+    assert p.returncode == 0
+    assert p.stdout.strip() == ""

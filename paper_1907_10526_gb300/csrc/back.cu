@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
                                                      const float4 *__restrict__ box,
                                                      const float4 *__restrict__ cell,
                                                      const float *__restrict__ sino, float *__restrict__ img,
-                                                     BpArgs a)
+                                                     BpArgs a, const int *__restrict__ order, int ntx)
 {
     __shared__ TileViewS<float> tv[BP_CHUNK];
     __shared__ int tj[BP_CHUNK];
@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
     // cells, so a warp's loads of the cell tables touch few cache lines.
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
-    const int it = blockIdx.x * BP_T, rt = blockIdx.y * BP_T;
+    const int tile = order[blockIdx.x];   // tiles with the most work first
+    const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const long long b = blockIdx.z;
     const int i = it + tx, r = rt + ty;
     const bool inside = i < g.nx && r < g.ny;
@@ -191,9 +192,10 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
     dim3 blk(BP_T, BP_T), grd((g.nx + BP_T - 1) / BP_T, (g.ny + BP_T - 1) / BP_T, batch);
     if (dtype == CNSF_F32) {
         BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(0.25 * g.h * g.h)};
-        bp_f32_kernel<<<dim3(grd.x, grd.y, grd.z), dim3(BP_T * BP_T), 0, st>>>(
+        bp_f32_kernel<<<dim3(grd.x * grd.y, 1, grd.z), dim3(BP_T * BP_T), 0, st>>>(
             g, geo->d_view_cs, reinterpret_cast<const float4 *>(geo->d_box),
-            reinterpret_cast<const float4 *>(geo->d_cellf), (const float *)sino, (float *)img, a);
+            reinterpret_cast<const float4 *>(geo->d_cellf), (const float *)sino, (float *)img, a, geo->d_bp_order,
+            (int)grd.x);
     } else {
         bp_f64_kernel<<<grd, blk, 0, st>>>(g, geo->d_view_cs, geo->d_cell_d, (const double *)sino, (double *)img,
                                            geo->bw.kz, geo->bw.ke);

@@ -113,13 +113,14 @@ __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__res
 }
 
 template <int NB4>
-__global__ void __launch_bounds__(128) fp_batch_kernel(const RayF *__restrict__ rays, const BoxF *__restrict__ box,
+__global__ void __launch_bounds__(128) fp_batch_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
+                                                       const BoxF *__restrict__ box,
                                                        float h2q, const float4 *__restrict__ P,
                                                        const float4 *__restrict__ Tt, int pitchP, int pitchT,
                                                        int pad, int nr, float *__restrict__ sino, int b0,
                                                        int nb_used)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
     if (q >= nr) return;
     const RayF R = rays[q];
     Acc<NB4> acc;
@@ -168,13 +169,14 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
                                                        const float4 *__restrict__ cell,
                                                        const float4 *__restrict__ Y, float *__restrict__ img,
                                                        float kz, float ke, float h2, float h2q, int b0,
-                                                       int nb_used)
+                                                       int nb_used, const int *__restrict__ order, int ntx)
 {
     __shared__ TileViewB tv[BPB_CHUNK];
     __shared__ int tj[BPB_CHUNK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
-    const int it = blockIdx.x * BPB_T, rt = blockIdx.y * BPB_T;
+    const int tile = order[blockIdx.x];   // heaviest tiles first
+    const int it = (tile % ntx) * BPB_T, rt = (tile / ntx) * BPB_T;
     const int i = it + tx, r = rt + ty;
     const bool inside = i < g.nx && r < g.ny;
     const float ctr = 0.5f * (BPB_T - 1);
@@ -261,11 +263,11 @@ int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino
         const float h2q = (float)(0.25 * g.h * g.h);
         const float4 *P4 = reinterpret_cast<const float4 *>(P), *T4 = reinterpret_cast<const float4 *>(Tt);
         if (nb4 == 4)
-            fp_batch_kernel<4><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+            fp_batch_kernel<4><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
         else if (nb4 == 2)
-            fp_batch_kernel<2><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+            fp_batch_kernel<2><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
         else
-            fp_batch_kernel<1><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+            fp_batch_kernel<1><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
         b0 += used;
     }
     cudaFreeAsync(buf, st);
@@ -280,7 +282,8 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
     float *buf = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)nvd * 16 * sizeof(float), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
-    dim3 blk(BPB_T * BPB_T), grd((g.nx + BPB_T - 1) / BPB_T, (g.ny + BPB_T - 1) / BPB_T);
+    const int ntx = (g.nx + BPB_T - 1) / BPB_T, nty = (g.ny + BPB_T - 1) / BPB_T;
+    dim3 blk(BPB_T * BPB_T), grd(ntx * nty);
     const float kz = (float)geo->bw.kz, ke = (float)geo->bw.ke, h2 = (float)(2.0 * g.h), h2q = (float)(0.25 * g.h * g.h);
     const float4 *box = reinterpret_cast<const float4 *>(geo->d_box), *cell = reinterpret_cast<const float4 *>(geo->d_cellf);
     for (int b0 = 0; b0 < batch;) {
@@ -289,11 +292,11 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
             sino, buf, nvd, b0, used, NB);
         const float4 *Y = reinterpret_cast<const float4 *>(buf);
         if (nb4 == 4)
-            bp_batch_kernel<4><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used);
+            bp_batch_kernel<4><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx);
         else if (nb4 == 2)
-            bp_batch_kernel<2><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used);
+            bp_batch_kernel<2><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx);
         else
-            bp_batch_kernel<1><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used);
+            bp_batch_kernel<1><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx);
         b0 += used;
     }
     cudaFreeAsync(buf, st);

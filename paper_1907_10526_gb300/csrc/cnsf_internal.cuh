@@ -211,5 +211,8 @@ struct cnsf_geometry {
     double *d_cell_d;         // [nd][4] s_j, L_j, dtan_j, 0 (FP64)
     cnsf::BoxF *d_box;        // [nv][nd]
     cnsf::CellF *d_cellf;     // [nd]
+    // launch orders, heaviest blocks first (so that the tail of the grid is short work)
+    int *d_fp_order;          // [ceil(nv*nd/128)] forward blocks of 128 rays
+    int *d_bp_order;          // [ceil(nx/16)*ceil(ny/16)] back-projection tiles
     cnsf::RayF *d_ray;        // [nv][nd]
 };

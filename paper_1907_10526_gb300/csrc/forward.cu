@@ -177,12 +177,14 @@ __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ b
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(128) fp_f32_kernel(const RayF *__restrict__ rays, const BoxF *__restrict__ box, float h2q,
+__global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
+                                                     const BoxF *__restrict__ box, float h2q,
                                                      const float *__restrict__ imgP, const float *__restrict__ imgT,
                                                      int pitchP, int pitchT, long long strideP, long long strideT,
                                                      int pad, int nr, float *__restrict__ sino)
 {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    // blocks of 128 rays in the geometry's launch order (longest walks first)
+    int q = order[blockIdx.x] * 128 + threadIdx.x;
     if (q >= nr) return;
     long long b = blockIdx.y;
     const RayF R = rays[q];
@@ -323,7 +325,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
         float *buf = nullptr;
         int s = make_padded<float>(geo, (const float *)img, batch, 0, st, &buf, &pitchP, &pitchT, &strideP, &strideT);
         if (s != CNSF_OK) return s;
-        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf,
+        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf,
                                                   buf + (size_t)batch * strideP, pitchP, pitchT, strideP, strideT,
                                                   geo->pad, nr, (float *)sino);
         cudaFreeAsync(buf, st);
@@ -366,7 +368,7 @@ int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void 
         float *P = (float *)scratch, *Tt = P + (size_t)batch * strideP;
         pad_rows_kernel<float><<<grdr, blk, 0, st>>>((const float *)img, P, g.nx, g.ny, pad, pitchP, 0);
         pad_transpose_kernel<float><<<grdt, blkt, 0, st>>>((const float *)img, Tt, g.nx, g.ny, pad, pitchT, 0);
-        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P, Tt, pitchP, pitchT,
+        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P, Tt, pitchP, pitchT,
                                                   strideP, strideT, pad, nr, (float *)sino);
     } else {
         double *P = (double *)scratch, *Tt = P + (size_t)batch * strideP;
@@ -393,7 +395,7 @@ int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t st)
     cudaError_t e = cudaMallocAsync((void **)&out, (size_t)nr * sizeof(float), st);
     if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
     dim3 blk(128), grd((nr + 127) / 128, 1);
-    fp_f32_kernel<true><<<grd, blk, 0, st>>>(geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + strideP, pitchP,
+    fp_f32_kernel<true><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + strideP, pitchP,
                                              pitchT, strideP, strideT, geo->pad, nr, out);
     std::vector<float> host(nr);
     e = cudaMemcpyAsync(host.data(), out, (size_t)nr * sizeof(float), cudaMemcpyDeviceToHost, st);

@@ -159,6 +159,33 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         }
     }
 
+    // Launch orders.  Forward: blocks of 128 consecutive rays by descending walk length
+    // (lines x candidates).  Back: 16 x 16 tiles by descending mean magnification of their
+    // centre over the views, 1/sqrt(D_po^2 - rho^2) for a tile at radius rho.
+    std::vector<int> fp_order((nr + 127) / 128), bp_order;
+    {
+        std::vector<std::pair<double, int>> w(fp_order.size());
+        for (size_t bi = 0; bi < fp_order.size(); ++bi) {
+            double s = 0.0;
+            for (size_t q = bi * 128; q < std::min(nr, bi * 128 + 128); ++q) s += (double)rays[q].nrows * rays[q].kc;
+            w[bi] = {-s, (int)bi};
+        }
+        std::stable_sort(w.begin(), w.end());
+        for (size_t bi = 0; bi < w.size(); ++bi) fp_order[bi] = w[bi].second;
+        const int tx = (g.nx + 15) / 16, ty = (g.ny + 15) / 16;
+        std::vector<std::pair<double, int>> t((size_t)tx * ty);
+        for (int b = 0; b < ty; ++b)
+            for (int a = 0; a < tx; ++a) {
+                double x = g.cx + (16.0 * a + 7.5 - 0.5 * (g.nx - 1)) * g.h;
+                double y = g.cy + (16.0 * b + 7.5 - 0.5 * (g.ny - 1)) * g.h;
+                double r2 = std::min(x * x + y * y, 0.99 * g.dpo * g.dpo);
+                t[(size_t)b * tx + a] = {-1.0 / std::sqrt(g.dpo * g.dpo - r2), b * tx + a};
+            }
+        std::stable_sort(t.begin(), t.end());
+        bp_order.resize(t.size());
+        for (size_t i = 0; i < t.size(); ++i) bp_order[i] = t[i].second;
+    }
+
     cnsf_geometry *geo = new (std::nothrow) cnsf_geometry();
     if (!geo) return CNSF_ERR_NOMEM;
     geo->gc = g;
@@ -188,6 +215,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         {(void **)&geo->d_box, box.data(), box.size() * sizeof(BoxF)},
         {(void **)&geo->d_cellf, cellf.data(), cellf.size() * sizeof(CellF)},
         {(void **)&geo->d_ray, rays.data(), rays.size() * sizeof(RayF)},
+        {(void **)&geo->d_fp_order, fp_order.data(), fp_order.size() * sizeof(int)},
+        {(void **)&geo->d_bp_order, bp_order.data(), bp_order.size() * sizeof(int)},
     };
     for (const Up &u : ups) {
         cudaError_t e = cudaMalloc(u.dst, u.bytes);
@@ -205,7 +234,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
 void destroy_geometry(cnsf_geometry *geo)
 {
     if (!geo) return;
-    void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray};
+    void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray,
+                    geo->d_fp_order, geo->d_bp_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete geo;

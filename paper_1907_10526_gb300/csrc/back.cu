@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
                                                      const float4 *__restrict__ box,
                                                      const float4 *__restrict__ cell,
                                                      const float *__restrict__ sino, float *__restrict__ img,
-                                                     BpArgs a, const int *__restrict__ order, int ntx)
+                                                     BpArgs a, const int *__restrict__ order, int ntx, int nsplit,
+                                                     float *__restrict__ partial)
 {
     __shared__ TileViewS<float> tv[BP_CHUNK];
     __shared__ int tj[BP_CHUNK];
@@ -78,15 +79,18 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
     const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
     const int tile = order[blockIdx.x];   // tiles with the most work first
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
+    // blockIdx.y: which part of the views this block gathers (the parts of a tile are summed
+    // afterwards in a fixed order, so the result does not depend on scheduling)
     const long long b = blockIdx.z;
+    const int vbeg = (int)((long long)g.nv * blockIdx.y / nsplit), vend = (int)((long long)g.nv * (blockIdx.y + 1) / nsplit);
     const int i = it + tx, r = rt + ty;
     const bool inside = i < g.nx && r < g.ny;
     const float *y = sino + b * (long long)g.nv * g.nd;
     const float ctr = 0.5f * (BP_T - 1);
     const float di = (float)tx - ctr, dr = (float)ty - ctr;
     float acc = 0.f;
-    for (int v0 = 0; v0 < g.nv; v0 += BP_CHUNK) {
-        const int nvc = min(BP_CHUNK, g.nv - v0);
+    for (int v0 = vbeg; v0 < vend; v0 += BP_CHUNK) {
+        const int nvc = min(BP_CHUNK, vend - v0);
         __syncthreads();
         if (tid < nvc) {
             double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
@@ -114,7 +118,22 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
             acc += part;
         }
     }
-    if (inside) img[(b * g.ny + r) * g.nx + i] = acc * a.h2q;
+    if (inside) {
+        if (nsplit == 1)
+            img[(b * g.ny + r) * g.nx + i] = acc * a.h2q;
+        else
+            partial[((blockIdx.y * (long long)gridDim.z + b) * g.ny + r) * g.nx + i] = acc * a.h2q;
+    }
+}
+
+// img = sum over the view parts, in part order
+__global__ void bp_sum_parts_kernel(const float *__restrict__ partial, float *__restrict__ img, long long n, int nsplit)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        float s = partial[t];
+        for (int k = 1; k < nsplit; ++k) s += partial[k * n + t];
+        img[t] = s;
+    }
 }
 
 // FP64: same tiling and window; every per-pair constant is recomputed in FP64 from the view
@@ -192,10 +211,29 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
     dim3 blk(BP_T, BP_T), grd((g.nx + BP_T - 1) / BP_T, (g.ny + BP_T - 1) / BP_T, batch);
     if (dtype == CNSF_F32) {
         BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(0.25 * g.h * g.h)};
-        bp_f32_kernel<<<dim3(grd.x * grd.y, 1, grd.z), dim3(BP_T * BP_T), 0, st>>>(
+        // Enough blocks for several waves: split each tile's views when the tiles alone give
+        // fewer than ~32 blocks per SM (partial images, then a fixed-order sum).
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long blocks = (long long)grd.x * grd.y * batch;
+        int nsplit = 1;
+        while (nsplit < 8 && blocks * nsplit < 32LL * std::max(sms, 1) && g.nv / (2 * nsplit) >= 32) nsplit *= 2;
+        float *partial = nullptr;
+        const long long nimg = (long long)batch * g.nx * g.ny;
+        if (nsplit > 1) {
+            cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nimg * sizeof(float), st);
+            if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+        }
+        bp_f32_kernel<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_T * BP_T), 0, st>>>(
             g, geo->d_view_cs, reinterpret_cast<const float4 *>(geo->d_box),
             reinterpret_cast<const float4 *>(geo->d_cellf), (const float *)sino, (float *)img, a, geo->d_bp_order,
-            (int)grd.x);
+            (int)grd.x, nsplit, partial);
+        if (nsplit > 1) {
+            bp_sum_parts_kernel<<<(unsigned)std::min<long long>((nimg + 255) / 256, 4096), 256, 0, st>>>(
+                partial, (float *)img, nimg, nsplit);
+            cudaFreeAsync(partial, st);
+        }
     } else {
         bp_f64_kernel<<<grd, blk, 0, st>>>(g, geo->d_view_cs, geo->d_cell_d, (const double *)sino, (double *)img,
                                            geo->bw.kz, geo->bw.ke);

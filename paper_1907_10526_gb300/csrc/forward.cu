@@ -10,6 +10,7 @@
 // adjacent pixels, and no bounds test is needed inside the walk.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "cnsf_internal.cuh"
@@ -181,13 +182,23 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
                                                      const BoxF *__restrict__ box, float h2q,
                                                      const float *__restrict__ imgP, const float *__restrict__ imgT,
                                                      int pitchP, int pitchT, long long strideP, long long strideT,
-                                                     int pad, int nr, float *__restrict__ sino)
+                                                     int pad, int nr, float *__restrict__ sino, int nsplit,
+                                                     float *__restrict__ partial)
 {
     // blocks of 128 rays in the geometry's launch order (longest walks first)
     int q = order[blockIdx.x] * 128 + threadIdx.x;
     if (q >= nr) return;
     long long b = blockIdx.y;
-    const RayF R = rays[q];
+    RayF R = rays[q];
+    // blockIdx.z: which part of the ray's lines this block walks (parts summed afterwards in
+    // a fixed order)
+    if (nsplit > 1) {
+        const int l0 = (int)((long long)R.nrows * blockIdx.z / nsplit), l1 = (int)((long long)R.nrows * (blockIdx.z + 1) / nsplit);
+        R.A0 += (long long)l0 * R.G;
+        R.e0 += (float)l0 * R.de;
+        R.r0 += l0;
+        R.nrows = l1 - l0;
+    }
     float acc = 0.f;
     if (R.nrows > 0) {
         const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
@@ -239,7 +250,20 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
         }
         if (!COUNT) acc *= h2q / (p + hC);   // h^2/(2B), B = 2(p + C/2)
     }
-    sino[b * nr + q] = acc;
+    if (nsplit > 1)
+        partial[((long long)blockIdx.z * gridDim.y + b) * nr + q] = acc;
+    else
+        sino[b * nr + q] = acc;
+}
+
+// sino = sum over the line parts, in part order
+__global__ void fp_sum_parts_kernel(const float *__restrict__ partial, float *__restrict__ sino, long long n, int nsplit)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        float s = partial[t];
+        for (int k = 1; k < nsplit; ++k) s += partial[k * n + t];
+        sino[t] = s;
+    }
 }
 
 // ------------------------------------------------------------------ FP64 walk
@@ -325,9 +349,26 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
         float *buf = nullptr;
         int s = make_padded<float>(geo, (const float *)img, batch, 0, st, &buf, &pitchP, &pitchT, &strideP, &strideT);
         if (s != CNSF_OK) return s;
-        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf,
-                                                  buf + (size_t)batch * strideP, pitchP, pitchT, strideP, strideT,
-                                                  geo->pad, nr, (float *)sino);
+        // several line parts per ray when the rays alone give fewer than ~64 blocks per SM
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int nsplit = 1;
+        while (nsplit < 4 && (long long)grd.x * nsplit < 64LL * std::max(sms, 1)) nsplit *= 2;
+        float *partial = nullptr;
+        const long long nout = (long long)nr * batch;
+        if (nsplit > 1) {
+            cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nout * sizeof(float), st);
+            if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
+        }
+        fp_f32_kernel<false><<<dim3(grd.x, grd.y, nsplit), blk, 0, st>>>(
+            geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + (size_t)batch * strideP,
+            pitchP, pitchT, strideP, strideT, geo->pad, nr, (float *)sino, nsplit, partial);
+        if (nsplit > 1) {
+            fp_sum_parts_kernel<<<(unsigned)std::min<long long>((nout + 255) / 256, 4096), 256, 0, st>>>(
+                partial, (float *)sino, nout, nsplit);
+            cudaFreeAsync(partial, st);
+        }
         cudaFreeAsync(buf, st);
     } else {
         double *buf = nullptr;
@@ -369,7 +410,7 @@ int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void 
         pad_rows_kernel<float><<<grdr, blk, 0, st>>>((const float *)img, P, g.nx, g.ny, pad, pitchP, 0);
         pad_transpose_kernel<float><<<grdt, blkt, 0, st>>>((const float *)img, Tt, g.nx, g.ny, pad, pitchT, 0);
         fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P, Tt, pitchP, pitchT,
-                                                  strideP, strideT, pad, nr, (float *)sino);
+                                                  strideP, strideT, pad, nr, (float *)sino, 1, nullptr);
     } else {
         double *P = (double *)scratch, *Tt = P + (size_t)batch * strideP;
         pad_rows_kernel<double><<<grdr, blk, 0, st>>>((const double *)img, P, g.nx, g.ny, pad, pitchP, 0);
@@ -396,7 +437,7 @@ int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t st)
     if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
     dim3 blk(128), grd((nr + 127) / 128, 1);
     fp_f32_kernel<true><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + strideP, pitchP,
-                                             pitchT, strideP, strideT, geo->pad, nr, out);
+                                             pitchT, strideP, strideT, geo->pad, nr, out, 1, nullptr);
     std::vector<float> host(nr);
     e = cudaMemcpyAsync(host.data(), out, (size_t)nr * sizeof(float), cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(buf, st);

@@ -10,6 +10,9 @@
 // (BpWindow), so few cells outside the support are visited.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
+
 #include "cnsf_internal.cuh"
 #include "cnsf_runtime.h"
 #include "footprint.cuh"
@@ -29,12 +32,15 @@ struct BpArgs {
     float h2q;          // h^2 / 4
 };
 
-// One view of the pixel's gather in FP32.  Per candidate cell it reads the trapezoid
-// constants of the (view, cell) pair, the cell's s' and tau' slopes and the sinogram value;
-// the normalisation h^2/(2B) = h^2/(4(p + C/2)) is folded into the division by tau'.
-__device__ __forceinline__ float bp_view_f32(const TileViewS<float> &T, int J, float di, float dr,
-                                             const BpArgs &a, int nd, const float *__restrict__ yrow,
-                                             const float4 *__restrict__ boxrow, const float4 *__restrict__ cell)
+// One view of the pixel's gather in FP32, two cells (2m, 2m + 1) per step with packed FP32x2
+// arithmetic on even-aligned pair tables.  Aligning the window to even cells adds at most
+// one cell at each end; those cells lie outside the window, which bounds the support with
+// margin, so their entries are exactly 0 (a padding cell past n_det has sinogram value 0).
+// The normalisation h^2/(2B) = h^2/(4(p + C/2)) is folded into the division by tau'.
+__device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, float di, float dr,
+                                              const BpArgs &a, int nd, const float2 *__restrict__ y2row,
+                                              const float4 *__restrict__ box2row, const float4 *__restrict__ cell2,
+                                              const float2 *__restrict__ cellc2)
 {
     const float Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));   // depth along u
     const float yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));    // coordinate along w
@@ -44,30 +50,36 @@ __device__ __forceinline__ float bp_view_f32(const TileViewS<float> &T, int J, f
     const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
     const float zs = fabsf(za) + fabsf(zb);
     const float hwc = fmaf(a.kz * zs * rD * rD, fmaf(a.h2, rD, 1.02f), a.ke);
-    const int jlo = max((int)ceilf(sig - hwc), -J);
-    const int jhi = min((int)floorf(sig + hwc), nd - 1 - J);
-    const float4 *bp = boxrow + J + jlo;
-    const float4 *cp = cell + J + jlo;
-    const float *yq = yrow + J + jlo;
-    float d = sig - (float)jlo;
-    float part = 0.f;
-    for (int jl = jlo; jl <= jhi; ++jl) {
-        const float4 A = __ldg(bp++);    // p, q/C, 1/C, C/2
-        const float4 C = __ldg(cp++);    // ds/L, D_ps dtan/(2L), s_j dtan/(2L)
-        const float yv = __ldg(yq++);
-        const float x = fabsf(Dn * C.x * d);          // |s'|
-        const float e = fmaf(Dn, C.y, yp * C.z);      // tau'/2 at the pixel depth
-        const float w = window_diff(x, e, A.x, A.y, A.z, A.w);
-        part = fmaf(yv * w, rcp_approx((A.x + A.w) * e), part);
-        d -= 1.f;
+    const int g0 = J + max((int)ceilf(sig - hwc), -J);               // first and last cell, global
+    const int g1 = J + min((int)floorf(sig + hwc), nd - 1 - J);
+    float2 acc = make_float2(0.f, 0.f);
+    const float2 Dn2 = make_float2(Dn, Dn), yp2 = make_float2(yp, yp);
+    const float2 ne1 = make_float2(-1.f, -1.f), m2 = make_float2(-2.f, -2.f);
+    const int m0 = g0 >> 1, m1 = g1 >> 1;
+    const float d0 = sig - (float)(2 * m0 - J);
+    float2 d = make_float2(d0, d0 - 1.f);
+    for (int m = m0; m <= m1; ++m) {
+        const float4 A0 = __ldg(box2row + 2 * m), A1 = __ldg(box2row + 2 * m + 1);   // p, q/C | 1/C, -C/2
+        const float4 C0 = __ldg(cell2 + m);                                          // g1 | c1
+        const float2 c2 = __ldg(cellc2 + m);
+        const float2 yv = __ldg(y2row + m);
+        const float2 xs = __fmul2_rn(__fmul2_rn(Dn2, make_float2(C0.x, C0.y)), d);
+        const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
+        const float2 e = __ffma2_rn(Dn2, make_float2(C0.z, C0.w), __fmul2_rn(yp2, c2));         // tau'/2
+        const float2 p = make_float2(A0.x, A0.y), nhC = make_float2(A1.z, A1.w);
+        const float2 w = window_diff2p(x, e, ne1, p, make_float2(A0.z, A0.w), make_float2(A1.x, A1.y), nhC);
+        const float2 den = __fmul2_rn(__ffma2_rn(nhC, ne1, p), e);                              // (p + C/2) e
+        acc = __ffma2_rn(yv, make_float2(w.x * rcp_approx(den.x), w.y * rcp_approx(den.y)), acc);
+        d = __fadd2_rn(d, m2);
     }
-    return part;
+    return acc;
 }
 
 __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double *__restrict__ view_cs,
-                                                     const float4 *__restrict__ box,
-                                                     const float4 *__restrict__ cell,
-                                                     const float *__restrict__ sino, float *__restrict__ img,
+                                                     const float4 *__restrict__ box2,
+                                                     const float4 *__restrict__ cell2,
+                                                     const float2 *__restrict__ cellc2,
+                                                     const float2 *__restrict__ y2, float *__restrict__ img,
                                                      BpArgs a, const int *__restrict__ order, int ntx, int nsplit,
                                                      float *__restrict__ partial)
 {
@@ -85,10 +97,11 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
     const int vbeg = (int)((long long)g.nv * blockIdx.y / nsplit), vend = (int)((long long)g.nv * (blockIdx.y + 1) / nsplit);
     const int i = it + tx, r = rt + ty;
     const bool inside = i < g.nx && r < g.ny;
-    const float *y = sino + b * (long long)g.nv * g.nd;
+    const int ndh = (g.nd + 1) >> 1;
+    const float2 *y = y2 + b * (long long)g.nv * ndh;
     const float ctr = 0.5f * (BP_T - 1);
     const float di = (float)tx - ctr, dr = (float)ty - ctr;
-    float acc = 0.f;
+    float2 acc = make_float2(0.f, 0.f);
     for (int v0 = vbeg; v0 < vend; v0 += BP_CHUNK) {
         const int nvc = min(BP_CHUNK, vend - v0);
         __syncthreads();
@@ -105,24 +118,25 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
         }
         __syncthreads();
         if (inside) {
-            float part = 0.f;
+            float2 part = make_float2(0.f, 0.f);
             for (int vv = 0; vv < nvc; ++vv) {
                 const int v = v0 + vv;
-                part += bp_view_f32(tv[vv], tj[vv], di, dr, a, g.nd, y + (long long)v * g.nd,
-                                    box + (long long)v * g.nd, cell);
+                part = __fadd2_rn(part, bp_view_f32(tv[vv], tj[vv], di, dr, a, g.nd, y + (long long)v * ndh,
+                                                    box2 + 2 * (long long)v * ndh, cell2, cellc2));
                 if ((vv & 15) == 15) {   // blocked summation over groups of 16 views
-                    acc += part;
-                    part = 0.f;
+                    acc = __fadd2_rn(acc, part);
+                    part = make_float2(0.f, 0.f);
                 }
             }
-            acc += part;
+            acc = __fadd2_rn(acc, part);
         }
     }
+    const float accs = acc.x + acc.y;
     if (inside) {
         if (nsplit == 1)
-            img[(b * g.ny + r) * g.nx + i] = acc * a.h2q;
+            img[(b * g.ny + r) * g.nx + i] = accs * a.h2q;
         else
-            partial[((blockIdx.y * (long long)gridDim.z + b) * g.ny + r) * g.nx + i] = acc * a.h2q;
+            partial[((blockIdx.y * (long long)gridDim.z + b) * g.ny + r) * g.nx + i] = accs * a.h2q;
     }
 }
 
@@ -203,6 +217,19 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
     if (inside) img[(b * g.ny + r) * g.nx + i] = acc;
 }
 
+// y2[b][v][m] = (y[b][v][2m], y[b][v][2m + 1]) with 0 for the padding cell of odd n_det.
+__global__ void sino_pairs_kernel(const float *__restrict__ y, float2 *__restrict__ y2, long long nrows, int nd)
+{
+    const int ndh = (nd + 1) >> 1;
+    const long long n = nrows * ndh;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const long long row = t / ndh;
+        const int j = 2 * (int)(t - row * ndh);
+        const float *yr = y + row * nd;
+        y2[t] = make_float2(yr[j], j + 1 < nd ? yr[j + 1] : 0.f);
+    }
+}
+
 int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch, int dtype, cudaStream_t st)
 {
     if (batch == 0) return CNSF_OK;
@@ -225,10 +252,27 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
             cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nimg * sizeof(float), st);
             if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
         }
+        // the sinogram read as cell pairs: directly when n_det is even and the pointer 8-byte
+        // aligned, otherwise through a padded copy
+        const bool direct = (g.nd % 2 == 0) && (((uintptr_t)sino & 7u) == 0);
+        const float2 *y2 = reinterpret_cast<const float2 *>(sino);
+        float2 *copy = nullptr;
+        if (!direct) {
+            const long long nrows = (long long)batch * g.nv, n = nrows * ((g.nd + 1) / 2);
+            cudaError_t e = cudaMallocAsync((void **)&copy, (size_t)n * sizeof(float2), st);
+            if (e != cudaSuccess) {
+                if (partial) cudaFreeAsync(partial, st);
+                return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+            }
+            sino_pairs_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(
+                (const float *)sino, copy, nrows, g.nd);
+            y2 = copy;
+        }
         bp_f32_kernel<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_T * BP_T), 0, st>>>(
-            g, geo->d_view_cs, reinterpret_cast<const float4 *>(geo->d_box),
-            reinterpret_cast<const float4 *>(geo->d_cellf), (const float *)sino, (float *)img, a, geo->d_bp_order,
+            g, geo->d_view_cs, reinterpret_cast<const float4 *>(geo->d_box2),
+            reinterpret_cast<const float4 *>(geo->d_cell2), geo->d_cellc2, y2, (float *)img, a, geo->d_bp_order,
             (int)grd.x, nsplit, partial);
+        if (copy) cudaFreeAsync(copy, st);
         if (nsplit > 1) {
             bp_sum_parts_kernel<<<(unsigned)std::min<long long>((nimg + 255) / 256, 4096), 256, 0, st>>>(
                 partial, (float *)img, nimg, nsplit);

@@ -67,4 +67,23 @@ __device__ __forceinline__ float2 window_diff2(float2 x, float2 e, float2 ne1, f
     return __ffma2_rn(cs, ne1, __fadd2_rn(t1, hC2));             // (t1 + C/2) - sgn(z0) h0
 }
 
+// Two entries with different trapezoid constants (cells j and j + 1), packed: p, qiC, iC
+// and nhC = -C/2 are pairs.  Same arithmetic as window_diff, lane by lane.
+__device__ __forceinline__ float2 window_diff2p(float2 x, float2 e, float2 ne1, float2 p, float2 qiC, float2 iC,
+                                                float2 nhC)
+{
+    const float2 z1 = __fadd2_rn(x, e);
+    const float2 z0 = __ffma2_rn(e, ne1, x);          // x - e
+    const float a0x = fabsf(z0.x), a0y = fabsf(z0.y);
+    const float2 m1 = make_float2(fminf(z1.x, p.x), fminf(z1.y, p.y));
+    const float2 m0 = make_float2(fminf(a0x, p.x), fminf(a0y, p.y));
+    const float2 v1 = make_float2(sat01(fmaf(-z1.x, iC.x, qiC.x)), sat01(fmaf(-z1.y, iC.y, qiC.y)));
+    const float2 v0 = make_float2(sat01(fmaf(-a0x, iC.x, qiC.x)), sat01(fmaf(-a0y, iC.y, qiC.y)));
+    const float2 t1 = __ffma2_rn(__fmul2_rn(nhC, v1), v1, m1);   // B H(z1) - C/2
+    const float2 t0 = __ffma2_rn(__fmul2_rn(nhC, v0), v0, m0);
+    const float2 h0 = __ffma2_rn(nhC, ne1, t0);                 // B H(|z0|)
+    const float2 cs = make_float2(copysignf(h0.x, z0.x), copysignf(h0.y, z0.y));
+    return __ffma2_rn(cs, ne1, __ffma2_rn(nhC, ne1, t1));       // (t1 + C/2) - sgn(z0) h0
+}
+
 }  // namespace cnsf

@@ -301,13 +301,15 @@ def run_cnsf(args):
                 "d2h_bytes_per_step": int(sino_host.numel() * 4 + back_host.numel() * 4)},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 4 * args.steps,
-        "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "bp_f32_kernel"],
+        "gpu_launches": 6 * args.steps,
+        "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "fp_sum_parts_kernel",
+                             "bp_f32_kernel", "bp_sum_parts_kernel"],
     }
     if rank == 0 and not args.no_extras:
         line["serving"] = bench_serving(args, dev)
         line["reconstruction_2048"] = bench_solvers(dev)
         line["batch16_512x360"] = bench_batch16(dev)
+        line["e4_ladder"] = bench_e4_ladder(dev)
         line["p50_recon_latency_s"] = line["serving"]["continuous"].get("p50_s")
         line["p99_recon_latency_s"] = line["serving"]["continuous"].get("p99_s")
     if rank == 0 and not args.no_cpu_baseline:
@@ -401,6 +403,38 @@ def bench_batch16(dev, steps: int = 5):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
     return {"ms_per_fp_bp": ms, "updates_per_s": 16 * g.nx * g.ny * g.n_views / (ms * 1e-3)}
+
+
+def bench_e4_ladder(dev, reps: int = 3):
+    """The paper's run-time ladder (Sec. IV-D): all-ones n x n images, n = 64 ... 2048 mm,
+    360 views, 205 ... 6499 cells of 1 mm, (D_po, D_so) = (100, 100) ... (3200, 3200) mm.
+    The paper reports only speed-ups over LTRI in a figure; these are absolute times."""
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import E4_LADDER, e4_geometry
+    out = []
+    for (n, n_det, d) in E4_LADDER:
+        g = e4_geometry(n)
+        geom = cnsf.Geometry(g)
+        x = torch.ones((n, n), dtype=torch.float32, device=dev)
+        y = cnsf.forward_project(geom, x)
+        c = cnsf.back_project(geom, y)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fp, bp = [], []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev[0].record()
+            cnsf.forward_project(geom, x, out=y)
+            ev[1].record()
+            cnsf.back_project(geom, y, out=c)
+            ev[2].record()
+            torch.cuda.synchronize()
+            fp.append(ev[0].elapsed_time(ev[1]))
+            bp.append(ev[1].elapsed_time(ev[2]))
+        out.append({"n": n, "n_det": n_det, "d_po_d_so_mm": d, "fp_ms": min(fp), "bp_ms": min(bp),
+                    "fp_per_view_ms": min(fp) / 360, "bp_per_view_ms": min(bp) / 360})
+        del geom
+    return out
 
 
 def main():

@@ -111,7 +111,9 @@ class Geometry:
         self.nx, self.ny = int(geom.nx), int(geom.ny)
         self.n_views, self.n_det = int(geom.n_views), int(geom.n_det)
         assert self.angles.shape == (self.n_views,)
-        self.parallel = bool(parallel)
+        # a workload description may name the parallel-beam kind itself
+        parallel = bool(parallel) or getattr(geom, "detector", "flat") == "parallel"
+        self.parallel = parallel
         self.c = _Geom(self.nx, self.ny, float(geom.pixel), float(geom.center_x),
                        float(geom.center_y), self.n_views,
                        self.angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),

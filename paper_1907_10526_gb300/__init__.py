@@ -15,7 +15,7 @@ from typing import Optional
 
 import torch
 
-from ._lib import CNSF_F32, CNSF_F64, CnsfError, GeometryDesc, check, lib  # noqa: F401
+from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, CnsfError, GeometryDesc, check, lib  # noqa: F401
 
 __all__ = ["Geometry", "forward_project", "back_project", "count_nonzeros", "forward_project_noalloc",
            "sirt", "cgls", "SolverWorkspace", "Projector", "project", "CnsfError"]
@@ -35,12 +35,12 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream], device) -> int:
 
 
 class Geometry:
-    """A fan-beam acquisition (Sec. II.A) with its device tables.
+    """A fan-beam (Sec. II.A) or parallel-beam (Theorem 1) acquisition with its device tables.
 
     Built from any object with the fields of ``synth.FanGeometry`` (nx, ny, n_views,
     n_det, pixel, det_spacing, det_width, d_po, d_ps, center_x, center_y, det_offset,
-    angles) or from the same names as keyword arguments.  The tables live on
-    ``device`` (default: the current CUDA device).
+    angles, and optionally detector = "flat" | "parallel") or from the same names as
+    keyword arguments.  The tables live on ``device`` (default: the current CUDA device).
     """
 
     def __init__(self, desc=None, device=None, **kw):
@@ -63,7 +63,7 @@ class Geometry:
                          self.n_views,
                          ctypes.cast(self._angles, ctypes.POINTER(ctypes.c_double)) if self._angles else None,
                          self.n_det, float(desc.det_spacing), float(desc.det_width), float(desc.det_offset),
-                         float(desc.d_po), float(desc.d_ps), 0)
+                         float(desc.d_po), float(desc.d_ps), CNSF_DETECTOR[getattr(desc, "detector", "flat")])
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(self._h)), "cnsf_geometry_create")

@@ -107,12 +107,12 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
         __syncthreads();
         if (tid < nvc) {
             double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
-            double Dt, yt, a1, b1, rho, phi;
+            double Dt, yt, a1, b1, rho, phi, hc, hs;
             int J;
-            tile_view_double(g, c, s, it + (double)ctr, rt + (double)ctr, &Dt, &yt, &a1, &b1, &rho, &phi, &J);
+            tile_view_double(g, c, s, it + (double)ctr, rt + (double)ctr, &Dt, &yt, &a1, &b1, &rho, &phi, &J, &hc, &hs);
             TileViewS<float> T;
             T.Dt = (float)Dt; T.yt = (float)yt; T.a1 = (float)a1; T.b1 = (float)b1;
-            T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)(g.h * c); T.hs = (float)(g.h * s);
+            T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)hc; T.hs = (float)hs;
             tv[tid] = T;
             tj[tid] = J;
         }
@@ -177,9 +177,8 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
             double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
             TileViewS<double> T;
             int J;
-            tile_view_double(g, c, s, it + ctr, rt + ctr, &T.Dt, &T.yt, &T.a1, &T.b1, &T.rho, &T.phi, &J);
-            T.hc = g.h * c;
-            T.hs = g.h * s;
+            tile_view_double(g, c, s, it + ctr, rt + ctr, &T.Dt, &T.yt, &T.a1, &T.b1, &T.rho, &T.phi, &J, &T.hc,
+                             &T.hs);
             tv[tid] = T;
             tj[tid] = J;
             tcs[tid][0] = c;
@@ -203,11 +202,12 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
             for (int jl = jlo; jl <= jhi; ++jl) {
                 const int j = J + jl;
                 const double sj = celld[4 * j], L = celld[4 * j + 1], dt = celld[4 * j + 2];
-                const double nxv = (sj * c - g.dps * s) / L, nyv = (sj * s + g.dps * c) / L;
+                // normal of the cell's ray: (s_j u + D_ps w)/L_j, or w for parallel rays (L_j = 1)
+                const double nxv = g.par ? -s : (sj * c - g.dps * s) / L, nyv = g.par ? c : (sj * s + g.dps * c) / L;
                 const double B = g.h * fmax(fabs(nxv), fabs(nyv)), C = g.h * fmin(fabs(nxv), fabs(nyv));
                 const BoxConsts<double> bc = make_box_consts<double>(B, C, g.h);
                 const double x = fabs(Dn * (g.ds / L) * (sig - jl));
-                const double e = (g.dps * Dn + sj * yp) / L * 0.5 * dt;
+                const double e = g.par ? 0.5 * g.tau : (g.dps * Dn + sj * yp) / L * 0.5 * dt;
                 const double w = window_diff(x, e, bc.p, bc.q * bc.iC, bc.iC, 0.5 * C);
                 part += yrow[j] * bc.nrm * (w / e);
             }

@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
         __syncthreads();
         if (tid < nvc) {
             double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
-            double Dt, yt, a1, b1, rho, phi;
+            double Dt, yt, a1, b1, rho, phi, hc, hs;
             int J;
-            tile_view_double(g, c, s, it + (double)ctr, rt + (double)ctr, &Dt, &yt, &a1, &b1, &rho, &phi, &J);
+            tile_view_double(g, c, s, it + (double)ctr, rt + (double)ctr, &Dt, &yt, &a1, &b1, &rho, &phi, &J, &hc, &hs);
             TileViewB T;
             T.Dt = (float)Dt; T.yt = (float)yt; T.a1 = (float)a1; T.b1 = (float)b1;
-            T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)(g.h * c); T.hs = (float)(g.h * s);
+            T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)hc; T.hs = (float)hs;
             tv[tid] = T;
             tj[tid] = J;
         }

@@ -33,6 +33,7 @@ struct GeomConsts {
     double dpo, dps;
     double rimg;      // distance from the rotation centre to the farthest image corner
     double s0;        // centre of cell 0
+    int par;          // 1: parallel beam (Theorem 1): rays along -u, s = x . w, tau' = tau
 };
 
 // Per-cell quantities that do not depend on the view.
@@ -66,15 +67,24 @@ struct RayParams {
     int na, nb;       // image extent across / along the walk
 };
 
+// Parallel beam: the ray of cell j is the line through s_j w along v = -u, its normal is w, and
+// the blur is tau at every depth (e = tau/2, de = kap = 0, dtan = 0).
 template <typename T>
 __host__ __device__ inline RayParams<T> make_ray_params(const GeomConsts &g, double c, double s, int j)
 {
     double sj = cell_centre(g, j);
-    double L = sqrt(g.dps * g.dps + sj * sj);
-    double vx = (-g.dps * c - sj * s) / L, vy = (-g.dps * s + sj * c) / L;
-    double nxv = (sj * c - g.dps * s) / L, nyv = (sj * s + g.dps * c) / L;
-    double px = g.dpo * c, py = g.dpo * s;
-    double dtan = cell_dtan(g, sj);
+    double vx, vy, nxv, nyv, px, py, dtan;
+    if (g.par) {
+        vx = -c; vy = -s; nxv = -s; nyv = c;
+        px = -sj * s; py = sj * c;
+        dtan = 0.0;
+    } else {
+        double L = sqrt(g.dps * g.dps + sj * sj);
+        vx = (-g.dps * c - sj * s) / L; vy = (-g.dps * s + sj * c) / L;
+        nxv = (sj * c - g.dps * s) / L; nyv = (sj * s + g.dps * c) / L;
+        px = g.dpo * c; py = g.dpo * s;
+        dtan = cell_dtan(g, sj);
+    }
     RayParams<T> R;
     int tr = fabs(vy) >= fabs(vx) ? 0 : 1;
     double va, vb, na_, nb_, pa, pb, ca, cb;
@@ -91,7 +101,7 @@ __host__ __device__ inline RayParams<T> make_ray_params(const GeomConsts &g, dou
     R.f0 = (T)(PA - PB * gg);
     R.g = (T)gg;
     // lambda(rb) = (rb - PB) h / vb
-    R.e0 = (T)((-PB * g.h / vb) * 0.5 * dtan);
+    R.e0 = (T)(g.par ? 0.5 * g.tau : (-PB * g.h / vb) * 0.5 * dtan);
     R.de = (T)((g.h / vb) * 0.5 * dtan);
     R.kap = (T)(va * g.h * 0.5 * dtan);
     R.B = (T)(g.h * fabs(na_));
@@ -138,19 +148,29 @@ struct TileView {
 };
 
 // (it, rt) is the reference point of the tile in pixel-index units (its centre, so that the
-// per-pixel offsets stay small).
+// per-pixel offsets stay small).  (hc, hs) = h (cos, sin) is the per-pixel step of the depth.
+// Parallel beam: the projection is affine, sigma = (y' - s_0)/ds; the depth is held at
+// D_n = 1 (hc = hs = 0) so that the same per-pixel arithmetic applies.
 __host__ __device__ inline void tile_view_double(const GeomConsts &g, double c, double s, double it, double rt,
                                                  double *Dt, double *yt, double *a1, double *b1,
-                                                 double *rho, double *phi, int *J)
+                                                 double *rho, double *phi, int *J, double *hc, double *hs)
 {
     double kx = g.cx + (it - 0.5 * (g.nx - 1)) * g.h;
     double ky = g.cy + (rt - 0.5 * (g.ny - 1)) * g.h;
     double xu = kx * c + ky * s, yw = -kx * s + ky * c;
-    double D = g.dpo - xu;
-    double aD = -g.h * c, bD = -g.h * s, ay = -g.h * s, by = g.h * c;
-    double Nt = (g.dps * yw - g.s0 * D) / g.ds;
-    double aN = (g.dps * ay - g.s0 * aD) / g.ds;
-    double bN = (g.dps * by - g.s0 * bD) / g.ds;
+    double ay = -g.h * s, by = g.h * c;
+    double D, aD, bD, Nt, aN, bN;
+    if (g.par) {
+        D = 1.0; aD = 0.0; bD = 0.0;
+        Nt = (yw - g.s0) / g.ds; aN = ay / g.ds; bN = by / g.ds;
+        *hc = 0.0; *hs = 0.0;
+    } else {
+        D = g.dpo - xu; aD = -g.h * c; bD = -g.h * s;
+        Nt = (g.dps * yw - g.s0 * D) / g.ds;
+        aN = (g.dps * ay - g.s0 * aD) / g.ds;
+        bN = (g.dps * by - g.s0 * bD) / g.ds;
+        *hc = g.h * c; *hs = g.h * s;
+    }
     double sig = Nt / D;
     double Jd = floor(sig);
     *Dt = D;

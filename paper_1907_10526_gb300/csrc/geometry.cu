@@ -31,13 +31,15 @@ static int validate(const cnsf_geometry_desc *d)
     if (d->n_x > (1 << 16) || d->n_y > (1 << 16) || d->n_det > (1 << 20) || d->n_views > (1 << 20))
         return CNSF_ERR_INVALID;
     if (!(d->pixel_mm > 0) || !(d->det_spacing_mm > 0) || !(d->det_width_mm > 0)) return CNSF_ERR_INVALID;
-    if (!(d->d_po_mm > 0) || !(d->d_ps_mm > d->d_po_mm)) return CNSF_ERR_INVALID;
     if (!std::isfinite(d->center_x_mm) || !std::isfinite(d->center_y_mm) || !std::isfinite(d->det_offset_mm))
         return CNSF_ERR_INVALID;
-    if (d->detector != CNSF_DETECTOR_FLAT) return CNSF_ERR_UNSUPPORTED;
-    double rx = std::fabs(d->center_x_mm) + 0.5 * d->n_x * d->pixel_mm;
-    double ry = std::fabs(d->center_y_mm) + 0.5 * d->n_y * d->pixel_mm;
-    if (std::hypot(rx, ry) + 2.0 * d->pixel_mm >= d->d_po_mm) return CNSF_ERR_INVALID;
+    if (d->detector != CNSF_DETECTOR_FLAT && d->detector != CNSF_DETECTOR_PARALLEL) return CNSF_ERR_UNSUPPORTED;
+    if (d->detector == CNSF_DETECTOR_FLAT) {   // parallel rays have no source: d_po, d_ps unused
+        if (!(d->d_po_mm > 0) || !(d->d_ps_mm > d->d_po_mm)) return CNSF_ERR_INVALID;
+        double rx = std::fabs(d->center_x_mm) + 0.5 * d->n_x * d->pixel_mm;
+        double ry = std::fabs(d->center_y_mm) + 0.5 * d->n_y * d->pixel_mm;
+        if (std::hypot(rx, ry) + 2.0 * d->pixel_mm >= d->d_po_mm) return CNSF_ERR_INVALID;
+    }
     if (d->angles_rad)
         for (int k = 0; k < d->n_views; ++k)
             if (!std::isfinite(d->angles_rad[k])) return CNSF_ERR_INVALID;
@@ -55,7 +57,9 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     g.nx = d->n_x; g.ny = d->n_y; g.nv = d->n_views; g.nd = d->n_det;
     g.h = d->pixel_mm; g.cx = d->center_x_mm; g.cy = d->center_y_mm;
     g.ds = d->det_spacing_mm; g.tau = d->det_width_mm; g.doff = d->det_offset_mm;
-    g.dpo = d->d_po_mm; g.dps = d->d_ps_mm;
+    g.par = d->detector == CNSF_DETECTOR_PARALLEL ? 1 : 0;
+    g.dpo = g.par ? 0.0 : d->d_po_mm;
+    g.dps = g.par ? 0.0 : d->d_ps_mm;
     g.rimg = std::hypot(std::fabs(g.cx) + 0.5 * g.nx * g.h, std::fabs(g.cy) + 0.5 * g.ny * g.h);
     g.s0 = cell_centre(g, 0);
 
@@ -70,7 +74,9 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     std::vector<double> celld(4 * (size_t)nd);
     double dtan_max = 0.0, smax = 0.0;
     for (int j = 0; j < nd; ++j) {
-        double sj = cell_centre(g, j), L = std::sqrt(g.dps * g.dps + sj * sj), dt = cell_dtan(g, sj);
+        // parallel rays: unit "length" and no perspective (the blur is tau at every depth)
+        double sj = cell_centre(g, j);
+        double L = g.par ? 1.0 : std::sqrt(g.dps * g.dps + sj * sj), dt = g.par ? 0.0 : cell_dtan(g, sj);
         celld[4 * j] = sj; celld[4 * j + 1] = L; celld[4 * j + 2] = dt; celld[4 * j + 3] = 0.0;
         dtan_max = std::max(dtan_max, dt);
         smax = std::max(smax, std::fabs(sj));
@@ -83,7 +89,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     for (int j = 0; j < nd; ++j) {
         const double sj = celld[4 * j], Lj = celld[4 * j + 1], dtj = celld[4 * j + 2];
         cellf[j].g1 = (float)(g.ds / Lj);
-        cellf[j].c1 = (float)(g.dps * dtj / (2.0 * Lj));
+        cellf[j].c1 = (float)(g.par ? 0.5 * g.tau : g.dps * dtj / (2.0 * Lj));
         cellf[j].c2 = (float)(sj * dtj / (2.0 * Lj));
         cellf[j].pad = 0.0f;
     }
@@ -101,7 +107,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
             V.qiC = (float)(bc.q * bc.iC);
             V.iC = (float)bc.iC;
             V.hC = (float)(0.5 * R.C);
-            double emax = tmax * 0.5 * R.dtan;
+            double emax = g.par ? 0.5 * g.tau : tmax * 0.5 * R.dtan;
             double hw = (0.5 * (R.B + R.C) + emax) / R.B + 1e-3;
             int kc = (int)std::floor(2.0 * hw) + 1;
             kc_max = std::max(kc_max, kc);
@@ -199,7 +205,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
                 double x = g.cx + (16.0 * a + 7.5 - 0.5 * (g.nx - 1)) * g.h;
                 double y = g.cy + (16.0 * b + 7.5 - 0.5 * (g.ny - 1)) * g.h;
                 double r2 = std::min(x * x + y * y, 0.99 * g.dpo * g.dpo);
-                t[(size_t)b * tx + a] = {-1.0 / std::sqrt(g.dpo * g.dpo - r2), b * tx + a};
+                // parallel rays: every tile has the same work per view
+                t[(size_t)b * tx + a] = {g.par ? 0.0 : -1.0 / std::sqrt(g.dpo * g.dpo - r2), b * tx + a};
             }
         std::stable_sort(t.begin(), t.end());
         bp_order.resize(t.size());
@@ -213,7 +220,11 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     geo->kc_max = kc_max;
     // Back-projector window: cells within kz*zs/D_n^2*(1.02 + 2h/D_n) + ke of the pixel's
     // projection.  W bounds |s_n - s_j| over the window (widest at the nearest pixel depth).
-    {
+    if (g.par) {
+        // s' = ds (sigma - j); the support of M_[B, C, tau] is |s'| < (B + C + tau)/2 and B + C <= sqrt(2) h
+        geo->bw.kz = 0.0;
+        geo->bw.ke = (std::sqrt(2.0) * g.h + g.tau) / (2.0 * g.ds) * 1.001 + 1e-3;
+    } else {
         double dmin = g.dpo - g.rimg;
         double lmax = std::sqrt(g.dps * g.dps + (smax + g.ds) * (smax + g.ds));
         double reach = 0.5 * (std::sqrt(2.0) * g.h + tmax * dtan_max);

@@ -43,6 +43,7 @@ class FanGeometry:
     center_y: float = 0.0
     det_offset: float = 0.0     # detector centre offset along s, mm
     angles: Optional[tuple] = None  # explicit view angles (rad); None -> 2*pi*k/V
+    detector: str = "flat"      # "flat" fan beam, or "parallel" beam (d_po, d_ps unused)
 
     def view_angles(self) -> np.ndarray:
         if self.angles is not None:
@@ -83,6 +84,19 @@ def config_geometry(cfg: int) -> FanGeometry:
     if cfg == 4:   # batch of 16 x 512^2, 888 cells x 360 views
         return FanGeometry(nx=512, ny=512, n_views=360, n_det=888)
     raise ValueError(f"unknown configuration {cfg}")
+
+
+# Run-time ladder of the paper's Sec. IV-D: all-ones images of n mm (1 mm pixels), 360 views
+# over 360 deg, tau = ds = 1 mm, the cell counts and (D_po, D_so) distances it lists.
+E4_LADDER = ((64, 205, 100.0), (128, 409, 200.0), (256, 815, 400.0), (512, 1627, 800.0),
+             (1024, 3250, 1600.0), (2048, 6499, 3200.0))
+
+
+def e4_geometry(n: int) -> FanGeometry:
+    for (m, n_det, d) in E4_LADDER:
+        if m == n:
+            return FanGeometry(nx=n, ny=n, n_views=360, n_det=n_det, d_po=d, d_ps=2.0 * d)
+    raise ValueError(f"no ladder rung of size {n}")
 
 
 def serving_geometry(n: int, n_views: int) -> FanGeometry:

@@ -38,7 +38,12 @@ def test_invalid_geometries_refused_without_gpu():
         GeometryDesc(8, 8, -1.0, 0, 0, 4, None, 8, 1, 1, 0, 30, 60, 0),     # negative pixel
         GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 0.0, 0, 30, 60, 0),    # zero cell width
     ]
+    bad.append(GeometryDesc(0, 4, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 0, 0, 2))   # parallel, no columns
     for d in bad:
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
+    from paper_1907_10526_gb300._lib import CNSF_ERR_UNSUPPORTED
+    for kind in (1, 3, -1):   # only flat fan beam (0) and parallel beam (2) are built
+        d = GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 30, 60, kind)
+        assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_UNSUPPORTED
     assert lib.cnsf_forward_project(None, None, None, 1, 0, None) == CNSF_ERR_INVALID
     assert lib.cnsf_status_string(0) == b"ok"

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import FanGeometry, config_geometry, ellipse_phantom, phantom_for_config
+from synth import FanGeometry, config_geometry, e4_geometry, ellipse_phantom, phantom_for_config
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -217,3 +217,15 @@ def test_config2_adjoint_fp32(cnsf, cfg2):
     lhs = float((y.double() * s.double()).sum())
     rhs = float((c.double() * cnsf.back_project(geom, s).double()).sum())
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_e4_ladder_smallest_rung(cnsf, dt):
+    """The paper's run-time workload (Sec. IV-D), 64 mm rung: all-ones image, 205 cells,
+    D_po = D_so = 100 mm, 360 views."""
+    g = e4_geometry(64)
+    geom = cnsf.Geometry(g)
+    img = np.ones((64, 64))
+    y_ref = oracle.forward(g, img)
+    assert rel(_fwd(cnsf, geom, img, dt), y_ref) < TOL[dt]
+    assert rel(_bwd(cnsf, geom, y_ref, dt), oracle.back(g, y_ref)) < TOL[dt]

@@ -20,6 +20,10 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                       unity (parallel), uniform-disk convergence, orientation
                       fixtures under tests/golden/.
 * ``ref_entry``       pinned: midpoint-rule supersampling, self-convergence.
+* arc detector        (``detector="arc"``) pinned: chords and Eq. (17) edge cuts built
+                      from explicit arc coordinates, Ref self-convergence, dense
+                      brute force of both enumerations, error vs distance, mirror
+                      symmetry (tests/test_oracle_arc.py).
 * ``sirt``/``cgls``   pinned: dense least-squares solution, monotone residuals.
 """
 from __future__ import annotations
@@ -46,7 +50,7 @@ class _Geom(ctypes.Structure):
         ("nviews", ctypes.c_int), ("angles", ctypes.POINTER(ctypes.c_double)),
         ("ndet", ctypes.c_int), ("ds", ctypes.c_double), ("tau", ctypes.c_double),
         ("det_off", ctypes.c_double), ("dpo", ctypes.c_double), ("dps", ctypes.c_double),
-        ("parallel", ctypes.c_int),
+        ("parallel", ctypes.c_int), ("arc", ctypes.c_int),
     ]
 
 
@@ -112,14 +116,18 @@ class Geometry:
         self.n_views, self.n_det = int(geom.n_views), int(geom.n_det)
         assert self.angles.shape == (self.n_views,)
         # a workload description may name the parallel-beam kind itself
-        parallel = bool(parallel) or getattr(geom, "detector", "flat") == "parallel"
+        kind = getattr(geom, "detector", "flat")
+        if kind not in ("flat", "parallel", "arc"):
+            raise ValueError(f"unknown detector kind {kind!r}")
+        parallel = bool(parallel) or kind == "parallel"
         self.parallel = parallel
+        self.arc = kind == "arc" and not parallel
         self.c = _Geom(self.nx, self.ny, float(geom.pixel), float(geom.center_x),
                        float(geom.center_y), self.n_views,
                        self.angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        self.n_det, float(geom.det_spacing), float(geom.det_width),
                        float(geom.det_offset), float(geom.d_po), float(geom.d_ps),
-                       1 if parallel else 0)
+                       1 if parallel else 0, 1 if self.arc else 0)
 
     @property
     def ptr(self):

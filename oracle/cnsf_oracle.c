@@ -36,6 +36,14 @@
  *
  * Parallel-beam mode (geometry flag `parallel`): every ray of a view runs along
  * -u, the detector coordinate is s = x . w and tau' = tau (Theorem 1, exact).
+ *
+ * Arc-detector mode (geometry flag `arc`, the equiangular fan of Sec. I): the
+ * cells lie on the circle of radius D_ps about the source; the detector
+ * coordinate s is the arc length from the point p - D_ps u, so the ray of
+ * coordinate s leaves the source at the angle s/D_ps from -u (towards w).  The
+ * entry follows the same steps as the flat case: the central ray through the
+ * cell centre, the two cell edges perspective-divided in its frame (Eq. 17),
+ * and Ref is the bin average over s of the exact chords.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,6 +66,7 @@ typedef struct {
     double dpo;          /* source to rotation centre (mm)                       */
     double dps;          /* source to detector line (mm)                         */
     int parallel;        /* 1: parallel-beam rays (Theorem 1)                    */
+    int arc;             /* 1: cells on the arc of radius D_ps about the source  */
 } og_geom;
 
 /* ------------------------------------------------------------------ frames */
@@ -94,6 +103,20 @@ static void og_pixel_centre(const og_geom *g, int i, int r, double *kx, double *
     *ky = g->cy + (r - 0.5 * (g->ny - 1)) * g->h;
 }
 
+/* The point of the detector at coordinate s (fan beam): on the flat line d + s w,
+ * or on the arc p + D_ps (-cos(s/D_ps) u + sin(s/D_ps) w). */
+static void og_detector_point(const og_geom *g, const og_view *w, double s, double *qx, double *qy)
+{
+    if (g->arc) {
+        double gam = s / g->dps, cg = cos(gam), sg = sin(gam);
+        *qx = w->px + g->dps * (-cg * w->ux + sg * w->wx);
+        *qy = w->py + g->dps * (-cg * w->uy + sg * w->wy);
+    } else {
+        *qx = w->dx + s * w->wx;
+        *qy = w->dy + s * w->wy;
+    }
+}
+
 /* A ray of the view for detector coordinate s: a point o on it, unit direction
  * v, unit normal n (the basis of v(s)perp), and whether it is a half-line from
  * the source (fan) or a full line (parallel). */
@@ -112,7 +135,8 @@ static og_ray og_make_ray(const og_geom *g, const og_view *w, double s)
         r.vy = -w->uy;
         r.halfline = 0;
     } else {
-        double qx = w->dx + s * w->wx, qy = w->dy + s * w->wy;  /* point on detector */
+        double qx, qy;                                          /* point on detector */
+        og_detector_point(g, w, s, &qx, &qy);
         double ex = qx - w->px, ey = qy - w->py;
         double len = sqrt(ex * ex + ey * ey);
         r.ox = w->px;
@@ -198,8 +222,10 @@ static double og_tau_prime_at(const og_geom *g, const og_view *w, const og_ray *
     if (g->parallel) return g->tau;
     double ratio[2];
     for (int e = 0; e < 2; ++e) {
-        double se = sj + (e ? 0.5 : -0.5) * g->tau;
-        double qx = w->dx + se * w->wx - w->px, qy = w->dy + se * w->wy - w->py;
+        double se = sj + (e ? 0.5 : -0.5) * g->tau, qx, qy;
+        og_detector_point(g, w, se, &qx, &qy);
+        qx -= w->px;
+        qy -= w->py;
         double x1 = ray->nx * qx + ray->ny * qy;   /* coordinate on v(s)perp */
         double x2 = ray->vx * qx + ray->vy * qy;   /* coordinate along v(s)  */
         ratio[e] = x1 / x2;                        /* perspective division   */
@@ -275,6 +301,7 @@ static double og_project_point(const og_geom *g, const og_view *w, double x, dou
     double xw = x * w->wx + y * w->wy;
     if (g->parallel) return xw;
     double xu = x * w->ux + y * w->uy;
+    if (g->arc) return g->dps * atan2(xw, g->dpo - xu);
     return g->dps * xw / (g->dpo - xu);
 }
 
@@ -369,6 +396,7 @@ static double og_tau_prime_bound(const og_geom *g)
     if (g->parallel) return g->tau;
     double rx = fabs(g->cx) + 0.5 * g->nx * g->h, ry = fabs(g->cy) + 0.5 * g->ny * g->h;
     double tmax = g->dpo + sqrt(rx * rx + ry * ry);
+    if (g->arc) return tmax * 2.0 * tan(0.5 * g->tau / g->dps);   /* edges at +-tau/(2 D_ps) rad */
     double smax = fabs(g->det_off) + 0.5 * g->ndet * g->ds + g->tau;
     /* the bin subtends at most tau*D_ps/(D_ps^2 + s^2 - s*tau) per unit depth */
     double denom = g->dps * g->dps - smax * g->tau;
@@ -497,7 +525,9 @@ static double og_pixel_sum(const og_geom *g, const double *y, int i, int r)
         og_view w = og_make_view(g, k);
         double sn = og_project_point(g, &w, kx, ky);
         double wdet = reach;
-        if (!g->parallel) wdet = reach * lmax / (g->dpo - (kx * w.ux + ky * w.uy));
+        double depth = g->dpo - (kx * w.ux + ky * w.uy);
+        if (g->arc) wdet = g->dps * asin(fmin(1.0, reach / depth));
+        else if (!g->parallel) wdet = reach * lmax / depth;
         double s0 = og_cell_centre(g, 0);
         int jlo = (int)ceil((sn - wdet - s0) / g->ds);
         int jhi = (int)floor((sn + wdet - s0) / g->ds);

@@ -61,11 +61,15 @@ typedef enum {
 typedef enum { CNSF_F32 = 0, CNSF_F64 = 1 } cnsf_dtype;
 
 /* Acquisition kind.  FLAT: fan beam from a point source onto a flat detector line (Sec. II.A).
+ * ARC: fan beam onto the arc of radius d_ps about the source (the equiangular fan of Sec. I);
+ * the cell coordinate s is the arc length from the point p - d_ps u, so cell j's central ray
+ * leaves the source at the angle s_j / d_ps from -u; det_spacing and det_width are arc
+ * lengths; every cell must lie within 80 degrees of -u.
  * PARALLEL: parallel beam, the limit D_po -> infinity (Sec. III, Theorem 1): every ray of a
  * view runs along -u, the detector line passes through the rotation centre, the detector
  * coordinate of a point x is s = x . w, and the blur is tau at every depth, so the entries of
  * Eq. (18) are the exact bin averages; d_po_mm and d_ps_mm are ignored. */
-typedef enum { CNSF_DETECTOR_FLAT = 0, CNSF_DETECTOR_PARALLEL = 2 } cnsf_detector;
+typedef enum { CNSF_DETECTOR_FLAT = 0, CNSF_DETECTOR_ARC = 1, CNSF_DETECTOR_PARALLEL = 2 } cnsf_detector;
 
 typedef struct cnsf_geometry cnsf_geometry; /* opaque, immutable after creation */
 
@@ -82,17 +86,18 @@ typedef struct {
     double det_spacing_mm;     /* Delta_s, pitch of the cell centres (> 0)           */
     double det_width_mm;       /* tau, cell width (> 0)                              */
     double det_offset_mm;      /* shift of the detector centre along w               */
-    double d_po_mm;            /* source to rotation centre (D_po); FLAT only         */
-    double d_ps_mm;            /* source to detector line (D_ps > D_po); FLAT only    */
-    int32_t detector;          /* cnsf_detector: FLAT or PARALLEL                    */
+    double d_po_mm;            /* source to rotation centre (D_po); fan beams only    */
+    double d_ps_mm;            /* source to detector (D_ps > D_po); fan beams only    */
+    int32_t detector;          /* cnsf_detector: FLAT, ARC or PARALLEL               */
 } cnsf_geometry_desc;
 
 /* Build a geometry and its device tables on the current device (Sec. II.A and
  * Eq. 17: per-view rotations, per-cell effective-blur slopes, per-ray walk
  * tables).  Synchronous.  Rejects (CNSF_ERR_INVALID): non-positive sizes or
- * lengths and, for FLAT, d_ps <= d_po and images that reach within two pixels of
- * the source circle (the footprint model needs every pixel in front of the source);
- * CNSF_ERR_UNSUPPORTED for a detector kind other than FLAT and PARALLEL.
+ * lengths and, for the fan beams, d_ps <= d_po and images that reach within two
+ * pixels of the source circle (the footprint model needs every pixel in front of the
+ * source), and arcs that reach 80 degrees from -u; CNSF_ERR_UNSUPPORTED for an unknown
+ * detector kind.
  * On success *out owns device memory until cnsf_geometry_destroy. */
 CNSF_API int cnsf_geometry_create(const cnsf_geometry_desc *desc, cnsf_geometry **out);
 

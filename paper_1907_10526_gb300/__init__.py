@@ -35,11 +35,12 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream], device) -> int:
 
 
 class Geometry:
-    """A fan-beam (Sec. II.A) or parallel-beam (Theorem 1) acquisition with its device tables.
+    """A fan-beam (Sec. II.A; flat or arc detector) or parallel-beam (Theorem 1) acquisition
+    with its device tables.
 
     Built from any object with the fields of ``synth.FanGeometry`` (nx, ny, n_views,
     n_det, pixel, det_spacing, det_width, d_po, d_ps, center_x, center_y, det_offset,
-    angles, and optionally detector = "flat" | "parallel") or from the same names as
+    angles, and optionally detector = "flat" | "arc" | "parallel") or from the same names as
     keyword arguments.  The tables live on ``device`` (default: the current CUDA device).
     """
 

@@ -26,7 +26,7 @@ class GeometryDesc(ctypes.Structure):
 
 CNSF_OK, CNSF_ERR_INVALID, CNSF_ERR_CUDA, CNSF_ERR_NOMEM, CNSF_ERR_UNSUPPORTED, CNSF_ERR_INTERNAL = range(6)
 CNSF_F32, CNSF_F64 = 0, 1
-CNSF_DETECTOR = {"flat": 0, "parallel": 2}
+CNSF_DETECTOR = {"flat": 0, "arc": 1, "parallel": 2}
 
 _P = ctypes.c_void_p
 _SIGNATURES = {

@@ -30,13 +30,33 @@ struct alignas(16) TileViewS {
 struct BpArgs {
     float kz, ke, h2;   // window constants; h2 = 2h
     float h2q;          // h^2 / 4
+    float kscale;       // arc detector: cells per radian, D_ps / ds
+    float dg;           // arc detector: radians per cell, ds / D_ps
+    float nk6;          // arc detector: -dg^2 / 6 (sine series)
 };
+
+// Cell coordinate (minus J) of the pixel's projection.  Flat or parallel detector: the ratio
+// of two affine functions of the pixel offset (perspective division, Eq. 4).  Arc detector:
+// the angle from the tile centre's ray, atan of (y' Dt - yt D_n)/(D_n Dt + y' yt), in cells.
+template <bool ARC, typename TV>
+__device__ __forceinline__ float bp_sigma(const TV &T, float di, float dr, float Dn, float yp, float rD, float kscale)
+{
+    if (ARC) {
+        const float den = fmaf(Dn, T.Dt, yp * T.yt);
+        return fmaf(atanf(fmaf(T.a1, di, T.b1 * dr) * rcp_approx(den)), kscale, T.phi);
+    }
+    return fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);
+}
 
 // One view of the pixel's gather in FP32, two cells (2m, 2m + 1) per step with packed FP32x2
 // arithmetic on even-aligned pair tables.  Aligning the window to even cells adds at most
 // one cell at each end; those cells lie outside the window, which bounds the support with
 // margin, so their entries are exactly 0 (a padding cell past n_det has sinogram value 0).
 // The normalisation h^2/(2B) = h^2/(4(p + C/2)) is folded into the division by tau'.
+// Arc detector: |s'| = R sin(dg d) for a cell d cells from the pixel's projection, R the
+// pixel's distance from the source; with dg d below ~0.05 rad, R dg d (1 - (dg d)^2/6) is
+// that sine to ~1e-9 relative (the next term of the series).
+template <bool ARC>
 __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, float di, float dr,
                                               const BpArgs &a, int nd, const float2 *__restrict__ y2row,
                                               const float4 *__restrict__ box2row, const float4 *__restrict__ cell2,
@@ -45,7 +65,7 @@ __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, 
     const float Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));   // depth along u
     const float yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));    // coordinate along w
     const float rD = rcp_approx(Dn);
-    const float sig = fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);   // cell coordinate - J
+    const float sig = bp_sigma<ARC>(T, di, dr, Dn, yp, rD, a.kscale);   // cell coordinate - J
     // footprint widths of the ray through the pixel centre: h(|n_x| + |n_y|) * rho
     const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
     const float zs = fabsf(za) + fabsf(zb);
@@ -55,6 +75,12 @@ __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, 
     float2 acc = make_float2(0.f, 0.f);
     const float2 Dn2 = make_float2(Dn, Dn), yp2 = make_float2(yp, yp);
     const float2 ne1 = make_float2(-1.f, -1.f), m2 = make_float2(-2.f, -2.f);
+    float2 G2 = Dn2, k2 = make_float2(0.f, 0.f);
+    if (ARC) {
+        const float G = sqrtf(fmaf(Dn, Dn, yp * yp)) * a.dg;
+        G2 = make_float2(G, G);
+        k2 = make_float2(a.nk6, a.nk6);
+    }
     const int m0 = g0 >> 1, m1 = g1 >> 1;
     const float d0 = sig - (float)(2 * m0 - J);
     float2 d = make_float2(d0, d0 - 1.f);
@@ -63,7 +89,11 @@ __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, 
         const float4 C0 = __ldg(cell2 + m);                                          // g1 | c1
         const float2 c2 = __ldg(cellc2 + m);
         const float2 yv = __ldg(y2row + m);
-        const float2 xs = __fmul2_rn(__fmul2_rn(Dn2, make_float2(C0.x, C0.y)), d);
+        float2 xs;
+        if (ARC)
+            xs = __fmul2_rn(__fmul2_rn(G2, d), __ffma2_rn(__fmul2_rn(d, d), k2, make_float2(1.f, 1.f)));
+        else
+            xs = __fmul2_rn(__fmul2_rn(Dn2, make_float2(C0.x, C0.y)), d);
         const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
         const float2 e = __ffma2_rn(Dn2, make_float2(C0.z, C0.w), __fmul2_rn(yp2, c2));         // tau'/2
         const float2 p = make_float2(A0.x, A0.y), nhC = make_float2(A1.z, A1.w);
@@ -75,6 +105,7 @@ __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, 
     return acc;
 }
 
+template <bool ARC>
 __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double *__restrict__ view_cs,
                                                      const float4 *__restrict__ box2,
                                                      const float4 *__restrict__ cell2,
@@ -121,7 +152,7 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
             float2 part = make_float2(0.f, 0.f);
             for (int vv = 0; vv < nvc; ++vv) {
                 const int v = v0 + vv;
-                part = __fadd2_rn(part, bp_view_f32(tv[vv], tj[vv], di, dr, a, g.nd, y + (long long)v * ndh,
+                part = __fadd2_rn(part, bp_view_f32<ARC>(tv[vv], tj[vv], di, dr, a, g.nd, y + (long long)v * ndh,
                                                     box2 + 2 * (long long)v * ndh, cell2, cellc2));
                 if ((vv & 15) == 15) {   // blocked summation over groups of 16 views
                     acc = __fadd2_rn(acc, part);
@@ -193,7 +224,9 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
             const double *yrow = y + (long long)(v0 + vv) * g.nd;
             const double Dn = T.Dt - T.hc * di - T.hs * dr;
             const double yp = T.yt - T.hs * di + T.hc * dr;
-            const double sig = T.phi + (T.rho + T.a1 * di + T.b1 * dr) / Dn;
+            const double sig = g.arc ? T.phi + atan((T.a1 * di + T.b1 * dr) / (Dn * T.Dt + yp * T.yt)) * (g.dps / g.ds)
+                                     : T.phi + (T.rho + T.a1 * di + T.b1 * dr) / Dn;
+            const double R = sqrt(Dn * Dn + yp * yp);
             const double zs = fabs(yp * T.hc - Dn * T.hs) + fabs(yp * T.hs + Dn * T.hc);
             const double hwc = kz * zs / (Dn * Dn) * (1.02 + 2.0 * g.h / Dn) + ke;
             const int jlo = max((int)ceil(sig - hwc), -J);
@@ -201,13 +234,17 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
             double part = 0.0;
             for (int jl = jlo; jl <= jhi; ++jl) {
                 const int j = J + jl;
-                const double sj = celld[4 * j], L = celld[4 * j + 1], dt = celld[4 * j + 2];
-                // normal of the cell's ray: (s_j u + D_ps w)/L_j, or w for parallel rays (L_j = 1)
-                const double nxv = g.par ? -s : (sj * c - g.dps * s) / L, nyv = g.par ? c : (sj * s + g.dps * c) / L;
+                const double sg = celld[4 * j], cg = celld[4 * j + 1], dt = celld[4 * j + 2];
+                // normal of the cell's ray: sin(g_j) u + cos(g_j) w (parallel rays: w)
+                const double nxv = sg * c - cg * s, nyv = sg * s + cg * c;
                 const double B = g.h * fmax(fabs(nxv), fabs(nyv)), C = g.h * fmin(fabs(nxv), fabs(nyv));
                 const BoxConsts<double> bc = make_box_consts<double>(B, C, g.h);
-                const double x = fabs(Dn * (g.ds / L) * (sig - jl));
-                const double e = g.par ? 0.5 * g.tau : (g.dps * Dn + sj * yp) / L * 0.5 * dt;
+                // |s'|: parallel ds |sigma - j|; flat D_n (ds / L_j) |sigma - j|; arc R |sin(angle)|
+                const double x = g.par ? fabs(g.ds * (sig - jl))
+                                 : g.arc ? fabs(R * sin((g.ds / g.dps) * (sig - jl)))
+                                         : fabs(Dn * (g.ds * cg / g.dps) * (sig - jl));
+                // tau'/2 = depth along the cell's ray * dtan_j / 2
+                const double e = g.par ? 0.5 * g.tau : (cg * Dn + sg * yp) * 0.5 * dt;
                 const double w = window_diff(x, e, bc.p, bc.q * bc.iC, bc.iC, 0.5 * C);
                 part += yrow[j] * bc.nrm * (w / e);
             }
@@ -237,7 +274,9 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
     const GeomConsts &g = geo->gc;
     dim3 blk(BP_T, BP_T), grd((g.nx + BP_T - 1) / BP_T, (g.ny + BP_T - 1) / BP_T, batch);
     if (dtype == CNSF_F32) {
-        BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(0.25 * g.h * g.h)};
+        const double dg = g.arc ? g.ds / g.dps : 0.0;
+        BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(0.25 * g.h * g.h),
+                 (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0)};
         // Enough blocks for several waves: split each tile's views when the tiles alone give
         // fewer than ~32 blocks per SM (partial images, then a fixed-order sum).
         int sms = 0, dev = 0;
@@ -268,7 +307,8 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
                 (const float *)sino, copy, nrows, g.nd);
             y2 = copy;
         }
-        bp_f32_kernel<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_T * BP_T), 0, st>>>(
+        auto kern = g.arc ? bp_f32_kernel<true> : bp_f32_kernel<false>;
+        kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_T * BP_T), 0, st>>>(
             g, geo->d_view_cs, reinterpret_cast<const float4 *>(geo->d_box2),
             reinterpret_cast<const float4 *>(geo->d_cell2), geo->d_cellc2, y2, (float *)img, a, geo->d_bp_order,
             (int)grd.x, nsplit, partial);

@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
                                                        const float4 *__restrict__ cell,
                                                        const float4 *__restrict__ Y, float *__restrict__ img,
                                                        float kz, float ke, float h2, float h2q, int b0,
-                                                       int nb_used, const int *__restrict__ order, int ntx)
+                                                       int nb_used, const int *__restrict__ order, int ntx,
+                                                       float kscale, float dg, float nk6)
 {
     __shared__ TileViewB tv[BPB_CHUNK];
     __shared__ int tj[BPB_CHUNK];
@@ -208,7 +209,12 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
             const float Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
             const float yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
             const float rD = rcp_approx(Dn);
-            const float sig = fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);
+            // cell coordinate - J: perspective ratio (flat, parallel) or angle (arc detector)
+            const float sig = g.arc ? fmaf(atanf(fmaf(T.a1, di, T.b1 * dr) * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))),
+                                           kscale, T.phi)
+                                    : fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);
+            // arc: |s'| = R sin(dg d) ~ R dg d (1 - (dg d)^2/6)
+            const float G = g.arc ? sqrtf(fmaf(Dn, Dn, yp * yp)) * dg : 0.f;
             const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
             const float hwc = fmaf(kz * (fabsf(za) + fabsf(zb)) * rD * rD, fmaf(h2, rD, 1.02f), ke);
             const int jlo = max((int)ceilf(sig - hwc), -J);
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
                 const long long q = vrow + J + jl;
                 const float4 A = __ldg(box + q);
                 const float4 C = __ldg(cell + J + jl);
-                const float x = fabsf(Dn * C.x * d);
+                const float x = g.arc ? fabsf(G * d * fmaf(d * d, nk6, 1.f)) : fabsf(Dn * C.x * d);
                 const float e = fmaf(Dn, C.y, yp * C.z);
                 const float w = window_diff(x, e, A.x, A.y, A.z, A.w);
                 part.fma_from(w * rcp_approx((A.x + A.w) * e), Y + q * NB4);
@@ -285,6 +291,8 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
     const int ntx = (g.nx + BPB_T - 1) / BPB_T, nty = (g.ny + BPB_T - 1) / BPB_T;
     dim3 blk(BPB_T * BPB_T), grd(ntx * nty);
     const float kz = (float)geo->bw.kz, ke = (float)geo->bw.ke, h2 = (float)(2.0 * g.h), h2q = (float)(0.25 * g.h * g.h);
+    const double dgd = g.arc ? g.ds / g.dps : 0.0;
+    const float kscale = (float)(g.arc ? g.dps / g.ds : 0.0), dg = (float)dgd, nk6 = (float)(-dgd * dgd / 6.0);
     const float4 *box = reinterpret_cast<const float4 *>(geo->d_box), *cell = reinterpret_cast<const float4 *>(geo->d_cellf);
     for (int b0 = 0; b0 < batch;) {
         const int nb4 = chunk_nb4(batch - b0), NB = 4 * nb4, used = std::min(NB, batch - b0);
@@ -292,11 +300,11 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
             sino, buf, nvd, b0, used, NB);
         const float4 *Y = reinterpret_cast<const float4 *>(buf);
         if (nb4 == 4)
-            bp_batch_kernel<4><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx);
+            bp_batch_kernel<4><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
         else if (nb4 == 2)
-            bp_batch_kernel<2><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx);
+            bp_batch_kernel<2><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
         else
-            bp_batch_kernel<1><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx);
+            bp_batch_kernel<1><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
         b0 += used;
     }
     cudaFreeAsync(buf, st);

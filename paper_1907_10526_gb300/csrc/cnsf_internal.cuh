@@ -34,6 +34,7 @@ struct GeomConsts {
     double rimg;      // distance from the rotation centre to the farthest image corner
     double s0;        // centre of cell 0
     int par;          // 1: parallel beam (Theorem 1): rays along -u, s = x . w, tau' = tau
+    int arc;          // 1: fan beam onto the arc of radius D_ps about the source (s = arc length)
 };
 
 // Per-cell quantities that do not depend on the view.
@@ -48,6 +49,26 @@ __host__ __device__ inline double cell_dtan(const GeomConsts &g, double sj)
 {
     double d2 = g.dps * g.dps + sj * sj, ht = 0.5 * g.tau;
     return ht * g.dps * (1.0 / (d2 + sj * ht) + 1.0 / (d2 - sj * ht));
+}
+
+// Direction of the central ray of cell j in the rotating frame: v_j = -cos(g_j) u + sin(g_j) w,
+// normal n_j = sin(g_j) u + cos(g_j) w, and the blur slope dtan_j (tau' = depth * dtan_j).
+// Flat detector: sin = s_j/L_j, cos = D_ps/L_j, dtan from the cell edges (cell_dtan).
+// Arc detector: g_j = s_j/D_ps and both edges sit at +-tau/(2 D_ps) from the central ray, so
+// dtan_j = 2 tan(tau/(2 D_ps)) for every cell.
+__host__ __device__ inline void cell_dir(const GeomConsts &g, double sj, double *sg, double *cg, double *dtan)
+{
+    if (g.arc) {
+        double ga = sj / g.dps;
+        *sg = sin(ga);
+        *cg = cos(ga);
+        *dtan = 2.0 * tan(0.5 * g.tau / g.dps);
+    } else {
+        double L = sqrt(g.dps * g.dps + sj * sj);
+        *sg = sj / L;
+        *cg = g.dps / L;
+        *dtan = cell_dtan(g, sj);
+    }
 }
 
 // Ray parameters of one (view, cell) in the walk frame.  The walk runs over the image
@@ -79,11 +100,11 @@ __host__ __device__ inline RayParams<T> make_ray_params(const GeomConsts &g, dou
         px = -sj * s; py = sj * c;
         dtan = 0.0;
     } else {
-        double L = sqrt(g.dps * g.dps + sj * sj);
-        vx = (-g.dps * c - sj * s) / L; vy = (-g.dps * s + sj * c) / L;
-        nxv = (sj * c - g.dps * s) / L; nyv = (sj * s + g.dps * c) / L;
+        double sg, cg;
+        cell_dir(g, sj, &sg, &cg, &dtan);
+        vx = -cg * c - sg * s; vy = -cg * s + sg * c;
+        nxv = sg * c - cg * s; nyv = sg * s + cg * c;
         px = g.dpo * c; py = g.dpo * s;
-        dtan = cell_dtan(g, sj);
     }
     RayParams<T> R;
     int tr = fabs(vy) >= fabs(vx) ? 0 : 1;
@@ -151,6 +172,10 @@ struct TileView {
 // per-pixel offsets stay small).  (hc, hs) = h (cos, sin) is the per-pixel step of the depth.
 // Parallel beam: the projection is affine, sigma = (y' - s_0)/ds; the depth is held at
 // D_n = 1 (hc = hs = 0) so that the same per-pixel arithmetic applies.
+// Arc detector: sigma = (D_ps atan2(y', D_n) - s_0)/ds.  Relative to the tile centre,
+//   sigma = J + phi + (D_ps/ds) atan((a1 di + b1 dr) / (D_n Dt + y' yt)),
+// where a1 di + b1 dr = y' Dt - yt D_n exactly (no constant term, so no cancellation), and
+// rho = 0.
 __host__ __device__ inline void tile_view_double(const GeomConsts &g, double c, double s, double it, double rt,
                                                  double *Dt, double *yt, double *a1, double *b1,
                                                  double *rho, double *phi, int *J, double *hc, double *hs)
@@ -172,12 +197,19 @@ __host__ __device__ inline void tile_view_double(const GeomConsts &g, double c, 
         *hc = g.h * c; *hs = g.h * s;
     }
     double sig = Nt / D;
+    if (g.arc) sig = (g.dps * atan2(yw, D) - g.s0) / g.ds;
     double Jd = floor(sig);
     *Dt = D;
     *yt = yw;
-    *a1 = aN - sig * aD;
-    *b1 = bN - sig * bD;
-    *rho = Nt - sig * D;
+    if (g.arc) {
+        *a1 = ay * D - yw * aD;
+        *b1 = by * D - yw * bD;
+        *rho = 0.0;
+    } else {
+        *a1 = aN - sig * aD;
+        *b1 = bN - sig * bD;
+        *rho = Nt - sig * D;
+    }
     *phi = sig - Jd;
     *J = (int)Jd;
 }
@@ -205,7 +237,7 @@ struct alignas(16) BoxF {
 // Per-cell constants of the FP32 back projector: s' = D_n g1 (sigma - j) and
 // tau'/2 = D_n c1 + y' c2 for a pixel at depth D_n and coordinate y' along w.
 struct alignas(16) CellF {
-    float g1, c1, c2, pad;   // ds/L_j, D_ps dtan_j/(2 L_j), s_j dtan_j/(2 L_j)
+    float g1, c1, c2, pad;   // ds/L_j, cos(g_j) dtan_j/2, sin(g_j) dtan_j/2 (flat: cos = D_ps/L_j)
 };
 
 // Pair constants of the FP32 back projector: entry m holds cells 2m and 2m + 1 side by
@@ -241,7 +273,7 @@ struct cnsf_geometry {
     cnsf::BpWindow bw;        // back projector cell window
     // device tables
     double *d_view_cs;        // [nv][2] cos, sin (FP64)
-    double *d_cell_d;         // [nd][4] s_j, L_j, dtan_j, 0 (FP64)
+    double *d_cell_d;         // [nd][4] sin(g_j), cos(g_j), dtan_j, s_j (FP64; parallel: 0, 1, 0, s_j)
     cnsf::BoxF *d_box;        // [nv][nd]
     cnsf::CellF *d_cellf;     // [nd]
     cnsf::BoxPairF *d_box2;   // [nv][ceil(n_det/2)]

@@ -33,12 +33,18 @@ static int validate(const cnsf_geometry_desc *d)
     if (!(d->pixel_mm > 0) || !(d->det_spacing_mm > 0) || !(d->det_width_mm > 0)) return CNSF_ERR_INVALID;
     if (!std::isfinite(d->center_x_mm) || !std::isfinite(d->center_y_mm) || !std::isfinite(d->det_offset_mm))
         return CNSF_ERR_INVALID;
-    if (d->detector != CNSF_DETECTOR_FLAT && d->detector != CNSF_DETECTOR_PARALLEL) return CNSF_ERR_UNSUPPORTED;
-    if (d->detector == CNSF_DETECTOR_FLAT) {   // parallel rays have no source: d_po, d_ps unused
+    if (d->detector != CNSF_DETECTOR_FLAT && d->detector != CNSF_DETECTOR_ARC &&
+        d->detector != CNSF_DETECTOR_PARALLEL)
+        return CNSF_ERR_UNSUPPORTED;
+    if (d->detector != CNSF_DETECTOR_PARALLEL) {   // parallel rays have no source: d_po, d_ps unused
         if (!(d->d_po_mm > 0) || !(d->d_ps_mm > d->d_po_mm)) return CNSF_ERR_INVALID;
         double rx = std::fabs(d->center_x_mm) + 0.5 * d->n_x * d->pixel_mm;
         double ry = std::fabs(d->center_y_mm) + 0.5 * d->n_y * d->pixel_mm;
         if (std::hypot(rx, ry) + 2.0 * d->pixel_mm >= d->d_po_mm) return CNSF_ERR_INVALID;
+    }
+    if (d->detector == CNSF_DETECTOR_ARC) {   // every cell's ray within 80 deg of the central one
+        double half = 0.5 * (d->n_det - 1) * d->det_spacing_mm + std::fabs(d->det_offset_mm) + 0.5 * d->det_width_mm;
+        if (!(half < (80.0 / 180.0) * M_PI * d->d_ps_mm)) return CNSF_ERR_INVALID;
     }
     if (d->angles_rad)
         for (int k = 0; k < d->n_views; ++k)
@@ -58,6 +64,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     g.h = d->pixel_mm; g.cx = d->center_x_mm; g.cy = d->center_y_mm;
     g.ds = d->det_spacing_mm; g.tau = d->det_width_mm; g.doff = d->det_offset_mm;
     g.par = d->detector == CNSF_DETECTOR_PARALLEL ? 1 : 0;
+    g.arc = d->detector == CNSF_DETECTOR_ARC ? 1 : 0;
     g.dpo = g.par ? 0.0 : d->d_po_mm;
     g.dps = g.par ? 0.0 : d->d_ps_mm;
     g.rimg = std::hypot(std::fabs(g.cx) + 0.5 * g.nx * g.h, std::fabs(g.cy) + 0.5 * g.ny * g.h);
@@ -74,10 +81,10 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     std::vector<double> celld(4 * (size_t)nd);
     double dtan_max = 0.0, smax = 0.0;
     for (int j = 0; j < nd; ++j) {
-        // parallel rays: unit "length" and no perspective (the blur is tau at every depth)
-        double sj = cell_centre(g, j);
-        double L = g.par ? 1.0 : std::sqrt(g.dps * g.dps + sj * sj), dt = g.par ? 0.0 : cell_dtan(g, sj);
-        celld[4 * j] = sj; celld[4 * j + 1] = L; celld[4 * j + 2] = dt; celld[4 * j + 3] = 0.0;
+        // parallel rays: no direction change across cells and no perspective (blur tau at every depth)
+        double sj = cell_centre(g, j), sg = 0.0, cg = 1.0, dt = 0.0;
+        if (!g.par) cell_dir(g, sj, &sg, &cg, &dt);
+        celld[4 * j] = sg; celld[4 * j + 1] = cg; celld[4 * j + 2] = dt; celld[4 * j + 3] = sj;
         dtan_max = std::max(dtan_max, dt);
         smax = std::max(smax, std::fabs(sj));
     }
@@ -87,10 +94,12 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     std::vector<BoxF> box(nr);
     std::vector<CellF> cellf(nd);
     for (int j = 0; j < nd; ++j) {
-        const double sj = celld[4 * j], Lj = celld[4 * j + 1], dtj = celld[4 * j + 2];
-        cellf[j].g1 = (float)(g.ds / Lj);
-        cellf[j].c1 = (float)(g.par ? 0.5 * g.tau : g.dps * dtj / (2.0 * Lj));
-        cellf[j].c2 = (float)(sj * dtj / (2.0 * Lj));
+        const double sg = celld[4 * j], cg = celld[4 * j + 1], dtj = celld[4 * j + 2], sj = celld[4 * j + 3];
+        // g1: s' per cell of (sigma - j) at unit depth, flat detector ds/L_j (parallel: ds);
+        // the arc detector takes s' from the angle instead and leaves it unused
+        cellf[j].g1 = (float)(g.par ? g.ds : g.arc ? 0.0 : g.ds / std::sqrt(g.dps * g.dps + sj * sj));
+        cellf[j].c1 = (float)(g.par ? 0.5 * g.tau : 0.5 * cg * dtj);
+        cellf[j].c2 = (float)(0.5 * sg * dtj);
         cellf[j].pad = 0.0f;
     }
     const double fx_one = 4294967296.0;  // 2^32
@@ -224,6 +233,12 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         // s' = ds (sigma - j); the support of M_[B, C, tau] is |s'| < (B + C + tau)/2 and B + C <= sqrt(2) h
         geo->bw.kz = 0.0;
         geo->bw.ke = (std::sqrt(2.0) * g.h + g.tau) / (2.0 * g.ds) * 1.001 + 1e-3;
+    } else if (g.arc) {
+        // Window in cells of D_ps/ds per radian: the footprint term as for the flat detector
+        // (the pixel's distance from the source is at least its depth D_n) and the blur term
+        // tau'_j/(2 R) <= dtan/2 rad, with 1% slack for the sine of the angles.
+        geo->bw.kz = g.dps / (2.0 * g.ds);
+        geo->bw.ke = 0.5 * dtan_max * g.dps / g.ds * 1.01 + 1e-3;
     } else {
         double dmin = g.dpo - g.rimg;
         double lmax = std::sqrt(g.dps * g.dps + (smax + g.ds) * (smax + g.ds));
@@ -231,7 +246,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         double W = std::max(64.0 * g.ds, 1.5 * reach * lmax / dmin + 2.0 * g.ds);
         double ke = 0.0;
         for (int j = 0; j < nd; ++j) {
-            double sj = celld[4 * j], L = celld[4 * j + 1], dt = celld[4 * j + 2];
+            double dt = celld[4 * j + 2], sj = celld[4 * j + 3], L = std::sqrt(g.dps * g.dps + sj * sj);
             ke = std::max(ke, (L * L / g.dps) * dt / (2.0 * g.ds) * (1.0 + std::fabs(sj) * W / (L * L)));
         }
         geo->bw.kz = g.dps / (2.0 * g.ds);

@@ -43,7 +43,7 @@ class FanGeometry:
     center_y: float = 0.0
     det_offset: float = 0.0     # detector centre offset along s, mm
     angles: Optional[tuple] = None  # explicit view angles (rad); None -> 2*pi*k/V
-    detector: str = "flat"      # "flat" fan beam, or "parallel" beam (d_po, d_ps unused)
+    detector: str = "flat"      # "flat" or "arc" fan beam, or "parallel" beam (d_po, d_ps unused)
 
     def view_angles(self) -> np.ndarray:
         if self.angles is not None:

@@ -39,10 +39,11 @@ def test_invalid_geometries_refused_without_gpu():
         GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 0.0, 0, 30, 60, 0),    # zero cell width
     ]
     bad.append(GeometryDesc(0, 4, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 0, 0, 2))   # parallel, no columns
+    bad.append(GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 200, 1, 1, 0, 30, 60, 1))   # arc past 80 degrees
     for d in bad:
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
     from paper_1907_10526_gb300._lib import CNSF_ERR_UNSUPPORTED
-    for kind in (1, 3, -1):   # only flat fan beam (0) and parallel beam (2) are built
+    for kind in (3, -1):   # flat (0) and arc (1) fan beams and parallel beam (2) are built
         d = GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 30, 60, kind)
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_UNSUPPORTED
     assert lib.cnsf_forward_project(None, None, None, 1, 0, None) == CNSF_ERR_INVALID

@@ -20,6 +20,8 @@ Parity status of each function (what pins it; see tests/test_oracle_*.py):
                       unity (parallel), uniform-disk convergence, orientation
                       fixtures under tests/golden/.
 * ``ref_entry``       pinned: midpoint-rule supersampling, self-convergence.
+* ``forward_ref``/``back_ref`` and their sampled forms: pinned against the dense Ref
+                      matrix (every triple, no culling) and the adjoint identity.
 * arc detector        (``detector="arc"``) pinned: chords and Eq. (17) edge cuts built
                       from explicit arc coordinates, Ref self-convergence, dense
                       brute force of both enumerations, error vs distance, mirror
@@ -94,6 +96,10 @@ def _load():
                 "og_forward_dense": (None, [G, D, D]),
                 "og_back_dense": (None, [G, D, D]),
                 "og_matrix": (None, [G, D]),
+                "og_back_ref": (None, [G, D, D, i]),
+                "og_forward_ref_rays": (None, [G, D, l, I, I, D, i]),
+                "og_back_ref_pixels": (None, [G, D, l, L, D, i]),
+                "og_matrix_ref": (None, [G, D, i]),
                 "og_num_threads": (i, []),
                 "og_set_num_threads": (None, [i]),
             }
@@ -202,6 +208,44 @@ def forward_ref(g, img, ngauss: int = 20, parallel=False) -> np.ndarray:
     y = np.zeros((G.n_views, G.n_det))
     _load().og_forward_ref(G.ptr, _dp(c), _dp(y), ngauss)
     return y
+
+
+def back_ref(g, sino, ngauss: int = 20, parallel=False) -> np.ndarray:
+    """A_ref^T y with the Ref entries (pixel-driven), float64 [ny][nx]."""
+    G = _geom(g, parallel)
+    y = _f64(sino)
+    c = np.zeros((G.ny, G.nx))
+    _load().og_back_ref(G.ptr, _dp(y), _dp(c), ngauss)
+    return c
+
+
+def forward_ref_rays(g, img, views, cells, ngauss: int = 20, parallel=False) -> np.ndarray:
+    G = _geom(g, parallel)
+    c = _f64(img)
+    v = np.ascontiguousarray(views, dtype=np.int32)
+    j = np.ascontiguousarray(cells, dtype=np.int32)
+    out = np.zeros(len(v))
+    _load().og_forward_ref_rays(G.ptr, _dp(c), len(v), v.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                j.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out), ngauss)
+    return out
+
+
+def back_ref_pixels(g, sino, pixels, ngauss: int = 20, parallel=False) -> np.ndarray:
+    G = _geom(g, parallel)
+    y = _f64(sino)
+    p = np.ascontiguousarray(pixels, dtype=np.int64)
+    out = np.zeros(len(p))
+    _load().og_back_ref_pixels(G.ptr, _dp(y), len(p), p.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                               _dp(out), ngauss)
+    return out
+
+
+def matrix_ref(g, ngauss: int = 20, parallel=False) -> np.ndarray:
+    """Dense A_ref (every triple evaluated): rows (view, cell), columns (r, i)."""
+    G = _geom(g, parallel)
+    a = np.zeros((G.n_views * G.n_det, G.nx * G.ny))
+    _load().og_matrix_ref(G.ptr, _dp(a), ngauss)
+    return a
 
 
 def forward_rays(g, img, views, cells, parallel=False) -> np.ndarray:

@@ -512,12 +512,13 @@ long og_count_nnz(const og_geom *g)
 }
 
 /* (A^T y)_n for one pixel: for each view, project the pixel centre onto the
- * detector and take the cells within reach. */
-static double og_pixel_sum(const og_geom *g, const double *y, int i, int r)
+ * detector and take the cells within reach (widened by `extra`). */
+static double og_pixel_sum_fn(const og_geom *g, const double *y, int i, int r, og_entry_fn fn, int ng,
+                              double extra)
 {
     double kx, ky;
     og_pixel_centre(g, i, r, &kx, &ky);
-    double reach = og_reach(g);
+    double reach = og_reach(g) + extra;
     double smax = fabs(g->det_off) + 0.5 * g->ndet * g->ds + g->ds;
     double lmax = sqrt(g->dps * g->dps + smax * smax);
     double acc = 0.0;
@@ -534,9 +535,14 @@ static double og_pixel_sum(const og_geom *g, const double *y, int i, int r)
         if (jlo < 0) jlo = 0;
         if (jhi > g->ndet - 1) jhi = g->ndet - 1;
         for (int j = jlo; j <= jhi; ++j)
-            acc += y[(long)k * g->ndet + j] * og_entry(g, k, j, i, r);
+            acc += y[(long)k * g->ndet + j] * fn(g, k, j, i, r, ng);
     }
     return acc;
+}
+
+static double og_pixel_sum(const og_geom *g, const double *y, int i, int r)
+{
+    return og_pixel_sum_fn(g, y, i, r, og_entry_cnsf_cb, 0, 0.0);
 }
 
 /* Back projection c = A^T y; c is [ny][nx]. */
@@ -554,6 +560,43 @@ void og_back_pixels(const og_geom *g, const double *y, long nsamp, const long *p
 #pragma omp parallel for schedule(dynamic, 4)
     for (long q = 0; q < nsamp; ++q)
         out[q] = og_pixel_sum(g, y, (int)(pix[q] % g->nx), (int)(pix[q] / g->nx));
+}
+
+/* Ref operators: the same enumerations with the Ref entries (bin-averaged exact
+ * chords), the reach widened by one pixel (the support of a bin's wedge is not
+ * centred on the central ray). */
+void og_back_ref(const og_geom *g, const double *y, double *c, int ng)
+{
+    long np = (long)g->nx * g->ny;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long n = 0; n < np; ++n)
+        c[n] = og_pixel_sum_fn(g, y, (int)(n % g->nx), (int)(n / g->nx), og_entry_ref_cb, ng, g->h);
+}
+
+void og_forward_ref_rays(const og_geom *g, const double *c, long nsamp, const int *views,
+                         const int *cells, double *out, int ng)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long q = 0; q < nsamp; ++q)
+        out[q] = og_ray_sum(g, c, views[q], cells[q], og_entry_ref_cb, ng, g->h, NULL);
+}
+
+void og_back_ref_pixels(const og_geom *g, const double *y, long nsamp, const long *pix, double *out, int ng)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long q = 0; q < nsamp; ++q)
+        out[q] = og_pixel_sum_fn(g, y, (int)(pix[q] % g->nx), (int)(pix[q] / g->nx), og_entry_ref_cb, ng, g->h);
+}
+
+/* Dense Ref matrix (every triple, no culling), row (view*ndet + cell), column (r*nx + i). */
+void og_matrix_ref(const og_geom *g, double *a, int ng)
+{
+    long nr = (long)g->nviews * g->ndet, np = (long)g->nx * g->ny;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (long kj = 0; kj < nr; ++kj)
+        for (long n = 0; n < np; ++n)
+            a[kj * np + n] = og_ref_entry(g, (int)(kj / g->ndet), (int)(kj % g->ndet), (int)(n % g->nx),
+                                          (int)(n / g->nx), ng);
 }
 
 /* Brute force: every (view, cell, pixel) triple, no support culling. */

@@ -116,3 +116,23 @@ def test_uniform_disk_converges():
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 5e-3
     assert math.log2(errs[0] / errs[2]) / 2 > 0.8
+
+
+@pytest.mark.parametrize("kind", ["flat", "arc", "parallel"])
+def test_ref_operators_match_dense_ref_matrix(kind):
+    """The Ref forward and back loops (support culled, reach widened by a pixel) against the
+    dense matrix of Ref entries, every triple evaluated; the sampled forms against both."""
+    g = FanGeometry(nx=7, ny=6, n_views=5, n_det=18, pixel=1.2, det_spacing=0.9, det_width=1.1, d_po=14.0,
+                    d_ps=30.0, center_x=0.3, center_y=-0.4, det_offset=0.2,
+                    angles=(0.0, 0.6, math.pi / 2, 2.2, 4.0), detector=kind)
+    A = O.matrix_ref(g, 12)
+    rng = np.random.default_rng(1)
+    c = rng.uniform(-1, 1, (g.ny, g.nx))
+    y = rng.uniform(-1, 1, (g.n_views, g.n_det))
+    assert np.max(np.abs(O.forward_ref(g, c, 12).ravel() - A @ c.ravel())) < 1e-13
+    assert np.max(np.abs(O.back_ref(g, y, 12).ravel() - A.T @ y.ravel())) < 1e-13
+    v, j = np.array([0, 2, 4]), np.array([3, 9, 14])
+    assert np.allclose(O.forward_ref_rays(g, c, v, j, 12), (A @ c.ravel()).reshape(5, 18)[v, j], atol=1e-13)
+    p = np.array([0, 17, 41])
+    assert np.allclose(O.back_ref_pixels(g, y, p, 12), (A.T @ y.ravel())[p], atol=1e-13)
+    assert np.count_nonzero(A) > 50

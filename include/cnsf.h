@@ -119,10 +119,29 @@ CNSF_API int cnsf_forward_project(const cnsf_geometry *geom, const void *image, 
 
 /* Back projection c = A^T y, the exact adjoint of cnsf_forward_project (same
  * entries), pixel-driven gather without atomics.  sino: device
- * [batch][n_views][n_det]; image: device [batch][n_y][n_x], overwritten.  Uses no
- * scratch memory. */
+ * [batch][n_views][n_det]; image: device [batch][n_y][n_x], overwritten.  FP32 may
+ * allocate scratch stream-ordered on `stream` (partial images of groups of views,
+ * summed in a fixed order; a padded copy of the sinogram when n_det is odd or the
+ * pointer is not 8-byte aligned; interleaved copies for batch >= 2) and frees it the
+ * same way.  FP64 uses no scratch. */
 CNSF_API int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch,
                       int32_t dtype, void *stream);
+
+/* Reference projector (Sec. IV, "Ref"): the same operator shape with the exact entries
+ * a_ref = (1/tau) int over the cell of the pixel's exact line integrals (Eq. 1-2),
+ * integrated by Gauss-Legendre on the smooth pieces between the detector coordinates
+ * of the pixel corners, in FP64 whatever dtype (about 1e-15 relative).  For the
+ * parallel kind this equals cnsf_forward_project (Theorem 1); for the fan kinds it is
+ * what the CNSF entries approximate.  Ray-driven, no atomics, no scratch; layouts and
+ * errors as cnsf_forward_project.  Tens of times slower than the CNSF path: a
+ * high-accuracy mode and the yardstick of the approximation error. */
+CNSF_API int cnsf_forward_project_ref(const cnsf_geometry *geom, const void *image, void *sino, int32_t batch,
+                                      int32_t dtype, void *stream);
+
+/* Adjoint of cnsf_forward_project_ref (same entries, pixel-driven, no atomics, no
+ * scratch); layouts and errors as cnsf_back_project. */
+CNSF_API int cnsf_back_project_ref(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch,
+                                   int32_t dtype, void *stream);
 
 /* Number of non-zero entries of A: pairs (view, cell, pixel) whose pixel centre lies
  * strictly inside the support of the footprint, |s'| < (zeta_1 + zeta_2 + tau')/2

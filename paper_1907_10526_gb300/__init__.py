@@ -17,7 +17,8 @@ import torch
 
 from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, CnsfError, GeometryDesc, check, lib  # noqa: F401
 
-__all__ = ["Geometry", "forward_project", "back_project", "count_nonzeros", "forward_project_noalloc",
+__all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
+           "count_nonzeros", "forward_project_noalloc",
            "sirt", "cgls", "SolverWorkspace", "Projector", "project", "CnsfError"]
 
 
@@ -144,6 +145,21 @@ def back_project(geom: Geometry, sino: torch.Tensor, out: Optional[torch.Tensor]
     """c = A^T y.  sinogram [..., n_views, n_det] -> image [..., ny, nx]."""
     return _run(lib.cnsf_back_project, "cnsf_back_project", geom, sino, geom.sino_shape, geom.image_shape,
                 out, stream)
+
+
+def forward_project_ref(geom: Geometry, image: torch.Tensor, out: Optional[torch.Tensor] = None,
+                        stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """y = A_ref c with the reference projector's exact entries (bin-averaged exact chords,
+    Sec. IV), FP64 inside whatever the dtype; shapes as ``forward_project``."""
+    return _run(lib.cnsf_forward_project_ref, "cnsf_forward_project_ref", geom, image, geom.image_shape,
+                geom.sino_shape, out, stream)
+
+
+def back_project_ref(geom: Geometry, sino: torch.Tensor, out: Optional[torch.Tensor] = None,
+                     stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """c = A_ref^T y, the adjoint of ``forward_project_ref``."""
+    return _run(lib.cnsf_back_project_ref, "cnsf_back_project_ref", geom, sino, geom.sino_shape,
+                geom.image_shape, out, stream)
 
 
 def forward_project_noalloc(geom: Geometry, image: torch.Tensor, out: Optional[torch.Tensor] = None,

@@ -35,6 +35,8 @@ _SIGNATURES = {
     "cnsf_geometry_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int32)] * 4),
     "cnsf_forward_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_back_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "cnsf_forward_project_ref": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "cnsf_back_project_ref": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_count_nonzeros": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), _P]),
     "cnsf_forward_project_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_solver_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),

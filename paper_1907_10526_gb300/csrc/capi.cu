@@ -97,6 +97,30 @@ int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void *image, 
     }
 }
 
+int cnsf_forward_project_ref(const cnsf_geometry *geom, const void *image, void *sino, int32_t batch, int32_t dtype,
+                             void *stream)
+{
+    try {
+        int s = check_call(geom, image, sino, batch, dtype);
+        if (s != CNSF_OK) return s;
+        return launch_forward_ref(geom, image, sino, batch, dtype, (cudaStream_t)stream);
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
+int cnsf_back_project_ref(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch, int32_t dtype,
+                          void *stream)
+{
+    try {
+        int s = check_call(geom, sino, image, batch, dtype);
+        if (s != CNSF_OK) return s;
+        return launch_back_ref(geom, sino, image, batch, dtype, (cudaStream_t)stream);
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
 int cnsf_count_nonzeros(const cnsf_geometry *geom, uint64_t *count, void *stream)
 {
     try {

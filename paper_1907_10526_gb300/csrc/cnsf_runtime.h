@@ -22,6 +22,12 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
                 cudaStream_t stream);
 int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t stream);
 
+// Reference projector (reference.cu): bin-averaged exact chords, FP64 entries.
+int launch_forward_ref(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,
+                       cudaStream_t stream);
+int launch_back_ref(const cnsf_geometry *geo, const void *sino, void *img, int batch, int dtype,
+                    cudaStream_t stream);
+
 // Forward projection into caller-provided scratch (bytes from forward_scratch_bytes).
 size_t forward_scratch_bytes(const cnsf_geometry *geo, int batch, int dtype);
 int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,

@@ -310,6 +310,7 @@ def run_cnsf(args):
         line["reconstruction_2048"] = bench_solvers(dev)
         line["batch16_512x360"] = bench_batch16(dev)
         line["e4_ladder"] = bench_e4_ladder(dev)
+        line["reference_projector"] = bench_reference(dev)
         line["p50_recon_latency_s"] = line["serving"]["continuous"].get("p50_s")
         line["p99_recon_latency_s"] = line["serving"]["continuous"].get("p99_s")
     if rank == 0 and not args.no_cpu_baseline:
@@ -434,6 +435,42 @@ def bench_e4_ladder(dev, reps: int = 3):
         out.append({"n": n, "n_det": n_det, "d_po_d_so_mm": d, "fp_ms": min(fp), "bp_ms": min(bp),
                     "fp_per_view_ms": min(fp) / 360, "bp_per_view_ms": min(bp) / 360})
         del geom
+    return out
+
+
+def bench_reference(dev):
+    """The reference projector (exact bin-averaged chords, FP64) against the CNSF kernels:
+    its run time at 512^2 x 720 x 888, and the CNSF approximation error on the whole-image
+    accuracy cases of Sec. IV-C (random-ellipse phantoms in place of the paper's)."""
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import E3_CASES, config_geometry, e3_geometry, ellipse_phantom, phantom_for_config
+    out = {}
+    g = config_geometry(2)
+    geom = cnsf.Geometry(g)
+    x = torch.tensor(phantom_for_config(2), dtype=torch.float64, device=dev)
+    y = cnsf.forward_project_ref(geom, x)
+    c = cnsf.back_project_ref(geom, y)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    cnsf.forward_project_ref(geom, x, out=y)
+    ev[1].record()
+    cnsf.back_project_ref(geom, y, out=c)
+    ev[2].record()
+    torch.cuda.synchronize()
+    yc = cnsf.forward_project(geom, x)
+    out["512x720x888"] = {"ref_fp_ms": ev[0].elapsed_time(ev[1]), "ref_bp_ms": ev[1].elapsed_time(ev[2]),
+                          "cnsf_vs_ref_rel_l2": float((yc - y).norm() / y.norm()), "dtype": "f64"}
+    for (n, n_det, d) in E3_CASES:
+        gg = e3_geometry(n)
+        gm = cnsf.Geometry(gg)
+        img = torch.tensor(ellipse_phantom(n, 12, 1.0, seed=30 + n), dtype=torch.float64, device=dev)
+        yr = cnsf.forward_project_ref(gm, img)
+        ya = cnsf.forward_project(gm, img)
+        out[f"{n}mm_{n_det}cells_tau0.5_D{int(d)}"] = {
+            "max_abs_err": float((ya - yr).abs().max()), "peak": float(yr.abs().max()),
+            "rel_l2": float((ya - yr).norm() / yr.norm())}
     return out
 
 

@@ -99,6 +99,19 @@ def e4_geometry(n: int) -> FanGeometry:
     raise ValueError(f"no ladder rung of size {n}")
 
 
+# Whole-image accuracy comparison of the paper's Sec. IV-C: n mm images (1 mm pixels), 360
+# views, cells of pitch 1 mm and width tau = 0.5 mm, D_po = D_so; the paper's phantoms
+# (Shepp-Logan, a brain slice) are stood in for by random-ellipse phantoms.
+E3_CASES = ((128, 409, 200.0), (256, 815, 400.0))
+
+
+def e3_geometry(n: int) -> FanGeometry:
+    for (m, n_det, d) in E3_CASES:
+        if m == n:
+            return FanGeometry(nx=n, ny=n, n_views=360, n_det=n_det, det_width=0.5, d_po=d, d_ps=2.0 * d)
+    raise ValueError(f"no accuracy case of size {n}")
+
+
 def serving_geometry(n: int, n_views: int) -> FanGeometry:
     """Geometry of one serving request: n x n image, n_det = round(1.75 n)."""
     d_po, d_ps = scaled_distances(n)

@@ -170,6 +170,52 @@ CNSF_API int cnsf_sirt(const cnsf_geometry *geom, const void *sino, void *image,
 CNSF_API int cnsf_cgls(const cnsf_geometry *geom, const void *sino, void *image, int32_t iters, int32_t resume,
                        int32_t dtype, void *ws, size_t ws_bytes, void *stream);
 
+/* ASD-POCS (adaptive steepest descent POCS with total variation, Sidky & Pan 2008), the
+ * reconstruction method of Sec. IV-E, on the device.  One outer iteration:
+ *   1. a data-consistency sweep over the ordered subsets of views, subset by subset
+ *      x += beta C_s A_s^T R_s (y_s - A_s x), R_s = 1/(A_s 1), C_s = 1/(A_s^T 1) (0 where
+ *      the sum is 0), then x = max(x, 0);
+ *   2. dp = |x - x_before_1|; dd = |A x - y| when data_tol > 0;
+ *   3. on the first iteration the TV step is alpha * dp;
+ *   4. tv_steps steps x -= step * d/|d|, d = grad TV(x) (none when d = 0), with
+ *      TV(x) = sum sqrt(tv_eps^2 + Dx^2 + Dy^2) over backward differences that vanish
+ *      across the image border;
+ *   5. dg = |x - x_after_1|; if dg > r_max dp and (data_tol <= 0 or dd > data_tol) the TV
+ *      step is multiplied by alpha_red;
+ *   6. beta *= relax_red.
+ * Fields left at the values in brackets reproduce Sidky and Pan's choices. */
+typedef enum { CNSF_PROJECTOR_CNSF = 0, CNSF_PROJECTOR_REF = 1 } cnsf_projector;
+
+typedef struct {
+    int32_t iters;         /* outer iterations (>= 0)                                  */
+    int32_t tv_steps;      /* TV steps per iteration (>= 0) [20]                       */
+    double relax;          /* beta, initial data-step relaxation, (0, 2) [1]           */
+    double relax_red;      /* beta reduction per iteration, (0, 1] [0.995]             */
+    double alpha;          /* first TV step relative to the first data move, >= 0 [0.2] */
+    double alpha_red;      /* TV step reduction, (0, 1] [0.95]                         */
+    double r_max;          /* TV/data move ratio that triggers a reduction, > 0 [0.95] */
+    double data_tol;       /* residual tolerance; <= 0: the test is always met [0]     */
+    double tv_eps;         /* TV smoothing, >= 0 [1e-4]                                */
+    int32_t projector;     /* cnsf_projector: the CNSF entries or the reference ones    */
+} cnsf_asd_pocs_params;
+
+/* Device bytes of the workspace of cnsf_asd_pocs for these subsets (0 on bad input). */
+CNSF_API size_t cnsf_asd_pocs_workspace_bytes(const cnsf_geometry *const *subsets, int32_t n_subsets,
+                                              int32_t dtype);
+
+/* Run ASD-POCS.  subsets: n_subsets geometries (host array of handles) that differ only
+ * in their views, swept in this order (one subset: the simultaneous SIRT form of the
+ * data step).  rows: host array of the subsets' views in order, the sinogram row of
+ * each (a permutation of 0 .. total views - 1).  sino: device [total views][n_det] in
+ * the original row order.  image: device [n_y][n_x], x0 in, the result out.  ws: device
+ * workspace of cnsf_asd_pocs_workspace_bytes, 256-byte aligned, owned by the caller
+ * (not touched by any other call while this one runs).  Asynchronous on `stream`
+ * (the rows array is copied before return).  CNSF_ERR_INVALID for inconsistent
+ * subsets, a bad permutation, parameters outside their ranges or a short workspace. */
+CNSF_API int cnsf_asd_pocs(const cnsf_geometry *const *subsets, int32_t n_subsets, const int32_t *rows,
+                           const void *sino, void *image, const cnsf_asd_pocs_params *params, int32_t dtype,
+                           void *ws, size_t ws_bytes, void *stream);
+
 /* Size of the static device array used by cnsf_forward_project_noalloc: 16 MiB. */
 #define CNSF_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 

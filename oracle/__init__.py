@@ -392,7 +392,7 @@ def tv_grad(img, eta: float = 1e-8) -> np.ndarray:
 
 
 ASD_DEFAULTS = dict(tv_steps=20, relax=1.0, relax_red=0.995, alpha=0.2, alpha_red=0.95, r_max=0.95,
-                    data_tol=0.0, tv_eps=1e-8)
+                    data_tol=0.0, tv_eps=1e-4)
 
 
 def view_subsets(n_views: int, subsets: int) -> list:

@@ -15,10 +15,10 @@ from typing import Optional
 
 import torch
 
-from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, CnsfError, GeometryDesc, check, lib  # noqa: F401
+from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, AsdPocsParams, CnsfError, GeometryDesc, check, lib  # noqa: F401
 
 __all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
-           "count_nonzeros", "forward_project_noalloc",
+           "count_nonzeros", "forward_project_noalloc", "asd_pocs",
            "sirt", "cgls", "SolverWorkspace", "Projector", "project", "CnsfError"]
 
 
@@ -73,6 +73,29 @@ class Geometry:
     @property
     def handle(self):
         return self._h
+
+    def view_angles(self):
+        """The view angles (rad): the given ones, else 2 pi k / n_views."""
+        if self._angles is not None:
+            return [float(a) for a in self._angles]
+        return [2.0 * math.pi * k / self.n_views for k in range(self.n_views)]
+
+    def subsets(self, n: int):
+        """Interleaved ordered subsets of the views (subset s: views s, s + n, s + 2n, ...),
+        each as a geometry of its own on the same device; cached."""
+        cache = self.__dict__.setdefault("_subsets", {})
+        if n not in cache:
+            from types import SimpleNamespace
+            ang = self.view_angles()
+            base = {k: getattr(self.desc, k) for k in ("nx", "ny", "pixel", "det_spacing", "det_width", "d_po",
+                                                       "d_ps", "center_x", "center_y", "det_offset")}
+            base["n_det"] = self.n_det
+            base["detector"] = getattr(self.desc, "detector", "flat")
+            views = [list(range(s, self.n_views, n)) for s in range(n)]
+            geoms = [Geometry(SimpleNamespace(n_views=len(v), angles=[ang[t] for t in v], **base), device=self.device)
+                     for v in views]
+            cache[n] = (geoms, [t for v in views for t in v])
+        return cache[n]
 
     @property
     def image_shape(self):
@@ -226,6 +249,50 @@ def cgls(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[torch.Tens
     """CGLS iterations (device); x0 (updated in place) or zeros.  resume=True continues the
     iteration whose state ``ws`` holds (x0 must be its result)."""
     return _solver("cnsf_cgls", lib.cnsf_cgls, geom, sino, iters, x0, ws, stream, (1 if resume else 0,))
+
+
+ASD_POCS_DEFAULTS = dict(tv_steps=20, relax=1.0, relax_red=0.995, alpha=0.2, alpha_red=0.95, r_max=0.95,
+                        data_tol=0.0, tv_eps=1e-4)
+
+
+def asd_pocs(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[torch.Tensor] = None,
+             subsets: int = 1, projector: str = "cnsf", stream=None, **params) -> torch.Tensor:
+    """ASD-POCS (Sidky & Pan) on the device: ``iters`` sweeps of the data step over
+    ``subsets`` interleaved ordered subsets of views, each followed by adaptive TV steepest
+    descent; ``projector`` "cnsf" or "ref" (the reference projector's exact entries).
+    x0 (updated in place) or zeros; ``params`` override ASD_POCS_DEFAULTS."""
+    p = dict(ASD_POCS_DEFAULTS)
+    unknown = set(params) - set(p)
+    if unknown:
+        raise TypeError(f"asd_pocs: unknown parameters {sorted(unknown)}")
+    p.update(params)
+    if sino.shape != geom.sino_shape:
+        raise ValueError(f"asd_pocs: sinogram shape {tuple(sino.shape)}, expected {geom.sino_shape}")
+    if projector not in ("cnsf", "ref"):
+        raise ValueError("asd_pocs: projector is 'cnsf' or 'ref'")
+    sino = sino.contiguous()
+    code = _dtype_code(sino.dtype)
+    x = torch.zeros(geom.image_shape, dtype=sino.dtype, device=geom.device) if x0 is None else x0
+    if x.shape != geom.image_shape or x.dtype != sino.dtype or not x.is_contiguous() or x.device != sino.device:
+        raise ValueError("asd_pocs: bad x0")
+    geoms, rows = geom.subsets(int(subsets))
+    handles = (ctypes.c_void_p * len(geoms))(*[g.handle.value for g in geoms])
+    rows_c = (ctypes.c_int32 * len(rows))(*rows)
+    P = AsdPocsParams(int(iters), int(p["tv_steps"]), float(p["relax"]), float(p["relax_red"]), float(p["alpha"]),
+                      float(p["alpha_red"]), float(p["r_max"]), float(p["data_tol"]), float(p["tv_eps"]),
+                      0 if projector == "cnsf" else 1)
+    n = int(lib.cnsf_asd_pocs_workspace_bytes(handles, len(geoms), code))
+    if n == 0:
+        raise CnsfError(1, "cnsf_asd_pocs_workspace_bytes", lib)
+    buf = torch.empty(n + 256, dtype=torch.uint8, device=geom.device)
+    ptr = buf.data_ptr() + (-buf.data_ptr()) % 256
+    with torch.cuda.device(geom.device):
+        check(lib.cnsf_asd_pocs(handles, len(geoms), rows_c, ctypes.c_void_p(sino.data_ptr()),
+                                ctypes.c_void_p(x.data_ptr()), ctypes.byref(P), code, ctypes.c_void_p(ptr), n,
+                                ctypes.c_void_p(_stream_ptr(stream, geom.device))), "cnsf_asd_pocs")
+        # the workspace is released stream-ordered: keep it alive until the work is done
+        buf.record_stream(torch.cuda.current_stream(geom.device) if stream is None else stream)
+    return x
 
 
 class Projector(torch.autograd.Function):

@@ -24,6 +24,16 @@ class GeometryDesc(ctypes.Structure):
     ]
 
 
+class AsdPocsParams(ctypes.Structure):
+    """Mirror of cnsf_asd_pocs_params (include/cnsf.h)."""
+    _fields_ = [
+        ("iters", ctypes.c_int32), ("tv_steps", ctypes.c_int32),
+        ("relax", ctypes.c_double), ("relax_red", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("alpha_red", ctypes.c_double), ("r_max", ctypes.c_double), ("data_tol", ctypes.c_double),
+        ("tv_eps", ctypes.c_double), ("projector", ctypes.c_int32),
+    ]
+
+
 CNSF_OK, CNSF_ERR_INVALID, CNSF_ERR_CUDA, CNSF_ERR_NOMEM, CNSF_ERR_UNSUPPORTED, CNSF_ERR_INTERNAL = range(6)
 CNSF_F32, CNSF_F64 = 0, 1
 CNSF_DETECTOR = {"flat": 0, "arc": 1, "parallel": 2}
@@ -44,6 +54,9 @@ _SIGNATURES = {
                                  _P]),
     "cnsf_cgls": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t,
                                  _P]),
+    "cnsf_asd_pocs_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32]),
+    "cnsf_asd_pocs": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P, _P,
+                                     ctypes.POINTER(AsdPocsParams), ctypes.c_int32, _P, ctypes.c_size_t, _P]),
     "cnsf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cnsf_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -2,9 +2,12 @@
 // error translation around the kernel launchers.  No exception crosses this boundary.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <new>
+#include <vector>
 
 #include "cnsf.h"
 #include "cnsf_internal.cuh"
@@ -162,6 +165,75 @@ int cnsf_cgls(const cnsf_geometry *geom, const void *sino, void *image, int32_t 
               void *ws, size_t ws_bytes, void *stream)
 {
     return solver_call(geom, 1, sino, image, iters, 1.0, resume, dtype, ws, ws_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Subsets must share everything but their views, live on the current device, and the rows
+// must be a permutation of the total views.
+int check_subsets(const cnsf_geometry *const *sub, int32_t nsub)
+{
+    if (!sub || nsub < 1) return CNSF_ERR_INVALID;
+    for (int k = 0; k < nsub; ++k) {
+        if (!sub[k]) return CNSF_ERR_INVALID;
+        const GeomConsts &a = sub[0]->gc, &b = sub[k]->gc;
+        if (a.nx != b.nx || a.ny != b.ny || a.nd != b.nd || a.h != b.h || a.cx != b.cx || a.cy != b.cy ||
+            a.ds != b.ds || a.tau != b.tau || a.doff != b.doff || a.dpo != b.dpo || a.dps != b.dps ||
+            a.par != b.par || a.arc != b.arc || sub[k]->device != sub[0]->device)
+            return CNSF_ERR_INVALID;
+    }
+    return check_device(sub[0]);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cnsf_asd_pocs_workspace_bytes(const cnsf_geometry *const *subsets, int32_t n_subsets, int32_t dtype)
+{
+    try {
+        if (dtype != CNSF_F32 && dtype != CNSF_F64) return 0;
+        if (!subsets || n_subsets < 1) return 0;
+        for (int k = 0; k < n_subsets; ++k)
+            if (!subsets[k]) return 0;
+        return asd_workspace_bytes(subsets, n_subsets, dtype);
+    } catch (...) {
+        return 0;
+    }
+}
+
+int cnsf_asd_pocs(const cnsf_geometry *const *subsets, int32_t n_subsets, const int32_t *rows, const void *sino,
+                  void *image, const cnsf_asd_pocs_params *params, int32_t dtype, void *ws, size_t ws_bytes,
+                  void *stream)
+{
+    try {
+        int s = check_subsets(subsets, n_subsets);
+        if (s != CNSF_OK) return s;
+        if (!rows || !sino || !image || !params || (dtype != CNSF_F32 && dtype != CNSF_F64)) return CNSF_ERR_INVALID;
+        const cnsf_asd_pocs_params &P = *params;
+        if (P.iters < 0 || P.tv_steps < 0 || !(P.relax > 0.0 && P.relax < 2.0) ||
+            !(P.relax_red > 0.0 && P.relax_red <= 1.0) || !(P.alpha >= 0.0) ||
+            !(P.alpha_red > 0.0 && P.alpha_red <= 1.0) || !(P.r_max > 0.0) || !(P.tv_eps >= 0.0) ||
+            !std::isfinite(P.data_tol) || (P.projector != CNSF_PROJECTOR_CNSF && P.projector != CNSF_PROJECTOR_REF))
+            return CNSF_ERR_INVALID;
+        long long total = 0;
+        for (int k = 0; k < n_subsets; ++k) total += subsets[k]->gc.nv;
+        std::vector<char> seen((size_t)total, 0);
+        std::vector<int> rows_copy((size_t)total);   // pageable: the upload is staged before return
+        for (long long t = 0; t < total; ++t) {
+            if (rows[t] < 0 || rows[t] >= total || seen[(size_t)rows[t]]) return CNSF_ERR_INVALID;
+            seen[(size_t)rows[t]] = 1;
+            rows_copy[(size_t)t] = rows[t];
+        }
+        return run_asd_pocs(subsets, n_subsets, rows_copy.data(), sino, image, P, dtype, ws, ws_bytes,
+                            (cudaStream_t)stream);
+    } catch (const std::bad_alloc &) {
+        return CNSF_ERR_NOMEM;
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
 }
 
 const char *cnsf_status_string(int status)

@@ -261,6 +261,245 @@ static int cgls_impl(const cnsf_geometry *geo, const T *y, T *x, int iters, int 
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
+// ================================================================ ASD-POCS
+// Adaptive steepest descent POCS (Sidky & Pan 2008), the reconstruction method of Sec. IV-E.
+// One outer iteration: a data-consistency sweep over the ordered subsets of views
+// (x += beta C_s A_s^T R_s (y_s - A_s x), then x = max(x, 0)), then tv_steps normalised
+// steepest-descent steps on the smoothed TV, with the TV step length adapted from the sizes
+// of the two moves.  All control scalars (beta, the TV step, the norms) live on the device, so
+// the whole loop is launched without a host round trip.
+
+// workspace: [ scal | part | rows | ysub | R | rbuf | C (S images) | gr | xprev | xdata | d ]
+struct AsdWs {
+    double *scal;   // [0] beta, [1] TV step, [2] dp^2, [3] dd^2, [4] |grad TV|^2, [5] dg^2
+    double *part;
+    int *rows;
+    void *ysub, *R, *rbuf, *C, *gr, *xprev, *xdata, *d;
+};
+
+static size_t asd_layout(const cnsf_geometry *const *sub, int nsub, int dtype, AsdWs *w, void *base)
+{
+    const GeomConsts &g = sub[0]->gc;
+    size_t el = dtype == CNSF_F64 ? sizeof(double) : sizeof(float);
+    size_t rows = 0;
+    for (int k = 0; k < nsub; ++k) rows += (size_t)sub[k]->gc.nv;
+    const size_t ns = rows * g.nd, ni = (size_t)g.nx * g.ny;
+    size_t off = 0;
+    size_t o_scal = off; off += align256(8 * sizeof(double));
+    size_t o_part = off; off += align256(RED_BLOCKS * sizeof(double));
+    size_t o_rows = off; off += align256(rows * sizeof(int));
+    size_t o_y = off; off += align256(ns * el);
+    size_t o_R = off; off += align256(ns * el);
+    size_t o_rb = off; off += align256(ns * el);
+    size_t o_C = off; off += align256((size_t)nsub * ni * el);
+    size_t o_gr = off; off += align256(ni * el);
+    size_t o_xp = off; off += align256(ni * el);
+    size_t o_xd = off; off += align256(ni * el);
+    size_t o_d = off; off += align256(ni * el);
+    if (w && base) {
+        char *b = (char *)base;
+        w->scal = (double *)(b + o_scal);
+        w->part = (double *)(b + o_part);
+        w->rows = (int *)(b + o_rows);
+        w->ysub = b + o_y; w->R = b + o_R; w->rbuf = b + o_rb; w->C = b + o_C;
+        w->gr = b + o_gr; w->xprev = b + o_xp; w->xdata = b + o_xd; w->d = b + o_d;
+    }
+    return off;
+}
+
+size_t asd_workspace_bytes(const cnsf_geometry *const *sub, int nsub, int dtype)
+{
+    return asd_layout(sub, nsub, dtype, nullptr, nullptr);
+}
+
+// ysub[t][:] = y[rows[t]][:]
+template <typename T>
+__global__ void gather_rows_kernel(const T *__restrict__ y, const int *__restrict__ rows, T *__restrict__ ysub,
+                                   size_t nrows, int nd)
+{
+    const size_t n = nrows * nd;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t t = i / nd;
+        ysub[i] = y[(size_t)rows[t] * nd + (i - t * nd)];
+    }
+}
+
+// x += beta C g with beta = scal[0]; the last subset of a sweep also clips x to >= 0
+template <typename T>
+__global__ void asd_update_kernel(T *x, const T *__restrict__ g, const T *__restrict__ C, size_t n,
+                                  const double *__restrict__ scal, int clip)
+{
+    const T beta = (T)scal[0];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const T v = x[i] + beta * C[i] * g[i];
+        x[i] = clip ? (v > T(0) ? v : T(0)) : v;
+    }
+}
+
+// sum of (a - b)^2, deterministic partials as sumsq_partial_kernel
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) diffsq_partial_kernel(const T *__restrict__ a, const T *__restrict__ b,
+                                                                     size_t n, double *__restrict__ part)
+{
+    __shared__ double sh[RED_THREADS];
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < n; i += (size_t)RED_BLOCKS * RED_THREADS) {
+        const double v = (double)a[i] - (double)b[i];
+        s = fma(v, v, s);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// Gradient of TV(x) = sum sqrt(eta^2 + Dx^2 + Dy^2), backward differences that vanish across
+// the image border: a pixel enters its own term and, with a minus sign, those of its right
+// and lower neighbours.
+template <typename T>
+__global__ void tv_grad_kernel(const T *__restrict__ x, T *__restrict__ d, int nx, int ny, T eta2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || r >= ny) return;
+    const size_t c = (size_t)r * nx + i;
+    const T v = x[c];
+    const T dx = i > 0 ? v - x[c - 1] : T(0), dy = r > 0 ? v - x[c - nx] : T(0);
+    T gsum = (dx + dy) / sqrt(eta2 + dx * dx + dy * dy);
+    if (i + 1 < nx) {
+        const T vr = x[c + 1];
+        const T ex = vr - v, ey = r > 0 ? vr - x[c + 1 - nx] : T(0);
+        gsum -= ex / sqrt(eta2 + ex * ex + ey * ey);
+    }
+    if (r + 1 < ny) {
+        const T vd = x[c + nx];
+        const T ex = i > 0 ? vd - x[c + nx - 1] : T(0), ey = vd - v;
+        gsum -= ey / sqrt(eta2 + ex * ex + ey * ey);
+    }
+    d[c] = gsum;
+}
+
+// x -= step d / |d| (step = scal[1], |d|^2 = scal[4]); nothing when d = 0
+template <typename T>
+__global__ void tv_step_kernel(T *x, const T *__restrict__ d, size_t n, const double *__restrict__ scal)
+{
+    const double nd2 = scal[4];
+    if (!(nd2 > 0.0)) return;
+    const T f = (T)(scal[1] / sqrt(nd2));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] -= f * d[i];
+}
+
+__global__ void asd_start_kernel(double *scal, double relax)
+{
+    scal[0] = relax;
+    scal[1] = 0.0;
+}
+
+// first iteration: TV step = alpha dp
+__global__ void asd_first_kernel(double *scal, double alpha) { scal[1] = alpha * sqrt(scal[2]); }
+
+// after the TV steps: shrink the TV step when the TV move outgrew the data move (while the
+// data residual is above its tolerance), and relax the data step
+__global__ void asd_adapt_kernel(double *scal, double r_max, double alpha_red, double data_tol, double relax_red)
+{
+    const double dp = sqrt(scal[2]), dd = sqrt(scal[3]), dg = sqrt(scal[5]);
+    if (dg > r_max * dp && (data_tol <= 0.0 || dd > data_tol)) scal[1] *= alpha_red;
+    scal[0] *= relax_red;
+}
+
+template <typename T>
+static void diffsq(const T *a, const T *b, size_t n, double *part, double *dst, cudaStream_t st)
+{
+    diffsq_partial_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(a, b, n, part);
+    sum_final_kernel<<<1, RED_THREADS, 0, st>>>(part, dst);
+}
+
+typedef int (*ProjFn)(const cnsf_geometry *, const void *, void *, int, int, cudaStream_t);
+
+template <typename T>
+static int asd_impl(const cnsf_geometry *const *sub, int nsub, const int *rows_host, const T *y, T *x,
+                    const cnsf_asd_pocs_params &P, int dtype, AsdWs &w, cudaStream_t st)
+{
+    const GeomConsts &g = sub[0]->gc;
+    const ProjFn fwd = P.projector == CNSF_PROJECTOR_REF ? launch_forward_ref : launch_forward;
+    const ProjFn bwd = P.projector == CNSF_PROJECTOR_REF ? launch_back_ref : launch_back;
+    const size_t ni = (size_t)g.nx * g.ny;
+    size_t nrows = 0;
+    for (int k = 0; k < nsub; ++k) nrows += (size_t)sub[k]->gc.nv;
+    const size_t ns = nrows * g.nd;
+    T *ysub = (T *)w.ysub, *R = (T *)w.R, *rb = (T *)w.rbuf, *C = (T *)w.C, *gr = (T *)w.gr;
+    T *xprev = (T *)w.xprev, *xdata = (T *)w.xdata, *d = (T *)w.d;
+    cudaError_t e = cudaMemcpyAsync(w.rows, rows_host, nrows * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    gather_rows_kernel<T><<<grid_for(ns), 256, 0, st>>>(y, w.rows, ysub, nrows, g.nd);
+    // per subset: R_s = 1/(A_s 1), C_s = 1/(A_s^T 1)
+    int s;
+    size_t off = 0;
+    for (int k = 0; k < nsub; ++k) {
+        const size_t nk = (size_t)sub[k]->gc.nv * g.nd;
+        fill_kernel<T><<<grid_for(ni), 256, 0, st>>>(gr, ni, T(1));
+        if ((s = fwd(sub[k], gr, R + off, 1, dtype, st)) != CNSF_OK) return s;
+        recip_kernel<T><<<grid_for(nk), 256, 0, st>>>(R + off, nk);
+        fill_kernel<T><<<grid_for(nk), 256, 0, st>>>(rb + off, nk, T(1));
+        if ((s = bwd(sub[k], rb + off, C + k * ni, 1, dtype, st)) != CNSF_OK) return s;
+        recip_kernel<T><<<grid_for(ni), 256, 0, st>>>(C + k * ni, ni);
+        off += nk;
+    }
+    asd_start_kernel<<<1, 1, 0, st>>>(w.scal, P.relax);
+    const dim3 tvb(16, 16), tvg((g.nx + 15) / 16, (g.ny + 15) / 16);
+    const T eta2 = (T)(P.tv_eps * P.tv_eps);
+    for (int it = 0; it < P.iters; ++it) {
+        if ((e = cudaMemcpyAsync(xprev, x, ni * sizeof(T), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return record_cuda_error(e);
+        off = 0;
+        for (int k = 0; k < nsub; ++k) {   // data-consistency sweep over the ordered subsets
+            const size_t nk = (size_t)sub[k]->gc.nv * g.nd;
+            if ((s = fwd(sub[k], x, rb + off, 1, dtype, st)) != CNSF_OK) return s;
+            sirt_residual_kernel<T><<<grid_for(nk), 256, 0, st>>>(rb + off, ysub + off, R + off, nk);
+            if ((s = bwd(sub[k], rb + off, gr, 1, dtype, st)) != CNSF_OK) return s;
+            asd_update_kernel<T><<<grid_for(ni), 256, 0, st>>>(x, gr, C + k * ni, ni, w.scal, k == nsub - 1);
+            off += nk;
+        }
+        diffsq<T>(x, xprev, ni, w.part, w.scal + 2, st);
+        if (P.data_tol > 0.0) {
+            off = 0;
+            for (int k = 0; k < nsub; ++k) {
+                if ((s = fwd(sub[k], x, rb + off, 1, dtype, st)) != CNSF_OK) return s;
+                off += (size_t)sub[k]->gc.nv * g.nd;
+            }
+            diffsq<T>(rb, ysub, ns, w.part, w.scal + 3, st);
+        }
+        if (it == 0) asd_first_kernel<<<1, 1, 0, st>>>(w.scal, P.alpha);
+        if ((e = cudaMemcpyAsync(xdata, x, ni * sizeof(T), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return record_cuda_error(e);
+        for (int m = 0; m < P.tv_steps; ++m) {
+            tv_grad_kernel<T><<<tvg, tvb, 0, st>>>(x, d, g.nx, g.ny, eta2);
+            sumsq_partial_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(d, ni, w.part);
+            sum_final_kernel<<<1, RED_THREADS, 0, st>>>(w.part, w.scal + 4);
+            tv_step_kernel<T><<<grid_for(ni), 256, 0, st>>>(x, d, ni, w.scal);
+        }
+        diffsq<T>(x, xdata, ni, w.part, w.scal + 5, st);
+        asd_adapt_kernel<<<1, 1, 0, st>>>(w.scal, P.r_max, P.alpha_red, P.data_tol, P.relax_red);
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
+int run_asd_pocs(const cnsf_geometry *const *sub, int nsub, const int *rows, const void *sino, void *image,
+                 const cnsf_asd_pocs_params &P, int dtype, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    if (!ws || ws_bytes < asd_workspace_bytes(sub, nsub, dtype) || ((uintptr_t)ws & 255u) != 0)
+        return CNSF_ERR_INVALID;
+    AsdWs w;
+    asd_layout(sub, nsub, dtype, &w, ws);
+    return dtype == CNSF_F64
+               ? asd_impl<double>(sub, nsub, rows, (const double *)sino, (double *)image, P, dtype, w, st)
+               : asd_impl<float>(sub, nsub, rows, (const float *)sino, (float *)image, P, dtype, w, st);
+}
+
 int run_solver(const cnsf_geometry *geo, int algo, const void *sino, void *image, int iters, double relax,
                int resume, int dtype, void *ws, size_t ws_bytes, cudaStream_t st)
 {

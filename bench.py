@@ -311,6 +311,7 @@ def run_cnsf(args):
         line["batch16_512x360"] = bench_batch16(dev)
         line["e4_ladder"] = bench_e4_ladder(dev)
         line["reference_projector"] = bench_reference(dev)
+        line["asd_pocs_limited_view"] = bench_asd_pocs(dev)
         line["p50_recon_latency_s"] = line["serving"]["continuous"].get("p50_s")
         line["p99_recon_latency_s"] = line["serving"]["continuous"].get("p99_s")
     if rank == 0 and not args.no_cpu_baseline:
@@ -471,6 +472,42 @@ def bench_reference(dev):
         out[f"{n}mm_{n_det}cells_tau0.5_D{int(d)}"] = {
             "max_abs_err": float((ya - yr).abs().max()), "peak": float(yr.abs().max()),
             "rel_l2": float((ya - yr).norm() / yr.norm())}
+    return out
+
+
+def bench_asd_pocs(dev, iters: int = 200):
+    """The limited-view reconstructions of Sec. IV-E: data from the reference projector,
+    ASD-POCS (one subset per view, Sidky-Pan parameters) with the CNSF and with the exact
+    entries, and SIRT with the same number of projector calls; SNR in dB and device time."""
+    import math
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import E5_CASES, e5_geometry, ellipse_phantom
+
+    def snr(x, t):
+        return 10.0 * math.log10(float((t * t).sum()) / float(((x - t) ** 2).sum()))
+
+    out = {}
+    for (n, views, n_det, d) in E5_CASES:
+        g = e5_geometry(n)
+        geom = cnsf.Geometry(g)
+        xt = torch.tensor(ellipse_phantom(n, 10, 1.0, seed=16 + n), dtype=torch.float64, device=dev)
+        y = cnsf.forward_project_ref(geom, xt)
+        res = {"iters": iters, "subsets": views, "phantom": "random ellipses (10), seed %d" % (16 + n)}
+        runs = [("cnsf_f32", {}, torch.float32)]
+        if n == E5_CASES[0][0]:   # the FP64 runs (tens of seconds at the larger case) on the first case only
+            runs += [("cnsf_f64", {}, torch.float64), ("ref_f64", {"projector": "ref"}, torch.float64)]
+        for name, kw, dt in runs:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record()
+            x = cnsf.asd_pocs(geom, y.to(dt), iters, subsets=views, **kw)
+            ev[1].record()
+            torch.cuda.synchronize()
+            res[name] = {"snr_db": snr(x.double(), xt), "seconds": ev[0].elapsed_time(ev[1]) * 1e-3}
+        xs = cnsf.sirt(geom, y.float(), iters * views)
+        res["sirt_f32_same_projector_calls"] = {"snr_db": snr(xs.double(), xt)}
+        out[f"{n}mm_{views}views_{n_det}cells_D{int(d)}"] = res
     return out
 
 

@@ -112,6 +112,19 @@ def e3_geometry(n: int) -> FanGeometry:
     raise ValueError(f"no accuracy case of size {n}")
 
 
+# Limited-view reconstructions of the paper's Sec. IV-E: n mm images, V views over 360 deg,
+# cells of 1 mm pitch and width, D_po = D_so; the paper's Shepp-Logan and brain phantoms are
+# stood in for by random-ellipse phantoms.
+E5_CASES = ((128, 16, 409, 200.0), (256, 30, 815, 400.0))
+
+
+def e5_geometry(n: int) -> FanGeometry:
+    for (m, views, n_det, d) in E5_CASES:
+        if m == n:
+            return FanGeometry(nx=n, ny=n, n_views=views, n_det=n_det, d_po=d, d_ps=2.0 * d)
+    raise ValueError(f"no limited-view case of size {n}")
+
+
 def serving_geometry(n: int, n_views: int) -> FanGeometry:
     """Geometry of one serving request: n x n image, n_det = round(1.75 n)."""
     d_po, d_ps = scaled_distances(n)

@@ -59,8 +59,7 @@ __device__ __forceinline__ float bp_sigma(const TV &T, float di, float dr, float
 template <bool ARC>
 __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, float di, float dr,
                                               const BpArgs &a, int nd, const float2 *__restrict__ y2row,
-                                              const float4 *__restrict__ box2row, const float4 *__restrict__ cell2,
-                                              const float2 *__restrict__ cellc2)
+                                              const float *__restrict__ boxrow, const float *__restrict__ cell2)
 {
     const float Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));   // depth along u
     const float yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));    // coordinate along w
@@ -85,19 +84,19 @@ __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, 
     const float d0 = sig - (float)(2 * m0 - J);
     float2 d = make_float2(d0, d0 - 1.f);
     for (int m = m0; m <= m1; ++m) {
-        const float4 A0 = __ldg(box2row + 2 * m), A1 = __ldg(box2row + 2 * m + 1);   // p, q/C | 1/C, -C/2
-        const float4 C0 = __ldg(cell2 + m);                                          // g1 | c1
-        const float2 c2 = __ldg(cellc2 + m);
+        float A[8], C[8];
+        ldg256(boxrow + 8 * m, A);    // p | q/C | 1/C | -C/2, pairs
+        ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
         const float2 yv = __ldg(y2row + m);
         float2 xs;
         if (ARC)
             xs = __fmul2_rn(__fmul2_rn(G2, d), __ffma2_rn(__fmul2_rn(d, d), k2, make_float2(1.f, 1.f)));
         else
-            xs = __fmul2_rn(__fmul2_rn(Dn2, make_float2(C0.x, C0.y)), d);
+            xs = __fmul2_rn(__fmul2_rn(Dn2, make_float2(C[0], C[1])), d);
         const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
-        const float2 e = __ffma2_rn(Dn2, make_float2(C0.z, C0.w), __fmul2_rn(yp2, c2));         // tau'/2
-        const float2 p = make_float2(A0.x, A0.y), nhC = make_float2(A1.z, A1.w);
-        const float2 w = window_diff2p(x, e, ne1, p, make_float2(A0.z, A0.w), make_float2(A1.x, A1.y), nhC);
+        const float2 e = __ffma2_rn(Dn2, make_float2(C[2], C[3]), __fmul2_rn(yp2, make_float2(C[4], C[5])));
+        const float2 p = make_float2(A[0], A[1]), nhC = make_float2(A[6], A[7]);
+        const float2 w = window_diff2p(x, e, ne1, p, make_float2(A[2], A[3]), make_float2(A[4], A[5]), nhC);
         const float2 den = __fmul2_rn(__ffma2_rn(nhC, ne1, p), e);                              // (p + C/2) e
         acc = __ffma2_rn(yv, make_float2(w.x * rcp_approx(den.x), w.y * rcp_approx(den.y)), acc);
         d = __fadd2_rn(d, m2);
@@ -107,9 +106,8 @@ __device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, 
 
 template <bool ARC>
 __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double *__restrict__ view_cs,
-                                                     const float4 *__restrict__ box2,
-                                                     const float4 *__restrict__ cell2,
-                                                     const float2 *__restrict__ cellc2,
+                                                     const float *__restrict__ box2,
+                                                     const float *__restrict__ cell2,
                                                      const float2 *__restrict__ y2, float *__restrict__ img,
                                                      BpArgs a, const int *__restrict__ order, int ntx, int nsplit,
                                                      float *__restrict__ partial)
@@ -153,7 +151,7 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
             for (int vv = 0; vv < nvc; ++vv) {
                 const int v = v0 + vv;
                 part = __fadd2_rn(part, bp_view_f32<ARC>(tv[vv], tj[vv], di, dr, a, g.nd, y + (long long)v * ndh,
-                                                    box2 + 2 * (long long)v * ndh, cell2, cellc2));
+                                                         box2 + 8 * (long long)v * ndh, cell2));
                 if ((vv & 15) == 15) {   // blocked summation over groups of 16 views
                     acc = __fadd2_rn(acc, part);
                     part = make_float2(0.f, 0.f);
@@ -309,8 +307,7 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         }
         auto kern = g.arc ? bp_f32_kernel<true> : bp_f32_kernel<false>;
         kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_T * BP_T), 0, st>>>(
-            g, geo->d_view_cs, reinterpret_cast<const float4 *>(geo->d_box2),
-            reinterpret_cast<const float4 *>(geo->d_cell2), geo->d_cellc2, y2, (float *)img, a, geo->d_bp_order,
+            g, geo->d_view_cs, geo->d_box2, geo->d_cell2, y2, (float *)img, a, geo->d_bp_order,
             (int)grd.x, nsplit, partial);
         if (copy) cudaFreeAsync(copy, st);
         if (nsplit > 1) {

@@ -241,17 +241,12 @@ struct alignas(16) CellF {
 };
 
 // Pair constants of the FP32 back projector: entry m holds cells 2m and 2m + 1 side by
-// side, so one 16-byte load gives two cells' values as FP32 pairs for the packed (FFMA2)
-// arithmetic, with no value stored twice.  n_det is padded to even; a padding cell repeats
-// the last cell's constants (its sinogram value is 0).  The view-dependent trapezoid
-// constants and the view-independent cell slopes are separate tables, so the latter (a
-// few KB) stay in L1 across views.
-struct alignas(16) BoxPairF {
-    float p[2], qiC[2], iC[2], nhC[2];   // (B - C)/2, q/C, 1/C (clamped), -C/2
-};
-struct alignas(16) CellPairF {
-    float g1[2], c1[2];                  // ds/L_j, D_ps dtan_j/(2 L_j)
-};
+// side, so the two cells' values come as FP32 pairs for the packed (FFMA2) arithmetic.
+// n_det is padded to even; a padding cell repeats the last cell's constants (its sinogram
+// value is 0).  Each entry is 32 bytes, read with one 256-bit load: per (view, pair) the
+// trapezoid constants (p, q/C, 1/C, -C/2 of both cells), per pair the view-independent
+// cell slopes (ds/L_j, cos(g_j) dtan_j/2, sin(g_j) dtan_j/2 of both cells), a table of a
+// few KB that stays in L1 across views.
 
 // Back-projector cell window (cells) of a pixel at depth D_n, coordinate y' along w:
 //   hwc = kz * h(|y' c - D_n s| + |y' s + D_n c|) / D_n^2 * (1.02 + 2 h / D_n) + ke
@@ -276,9 +271,8 @@ struct cnsf_geometry {
     double *d_cell_d;         // [nd][4] sin(g_j), cos(g_j), dtan_j, s_j (FP64; parallel: 0, 1, 0, s_j)
     cnsf::BoxF *d_box;        // [nv][nd]
     cnsf::CellF *d_cellf;     // [nd]
-    cnsf::BoxPairF *d_box2;   // [nv][ceil(n_det/2)]
-    cnsf::CellPairF *d_cell2; // [ceil(n_det/2)]
-    float2 *d_cellc2;         // [ceil(n_det/2)]  s_j dtan_j/(2 L_j) of cells 2m, 2m + 1
+    float *d_box2;            // [nv][ceil(n_det/2)][8]: p, q/C, 1/C, -C/2 of cells 2m, 2m + 1
+    float *d_cell2;           // [ceil(n_det/2)][8]: ds/L, c1, c2 of cells 2m, 2m + 1, 0, 0
     // launch orders, heaviest blocks first (so that the tail of the grid is short work)
     int *d_fp_order;          // [ceil(nv*nd/128)] forward blocks of 128 rays
     int *d_bp_order;          // [ceil(nx/16)*ceil(ny/16)] back-projection tiles

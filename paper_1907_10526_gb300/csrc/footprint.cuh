@@ -46,6 +46,15 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// 32 bytes from global memory through the read-only path in one 256-bit load (sm_100+);
+// p must be 32-byte aligned.
+__device__ __forceinline__ void ldg256(const float *p, float (&r)[8])
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+        : "l"(p));
+}
+
 // Two entries at once with the packed FP32 instructions of sm_100+ (FADD2/FMUL2/FFMA2):
 // the same arithmetic as window_diff, lane by lane, for candidates that share the
 // trapezoid constants (p, q/C, 1/C, C/2 given as pairs).  min, saturate and sign

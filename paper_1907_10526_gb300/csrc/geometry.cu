@@ -163,23 +163,26 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     }
     // even-aligned cell pairs for the back projector
     const int ndh = (nd + 1) / 2;
-    std::vector<BoxPairF> box2((size_t)nv * ndh);
-    std::vector<CellPairF> cell2(ndh);
-    std::vector<float> cellc2(2 * (size_t)ndh);
+    // 32 bytes per cell pair (read with one 256-bit load): trapezoid constants
+    // (p, p, q/C, q/C, 1/C, 1/C, -C/2, -C/2) per (view, pair); cell slopes
+    // (ds/L, ds/L, c1, c1, c2, c2, 0, 0) per pair
+    const size_t npairs = (size_t)nv * ndh;
+    std::vector<float> box2(8 * npairs);
+    std::vector<float> cell2(8 * (size_t)ndh, 0.0f);
     for (int k = 0; k < nv; ++k)
         for (int m = 0; m < ndh; ++m) {
-            BoxPairF &P = box2[(size_t)k * ndh + m];
+            float *A = &box2[8 * ((size_t)k * ndh + m)];
             for (int h = 0; h < 2; ++h) {
                 const BoxF &b = box[(size_t)k * nd + std::min(2 * m + h, nd - 1)];
-                P.p[h] = b.p; P.qiC[h] = b.qiC; P.iC[h] = b.iC; P.nhC[h] = -b.hC;
+                A[h] = b.p; A[2 + h] = b.qiC; A[4 + h] = b.iC; A[6 + h] = -b.hC;
             }
         }
     for (int m = 0; m < ndh; ++m)
         for (int h = 0; h < 2; ++h) {
             const CellF &c = cellf[std::min(2 * m + h, nd - 1)];
-            cell2[m].g1[h] = c.g1;
-            cell2[m].c1[h] = c.c1;
-            cellc2[2 * m + h] = c.c2;
+            cell2[8 * m + h] = c.g1;
+            cell2[8 * m + 2 + h] = c.c1;
+            cell2[8 * m + 4 + h] = c.c2;
         }
     int pad = ((kc_max + 1 + 3) / 4) * 4;
     // The walk never leaves [-pad, na-1+pad]: windows that meet [0, na-1] are at most kc wide.
@@ -260,9 +263,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         {(void **)&geo->d_cell_d, celld.data(), celld.size() * sizeof(double)},
         {(void **)&geo->d_box, box.data(), box.size() * sizeof(BoxF)},
         {(void **)&geo->d_cellf, cellf.data(), cellf.size() * sizeof(CellF)},
-        {(void **)&geo->d_box2, box2.data(), box2.size() * sizeof(BoxPairF)},
-        {(void **)&geo->d_cell2, cell2.data(), cell2.size() * sizeof(CellPairF)},
-        {(void **)&geo->d_cellc2, cellc2.data(), cellc2.size() * sizeof(float)},
+        {(void **)&geo->d_box2, box2.data(), box2.size() * sizeof(float)},
+        {(void **)&geo->d_cell2, cell2.data(), cell2.size() * sizeof(float)},
         {(void **)&geo->d_ray, rays.data(), rays.size() * sizeof(RayF)},
         {(void **)&geo->d_fp_order, fp_order.data(), fp_order.size() * sizeof(int)},
         {(void **)&geo->d_bp_order, bp_order.data(), bp_order.size() * sizeof(int)},
@@ -284,7 +286,7 @@ void destroy_geometry(cnsf_geometry *geo)
 {
     if (!geo) return;
     void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray,
-                    geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2, geo->d_cellc2};
+                    geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete geo;

@@ -95,13 +95,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def _kernel_source_hash() -> str:
+# the sources each timed kernel is built from (its table builder included)
+KERNEL_SOURCES = {
+    "fp_f32_kernel": ("forward.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
+    "bp_f32_kernel": ("back.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
+}
+
+
+def _kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1907_10526_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in sorted(KERNEL_SOURCES[kernel]):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -114,7 +120,7 @@ def _recorded_traffic(kernel: str):
     except (OSError, ValueError):
         return None
     ent = rec.get(kernel)
-    if not ent or ent.get("source_hash") != _kernel_source_hash():
+    if not ent or kernel not in KERNEL_SOURCES or ent.get("source_hash") != _kernel_source_hash(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 

@@ -170,6 +170,20 @@ CNSF_API int cnsf_sirt(const cnsf_geometry *geom, const void *sino, void *image,
 CNSF_API int cnsf_cgls(const cnsf_geometry *geom, const void *sino, void *image, int32_t iters, int32_t resume,
                        int32_t dtype, void *ws, size_t ws_bytes, void *stream);
 
+/* CGLS on `batch` independent problems that share the geometry (the same A): sino device
+ * [batch][n_views][n_det], image device [batch][n_y][n_x] (x0 in, result out), each image
+ * with its own FP64 state and step lengths, the projections run once per iteration over
+ * the batch.  In FP32 the projections always take the batched kernels, whose arithmetic
+ * for one image does not depend on the batch's size or other members: an image's iterates
+ * are bitwise the same whichever problems it is batched with (they may differ from
+ * cnsf_cgls's at the FP32 rounding level).  Workspace: device, 256-byte aligned, of
+ * cnsf_cgls_batched_workspace_bytes; `resume` continues from the state it holds.
+ * batch in [0, 65535]. */
+CNSF_API size_t cnsf_cgls_batched_workspace_bytes(const cnsf_geometry *geom, int32_t batch, int32_t dtype);
+CNSF_API int cnsf_cgls_batched(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch,
+                               int32_t iters, int32_t resume, int32_t dtype, void *ws, size_t ws_bytes,
+                               void *stream);
+
 /* ASD-POCS (adaptive steepest descent POCS with total variation, Sidky & Pan 2008), the
  * reconstruction method of Sec. IV-E, on the device.  One outer iteration:
  *   1. a data-consistency sweep over the ordered subsets of views, subset by subset

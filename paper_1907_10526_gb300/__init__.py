@@ -19,7 +19,8 @@ from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, AsdPocsParams, CnsfError, G
 
 __all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
            "count_nonzeros", "forward_project_noalloc", "asd_pocs",
-           "sirt", "cgls", "SolverWorkspace", "Projector", "project", "CnsfError"]
+           "sirt", "cgls", "cgls_batched", "SolverWorkspace", "BatchedSolverWorkspace", "Projector", "project",
+           "CnsfError"]
 
 
 def _dtype_code(t: torch.dtype) -> int:
@@ -249,6 +250,44 @@ def cgls(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[torch.Tens
     """CGLS iterations (device); x0 (updated in place) or zeros.  resume=True continues the
     iteration whose state ``ws`` holds (x0 must be its result)."""
     return _solver("cnsf_cgls", lib.cnsf_cgls, geom, sino, iters, x0, ws, stream, (1 if resume else 0,))
+
+
+class BatchedSolverWorkspace:
+    """Device workspace of ``cgls_batched`` for ``batch`` problems (one call at a time); it
+    holds the CGLS state that ``resume=True`` continues from."""
+
+    def __init__(self, geom: Geometry, batch: int, dtype: torch.dtype = torch.float32):
+        self.geom, self.batch, self.dtype = geom, int(batch), dtype
+        n = int(lib.cnsf_cgls_batched_workspace_bytes(geom.handle, self.batch, _dtype_code(dtype)))
+        if n == 0:
+            raise CnsfError(1, "cnsf_cgls_batched_workspace_bytes", lib)
+        self.buf = torch.empty(n + 256, dtype=torch.uint8, device=geom.device)
+        self.ptr = self.buf.data_ptr() + (-self.buf.data_ptr()) % 256
+        self.nbytes = n
+
+
+def cgls_batched(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[torch.Tensor] = None,
+                 ws: Optional[BatchedSolverWorkspace] = None, resume: bool = False, stream=None) -> torch.Tensor:
+    """CGLS on a batch of sinograms [B, n_views, n_det] of one geometry (device); x0
+    [B, ny, nx] (updated in place) or zeros.  Each image's iterates do not depend on the
+    other members of the batch."""
+    if sino.dim() != 3 or tuple(sino.shape[1:]) != geom.sino_shape:
+        raise ValueError(f"cgls_batched: sinograms {tuple(sino.shape)}, expected [B, {geom.sino_shape}]")
+    B = int(sino.shape[0])
+    sino = sino.contiguous()
+    code = _dtype_code(sino.dtype)
+    x = torch.zeros((B,) + geom.image_shape, dtype=sino.dtype, device=geom.device) if x0 is None else x0
+    if x.shape != (B,) + geom.image_shape or x.dtype != sino.dtype or not x.is_contiguous() or x.device != sino.device:
+        raise ValueError("cgls_batched: bad x0")
+    if ws is None:
+        ws = BatchedSolverWorkspace(geom, B, sino.dtype)
+    if ws.batch != B or ws.dtype != sino.dtype:
+        raise ValueError("cgls_batched: workspace made for another batch or dtype")
+    with torch.cuda.device(geom.device):
+        check(lib.cnsf_cgls_batched(geom.handle, ctypes.c_void_p(sino.data_ptr()), ctypes.c_void_p(x.data_ptr()), B,
+                                    int(iters), 1 if resume else 0, code, ctypes.c_void_p(ws.ptr), ws.nbytes,
+                                    ctypes.c_void_p(_stream_ptr(stream, geom.device))), "cnsf_cgls_batched")
+    return x
 
 
 ASD_POCS_DEFAULTS = dict(tv_steps=20, relax=1.0, relax_red=0.995, alpha=0.2, alpha_red=0.95, r_max=0.95,

@@ -54,6 +54,9 @@ _SIGNATURES = {
                                  _P]),
     "cnsf_cgls": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t,
                                  _P]),
+    "cnsf_cgls_batched_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "cnsf_cgls_batched": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         _P, ctypes.c_size_t, _P]),
     "cnsf_asd_pocs_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int32]),
     "cnsf_asd_pocs": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P, _P,
                                      ctypes.POINTER(AsdPocsParams), ctypes.c_int32, _P, ctypes.c_size_t, _P]),

@@ -167,6 +167,25 @@ int cnsf_cgls(const cnsf_geometry *geom, const void *sino, void *image, int32_t 
     return solver_call(geom, 1, sino, image, iters, 1.0, resume, dtype, ws, ws_bytes, stream);
 }
 
+size_t cnsf_cgls_batched_workspace_bytes(const cnsf_geometry *geom, int32_t batch, int32_t dtype)
+{
+    if (!geom || batch < 0 || batch > 65535 || (dtype != CNSF_F32 && dtype != CNSF_F64)) return 0;
+    return cgls_batched_workspace_bytes(geom, batch, dtype);
+}
+
+int cnsf_cgls_batched(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch, int32_t iters,
+                      int32_t resume, int32_t dtype, void *ws, size_t ws_bytes, void *stream)
+{
+    try {
+        int s = check_call(geom, sino, image, batch, dtype);
+        if (s != CNSF_OK) return s;
+        if (iters < 0) return CNSF_ERR_INVALID;
+        return run_cgls_batched(geom, sino, image, batch, iters, resume, dtype, ws, ws_bytes, (cudaStream_t)stream);
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
 }  // extern "C"
 
 namespace {

@@ -39,6 +39,10 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
 
 // Iterative drivers (solver.cu): algo 0 = SIRT, 1 = CGLS.
 size_t solver_workspace_bytes(const cnsf_geometry *geo, int dtype);
+// CGLS over a batch of problems with one geometry (solver.cu).
+size_t cgls_batched_workspace_bytes(const cnsf_geometry *geo, int batch, int dtype);
+int run_cgls_batched(const cnsf_geometry *geo, const void *sino, void *image, int batch, int iters, int resume,
+                     int dtype, void *ws, size_t ws_bytes, cudaStream_t stream);
 // ASD-POCS (solver.cu) over ordered subsets of views, one geometry per subset.
 size_t asd_workspace_bytes(const cnsf_geometry *const *subsets, int n_subsets, int dtype);
 int run_asd_pocs(const cnsf_geometry *const *subsets, int n_subsets, const int *rows, const void *sino, void *image,

@@ -261,6 +261,191 @@ static int cgls_impl(const cnsf_geometry *geo, const T *y, T *x, int iters, int 
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
+// ================================================================ batched CGLS
+// CGLS on a batch of independent problems with one geometry (the same A): each image keeps
+// its own FP64 state and step lengths; the projections run once per iteration over the
+// whole batch.  In FP32 they always take the batched kernels (batch.cu), whose arithmetic
+// per image does not depend on the batch's size or other members, so every iterate is the
+// same whichever requests it is batched with.
+
+// workspace: [ scal (B x 8) | part (B x RED_BLOCKS) | x64 | p64 | r64 | pT | sT | qT | rT ], each B x
+static size_t cglsb_layout(const cnsf_geometry *geo, int B, int dtype, SolverWs *w, void *base)
+{
+    const GeomConsts &g = geo->gc;
+    size_t el = dtype == CNSF_F64 ? sizeof(double) : sizeof(float);
+    size_t ns = (size_t)B * g.nv * g.nd, ni = (size_t)B * g.nx * g.ny;
+    size_t off = 0;
+    size_t o_scal = off; off += align256((size_t)B * 8 * sizeof(double));
+    size_t o_part = off; off += align256((size_t)B * RED_BLOCKS * sizeof(double));
+    size_t o_x = off; off += align256(ni * sizeof(double));
+    size_t o_p = off; off += align256(ni * sizeof(double));
+    size_t o_r = off; off += align256(ns * sizeof(double));
+    size_t o_pT = off; off += align256(ni * el);
+    size_t o_sT = off; off += align256(ni * el);
+    size_t o_qT = off; off += align256(ns * el);
+    size_t o_rT = off; off += align256(ns * el);
+    if (w && base) {
+        char *b = (char *)base;
+        w->scal = (double *)(b + o_scal);
+        w->part = (double *)(b + o_part);
+        w->x64 = (double *)(b + o_x);
+        w->p64 = (double *)(b + o_p);
+        w->r64 = (double *)(b + o_r);
+        w->pT = b + o_pT; w->sT = b + o_sT; w->qT = b + o_qT; w->rT = b + o_rT;
+    }
+    return off;
+}
+
+size_t cgls_batched_workspace_bytes(const cnsf_geometry *geo, int batch, int dtype)
+{
+    return cglsb_layout(geo, batch, dtype, nullptr, nullptr);
+}
+
+// per image b (blockIdx.y): partial sums of squares of its n values
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) sumsq_partial_batched_kernel(const T *__restrict__ a, size_t n,
+                                                                            double *__restrict__ part)
+{
+    __shared__ double sh[RED_THREADS];
+    const T *ab = a + blockIdx.y * n;
+    double s = 0.0;
+    for (size_t i = blockIdx.x * (size_t)RED_THREADS + threadIdx.x; i < n; i += (size_t)RED_BLOCKS * RED_THREADS) {
+        double v = (double)ab[i];
+        s = fma(v, v, s);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.y * RED_BLOCKS + blockIdx.x] = sh[0];
+}
+
+// scal[8 b + slot] = sum of image b's partials (one block per image)
+__global__ void __launch_bounds__(RED_THREADS) sum_final_batched_kernel(const double *__restrict__ part, double *scal,
+                                                                        int slot)
+{
+    __shared__ double sh[RED_THREADS];
+    const double *pb = part + blockIdx.x * RED_BLOCKS;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += RED_THREADS) s += pb[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) scal[8 * blockIdx.x + slot] = sh[0];
+}
+
+// x_b += alpha_b p_b and r_b -= alpha_b q_b, alpha_b = gamma_b / <q_b, q_b>, for every image
+template <typename T>
+__global__ void cglsb_xr_kernel(double *x, const double *__restrict__ p, size_t nimg, double *r, T *rT,
+                                const T *__restrict__ q, size_t nsino, int B, const double *__restrict__ scal)
+{
+    const size_t ni = (size_t)B * nimg, n = ni + (size_t)B * nsino;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i < ni ? i / nimg : (i - ni) / nsino;
+        const double gam = scal[8 * b], qq = scal[8 * b + 1];
+        const double alpha = (gam > 0.0 && qq > 0.0) ? gam / qq : 0.0;
+        if (i < ni) {
+            x[i] = fma(alpha, p[i], x[i]);
+        } else {
+            const size_t k = i - ni;
+            const double rv = fma(-alpha, (double)q[k], r[k]);
+            r[k] = rv;
+            rT[k] = (T)rv;
+        }
+    }
+}
+
+// p_b = s_b + beta_b p_b, beta_b = gamma_new_b / gamma_b
+template <typename T>
+__global__ void cglsb_p_kernel(double *p, T *pT, const T *__restrict__ s, size_t nimg, int B,
+                               const double *__restrict__ scal)
+{
+    const size_t n = (size_t)B * nimg;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = i / nimg;
+        const double gam = scal[8 * b], gnew = scal[8 * b + 2];
+        const double beta = gam > 0.0 ? gnew / gam : 0.0;
+        const double pv = fma(beta, p[i], (double)s[i]);
+        p[i] = pv;
+        pT[i] = (T)pv;
+    }
+}
+
+__global__ void cglsb_roll_kernel(double *scal, int B)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) scal[8 * b] = scal[8 * b + 2];
+}
+
+template <typename T>
+static void sumsq_batched(const T *a, size_t n, int B, double *part, double *scal, int slot, cudaStream_t st)
+{
+    sumsq_partial_batched_kernel<T><<<dim3(RED_BLOCKS, B), RED_THREADS, 0, st>>>(a, n, part);
+    sum_final_batched_kernel<<<B, RED_THREADS, 0, st>>>(part, scal, slot);
+}
+
+template <typename T>
+static int proj_fwd_b(const cnsf_geometry *geo, const T *x, T *y, int B, int dtype, cudaStream_t st)
+{
+    if (dtype == CNSF_F32) return launch_forward_batch(geo, (const float *)x, (float *)y, B, st);
+    return launch_forward(geo, x, y, B, dtype, st);
+}
+
+template <typename T>
+static int proj_back_b(const cnsf_geometry *geo, const T *y, T *x, int B, int dtype, cudaStream_t st)
+{
+    if (dtype == CNSF_F32) return launch_back_batch(geo, (const float *)y, (float *)x, B, st);
+    return launch_back(geo, y, x, B, dtype, st);
+}
+
+template <typename T>
+static int cglsb_impl(const cnsf_geometry *geo, const T *y, T *x, int B, int iters, int resume, int dtype,
+                      SolverWs &w, cudaStream_t st)
+{
+    const GeomConsts &g = geo->gc;
+    const size_t ns = (size_t)g.nv * g.nd, ni = (size_t)g.nx * g.ny;
+    T *pT = (T *)w.pT, *sT = (T *)w.sT, *qT = (T *)w.qT, *rT = (T *)w.rT;
+    int s;
+    if (!resume) {
+        convert_kernel<T, double><<<grid_for(B * ni), 256, 0, st>>>(w.x64, x, B * ni);
+        if ((s = proj_fwd_b<T>(geo, x, qT, B, dtype, st)) != CNSF_OK) return s;
+        cgls_init_r_kernel<T><<<grid_for(B * ns), 256, 0, st>>>(w.r64, rT, y, qT, B * ns);
+        if ((s = proj_back_b<T>(geo, rT, sT, B, dtype, st)) != CNSF_OK) return s;
+        cgls_init_p_kernel<T><<<grid_for(B * ni), 256, 0, st>>>(w.p64, pT, sT, B * ni);
+        sumsq_batched<T>(sT, ni, B, w.part, w.scal, 0, st);
+    }
+    for (int k = 0; k < iters; ++k) {
+        if ((s = proj_fwd_b<T>(geo, pT, qT, B, dtype, st)) != CNSF_OK) return s;
+        sumsq_batched<T>(qT, ns, B, w.part, w.scal, 1, st);
+        cglsb_xr_kernel<T><<<grid_for(B * (ni + ns)), 256, 0, st>>>(w.x64, w.p64, ni, w.r64, rT, qT, ns, B, w.scal);
+        if ((s = proj_back_b<T>(geo, rT, sT, B, dtype, st)) != CNSF_OK) return s;
+        sumsq_batched<T>(sT, ni, B, w.part, w.scal, 2, st);
+        cglsb_p_kernel<T><<<grid_for(B * ni), 256, 0, st>>>(w.p64, pT, sT, ni, B, w.scal);
+        cglsb_roll_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.scal, B);
+    }
+    convert_kernel<double, T><<<grid_for(B * ni), 256, 0, st>>>(x, w.x64, B * ni);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
+int run_cgls_batched(const cnsf_geometry *geo, const void *sino, void *image, int batch, int iters, int resume,
+                     int dtype, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    if (!ws || ws_bytes < cgls_batched_workspace_bytes(geo, batch, dtype) || ((uintptr_t)ws & 255u) != 0)
+        return CNSF_ERR_INVALID;
+    if (batch == 0) return CNSF_OK;
+    SolverWs w;
+    cglsb_layout(geo, batch, dtype, &w, ws);
+    return dtype == CNSF_F64
+               ? cglsb_impl<double>(geo, (const double *)sino, (double *)image, batch, iters, resume, dtype, w, st)
+               : cglsb_impl<float>(geo, (const float *)sino, (float *)image, batch, iters, resume, dtype, w, st);
+}
+
 // ================================================================ ASD-POCS
 // Adaptive steepest descent POCS (Sidky & Pan 2008), the reconstruction method of Sec. IV-E.
 // One outer iteration: a data-consistency sweep over the ordered subsets of views

@@ -1,15 +1,22 @@
 """Continuous-batching reconstruction server on one GPU.
 
 Requests (an n x n image, V views, a sinogram, a CGLS iteration count) arrive over time.
-The scheduler admits them in arrival order whenever a stream slot is free and their
-device footprint fits the HBM budget; every admitted request runs on its own CUDA stream
-(sinogram upload, CGLS iterations through the C library, image download), so the work of
-requests that arrive while others run overlaps on the device.  A finished request frees
-its slot and memory for the next one.  Results do not depend on the mix: the kernels use
-no atomics and the solver's reductions have a fixed order.
+The scheduler admits work in arrival order whenever a stream slot is free and its device
+footprint fits the HBM budget; every admitted job runs on its own CUDA stream (sinogram
+upload, CGLS iterations through the C library, image download), so the work of requests
+that arrive while others run overlaps on the device.  A finished job frees its slot and
+memory for the next one.
 
-Latency = completion on the device (CUDA event, same clock as the arrivals) minus arrival.
-``mode="sequential"`` serves the same trace one request at a time (the baseline).
+Modes:
+* ``"batched"`` (continuous batching): a job is the oldest waiting request together with
+  the waiting requests of the same shape (n, V) and iteration count, up to ``max_batch``;
+  it runs as one batched CGLS (``cgls_batched``), which evaluates each matrix entry once
+  for the whole batch.  An image's iterates do not depend on the batch it ran in.
+* ``"continuous"``: one request per job, jobs overlapping on streams.
+* ``"sequential"``: one request at a time (the baseline).
+Results do not depend on the mix in any mode: the kernels use no atomics and the solver's
+reductions have a fixed order.  Latency = completion on the device (CUDA event, same clock
+as the arrivals) minus arrival.
 """
 from __future__ import annotations
 
@@ -24,7 +31,7 @@ from typing import Dict, List, Optional, Tuple
 
 import torch
 
-from . import CNSF_F32, Geometry, SolverWorkspace, _lib, cgls
+from . import CNSF_F32, BatchedSolverWorkspace, Geometry, SolverWorkspace, _lib, cgls, cgls_batched
 
 
 @dataclass
@@ -61,10 +68,11 @@ def serving_geometry_desc(n: int, n_views: int):
 class ReconServer:
     """Admission by device footprint, one stream per active request."""
 
-    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, device: int = 0):
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, device: int = 0, max_batch: int = 16):
         self.device = torch.device("cuda", device)
         self.budget = int(hbm_budget_bytes)
         self.max_active = int(max_active)
+        self.max_batch = int(max_batch)
         self.geoms: Dict[Tuple[int, int], Geometry] = {}
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_active)]
 
@@ -87,20 +95,81 @@ class ReconServer:
         scratch = 2 * n * (n + 2 * pad) * 4
         return g.n_views * g.n_det * 4 + n * n * 4 + ws + 256 + scratch
 
+    def batch_footprint(self, n: int, n_views: int, batch: int) -> int:
+        """Device bytes of a batched job: sinograms, images, batched workspace and the
+        batched projectors' interleaved copies (chunks of up to 16 images)."""
+        g = self.geometry(n, n_views)
+        ws = int(_lib.lib.cnsf_cgls_batched_workspace_bytes(g.handle, batch, CNSF_F32))
+        pad = 16
+        chunk = 16 * 4 * max(2 * n * (n + 2 * pad), g.n_views * g.n_det)
+        return batch * (g.n_views * g.n_det * 4 + n * n * 4) + ws + 512 + chunk
+
     # ------------------------------------------------------------------ serving
+    def _take_job(self, queue: deque, mode: str, used: int):
+        """The next job from the head of the queue: (requests, bytes), None to wait for
+        memory, or a rejection."""
+        r = queue[0]
+        if mode != "batched":
+            nbytes = self.footprint(r.n, r.n_views)
+            if nbytes > self.budget:
+                return "reject", [r], nbytes
+            if used + nbytes > self.budget:
+                return None
+            return "run", [r], nbytes
+        same = [q for q in queue if (q.n, q.n_views, q.iters) == (r.n, r.n_views, r.iters)][:self.max_batch]
+        if self.batch_footprint(r.n, r.n_views, 1) > self.budget:
+            return "reject", [r], 0
+        while same and used + self.batch_footprint(r.n, r.n_views, len(same)) > self.budget:
+            same.pop()
+        if not same:
+            return None
+        return "run", same, self.batch_footprint(r.n, r.n_views, len(same))
+
+    def _launch(self, job, mode: str, stream):
+        dev = self.device
+        r0 = job[0]
+        g = self.geometry(r0.n, r0.n_views)
+        with torch.cuda.device(dev), torch.cuda.stream(stream):
+            if mode == "batched":
+                sino = torch.empty((len(job),) + g.sino_shape, dtype=torch.float32, device=dev)
+                for k, r in enumerate(job):
+                    sino[k].copy_(r.sino, non_blocking=True)
+                x = torch.zeros((len(job), r0.n, r0.n), dtype=torch.float32, device=dev)
+                ws = BatchedSolverWorkspace(g, len(job), torch.float32)
+                cgls_batched(g, sino, r0.iters, x0=x, ws=ws, stream=stream)
+                outs = []
+                for k in range(len(job)):
+                    o = torch.empty((r0.n, r0.n), dtype=torch.float32, pin_memory=True)
+                    o.copy_(x[k], non_blocking=True)
+                    outs.append(o)
+            else:
+                sino = r0.sino.to(dev, non_blocking=True)
+                x = torch.zeros((r0.n, r0.n), dtype=torch.float32, device=dev)
+                ws = SolverWorkspace(g, torch.float32)
+                cgls(g, sino, r0.iters, x0=x, ws=ws, stream=stream)
+                o = torch.empty((r0.n, r0.n), dtype=torch.float32, pin_memory=True)
+                o.copy_(x, non_blocking=True)
+                outs = [o]
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+        return ev, {"sino": sino, "x": x, "ws": ws, "outs": outs}
+
     def run(self, requests: List[ReconRequest], mode: str = "continuous", keep_images: bool = True,
             poll_s: float = 2e-5) -> List[ReconResult]:
+        if mode not in ("batched", "continuous", "sequential"):
+            raise ValueError(f"unknown mode {mode!r}")
         dev = self.device
         reqs = sorted(requests, key=lambda r: (r.arrival_s, r.rid))
         for r in reqs:
             self.geometry(r.n, r.n_views)          # geometries are built before the clock starts
         pending = deque(reqs)
         queue: deque = deque()
-        active = {}                                # slot -> (request, done event, buffers, bytes)
-        free_slots = list(range(self.max_active if mode == "continuous" else 1))
+        active = {}                                # slot -> (job, done event, buffers, bytes)
+        free_slots = list(range(self.max_active if mode != "sequential" else 1))
         used = 0
         self.max_used = 0
         self.max_concurrent = 0
+        self.batch_sizes = []
         results: Dict[int, ReconResult] = {}
         torch.cuda.synchronize(dev)
         start_ev = torch.cuda.Event(enable_timing=True)
@@ -114,46 +183,42 @@ class ReconServer:
                 queue.append(pending.popleft())
             progressed = False
             for slot in list(active):
-                r, ev, bufs, nbytes = active[slot]
+                job, ev, bufs, nbytes = active[slot]
                 if ev.query():
-                    res = results[r.rid]
-                    res.done_s = start_ev.elapsed_time(ev) * 1e-3
-                    res.latency_s = res.done_s - r.arrival_s
-                    res.image = bufs["out"] if keep_images else None
+                    done = start_ev.elapsed_time(ev) * 1e-3
+                    for k, r in enumerate(job):
+                        res = results[r.rid]
+                        res.done_s = done
+                        res.latency_s = done - r.arrival_s
+                        res.image = bufs["outs"][k] if keep_images else None
                     used -= nbytes
                     del active[slot]
                     free_slots.append(slot)
                     progressed = True
             while queue and free_slots:
-                r = queue[0]
-                nbytes = self.footprint(r.n, r.n_views)
-                if nbytes > self.budget:
-                    queue.popleft()
-                    results[r.rid] = ReconResult(r.rid, "rejected: exceeds HBM budget", arrival_s=r.arrival_s)
+                taken = self._take_job(queue, mode, used)
+                if taken is None:
+                    break                          # wait for memory: keep arrival order
+                what, job, nbytes = taken
+                for r in job:
+                    queue.remove(r)
+                if what == "reject":
+                    for r in job:
+                        results[r.rid] = ReconResult(r.rid, "rejected: exceeds HBM budget", arrival_s=r.arrival_s)
                     progressed = True
                     continue
-                if used + nbytes > self.budget:
-                    break                          # wait for memory: keep arrival order
-                queue.popleft()
                 slot = free_slots.pop()
-                stream = self.streams[slot]
-                g = self.geometry(r.n, r.n_views)
-                with torch.cuda.device(dev), torch.cuda.stream(stream):
-                    sino = r.sino.to(dev, non_blocking=True)
-                    x = torch.zeros((r.n, r.n), dtype=torch.float32, device=dev)
-                    ws = SolverWorkspace(g, torch.float32)
-                    cgls(g, sino, r.iters, x0=x, ws=ws, stream=stream)
-                    out = torch.empty((r.n, r.n), dtype=torch.float32, pin_memory=True)
-                    out.copy_(x, non_blocking=True)
-                    ev = torch.cuda.Event(enable_timing=True)
-                    ev.record(stream)
-                results[r.rid] = ReconResult(r.rid, "ok", arrival_s=r.arrival_s, admit_s=time.perf_counter() - t0)
-                active[slot] = (r, ev, {"sino": sino, "x": x, "ws": ws, "out": out}, nbytes)
+                ev, bufs = self._launch(job, mode, self.streams[slot])
+                admit = time.perf_counter() - t0
+                for r in job:
+                    results[r.rid] = ReconResult(r.rid, "ok", arrival_s=r.arrival_s, admit_s=admit)
+                active[slot] = (job, ev, bufs, nbytes)
+                self.batch_sizes.append(len(job))
                 used += nbytes
                 self.max_used = max(self.max_used, used)
                 self.max_concurrent = max(self.max_concurrent, len(active))
                 progressed = True
-                if mode != "continuous":
+                if mode == "sequential":
                     break
             if not progressed:
                 if active:
@@ -220,7 +285,7 @@ def main():
     sinos = synthetic_sinograms(server, sorted({(t.n, t.n_views) for t in trace}))
     reqs = make_requests(trace, lambda n, v: sinos[(n, v)], args.iters)
     out = {}
-    for mode in ("sequential", "continuous"):
+    for mode in ("sequential", "continuous", "batched"):
         out[mode] = summarize(server.run(reqs, mode=mode, keep_images=False))
     json.dump(out, sys.stdout)
     print()

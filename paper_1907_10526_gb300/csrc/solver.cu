@@ -197,6 +197,51 @@ __global__ void cgls_roll_kernel(double *scal) { scal[0] = scal[2]; }
 
 static inline dim3 grid_for(size_t n) { return dim3((unsigned)std::min<size_t>((n + 255) / 256, 4096)); }
 
+// Run `iters` identical iterations.  The launches of one iteration (projections with their
+// stream-ordered scratch, reductions, updates: tens of small launches) are captured once
+// into a CUDA graph on a private stream and the graph is launched `iters` times on the
+// caller's stream, so the host submits one launch per iteration.  Short runs (fewer than
+// `min_graph` iterations) launch directly.  `body(stream)` issues one iteration and returns
+// a status; it must not depend on the iteration index (step-dependent choices are made by
+// the kernels from device scalars).
+template <typename Body>
+static int run_iterations(int iters, cudaStream_t st, Body body, int min_graph = 3)
+{
+    if (iters < min_graph) {
+        for (int k = 0; k < iters; ++k) {
+            int s = body(st);
+            if (s != CNSF_OK) return s;
+        }
+        return CNSF_OK;
+    }
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    int s = CNSF_OK;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        s = body(cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (s == CNSF_OK && e2 != cudaSuccess) s = record_cuda_error(e2);
+    } else {
+        s = record_cuda_error(e);
+    }
+    if (s == CNSF_OK) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) s = record_cuda_error(e);
+    }
+    for (int k = 0; s == CNSF_OK && k < iters; ++k) {
+        e = cudaGraphLaunch(exec, st);
+        if (e != cudaSuccess) s = record_cuda_error(e);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);   // returns at once; the stream is released when its work is done
+    return s;
+}
+
 template <typename T>
 static void sumsq(const T *a, size_t n, SolverWs &w, double *dst, cudaStream_t st)
 {
@@ -220,12 +265,15 @@ static int sirt_impl(const cnsf_geometry *geo, const T *y, T *x, int iters, doub
     fill_kernel<T><<<grid_for(ns), 256, 0, st>>>(r, ns, T(1));
     if ((s = launch_back(geo, r, C, 1, dtype, st)) != CNSF_OK) return s;
     recip_kernel<T><<<grid_for(ni), 256, 0, st>>>(C, ni);
-    for (int k = 0; k < iters; ++k) {
-        if ((s = launch_forward(geo, x, r, 1, dtype, st)) != CNSF_OK) return s;
-        sirt_residual_kernel<T><<<grid_for(ns), 256, 0, st>>>(r, y, R, ns);
-        if ((s = launch_back(geo, r, gr, 1, dtype, st)) != CNSF_OK) return s;
-        sirt_update_kernel<T><<<grid_for(ni), 256, 0, st>>>(x, gr, C, (T)relax, ni);
-    }
+    s = run_iterations(iters, st, [&](cudaStream_t q) -> int {
+        int t;
+        if ((t = launch_forward(geo, x, r, 1, dtype, q)) != CNSF_OK) return t;
+        sirt_residual_kernel<T><<<grid_for(ns), 256, 0, q>>>(r, y, R, ns);
+        if ((t = launch_back(geo, r, gr, 1, dtype, q)) != CNSF_OK) return t;
+        sirt_update_kernel<T><<<grid_for(ni), 256, 0, q>>>(x, gr, C, (T)relax, ni);
+        return CNSF_OK;
+    });
+    if (s != CNSF_OK) return s;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
@@ -247,15 +295,18 @@ static int cgls_impl(const cnsf_geometry *geo, const T *y, T *x, int iters, int 
         cgls_init_p_kernel<T><<<grid_for(ni), 256, 0, st>>>(w.p64, pT, sT, ni);
         sumsq<T>(sT, ni, w, w.scal + 0, st);
     }
-    for (int k = 0; k < iters; ++k) {
-        if ((s = launch_forward(geo, pT, qT, 1, dtype, st)) != CNSF_OK) return s;
-        sumsq<T>(qT, ns, w, w.scal + 1, st);
-        cgls_xr_kernel<T><<<grid_for(ni + ns), 256, 0, st>>>(w.x64, w.p64, ni, w.r64, rT, qT, ns, w.scal);
-        if ((s = launch_back(geo, rT, sT, 1, dtype, st)) != CNSF_OK) return s;
-        sumsq<T>(sT, ni, w, w.scal + 2, st);
-        cgls_p_kernel<T><<<grid_for(ni), 256, 0, st>>>(w.p64, pT, sT, ni, w.scal);
-        cgls_roll_kernel<<<1, 1, 0, st>>>(w.scal);
-    }
+    s = run_iterations(iters, st, [&](cudaStream_t q) -> int {
+        int t;
+        if ((t = launch_forward(geo, pT, qT, 1, dtype, q)) != CNSF_OK) return t;
+        sumsq<T>(qT, ns, w, w.scal + 1, q);
+        cgls_xr_kernel<T><<<grid_for(ni + ns), 256, 0, q>>>(w.x64, w.p64, ni, w.r64, rT, qT, ns, w.scal);
+        if ((t = launch_back(geo, rT, sT, 1, dtype, q)) != CNSF_OK) return t;
+        sumsq<T>(sT, ni, w, w.scal + 2, q);
+        cgls_p_kernel<T><<<grid_for(ni), 256, 0, q>>>(w.p64, pT, sT, ni, w.scal);
+        cgls_roll_kernel<<<1, 1, 0, q>>>(w.scal);
+        return CNSF_OK;
+    });
+    if (s != CNSF_OK) return s;
     convert_kernel<double, T><<<grid_for(ni), 256, 0, st>>>(x, w.x64, ni);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
@@ -419,15 +470,18 @@ static int cglsb_impl(const cnsf_geometry *geo, const T *y, T *x, int B, int ite
         cgls_init_p_kernel<T><<<grid_for(B * ni), 256, 0, st>>>(w.p64, pT, sT, B * ni);
         sumsq_batched<T>(sT, ni, B, w.part, w.scal, 0, st);
     }
-    for (int k = 0; k < iters; ++k) {
-        if ((s = proj_fwd_b<T>(geo, pT, qT, B, dtype, st)) != CNSF_OK) return s;
-        sumsq_batched<T>(qT, ns, B, w.part, w.scal, 1, st);
-        cglsb_xr_kernel<T><<<grid_for(B * (ni + ns)), 256, 0, st>>>(w.x64, w.p64, ni, w.r64, rT, qT, ns, B, w.scal);
-        if ((s = proj_back_b<T>(geo, rT, sT, B, dtype, st)) != CNSF_OK) return s;
-        sumsq_batched<T>(sT, ni, B, w.part, w.scal, 2, st);
-        cglsb_p_kernel<T><<<grid_for(B * ni), 256, 0, st>>>(w.p64, pT, sT, ni, B, w.scal);
-        cglsb_roll_kernel<<<(B + 127) / 128, 128, 0, st>>>(w.scal, B);
-    }
+    s = run_iterations(iters, st, [&](cudaStream_t q) -> int {
+        int t;
+        if ((t = proj_fwd_b<T>(geo, pT, qT, B, dtype, q)) != CNSF_OK) return t;
+        sumsq_batched<T>(qT, ns, B, w.part, w.scal, 1, q);
+        cglsb_xr_kernel<T><<<grid_for(B * (ni + ns)), 256, 0, q>>>(w.x64, w.p64, ni, w.r64, rT, qT, ns, B, w.scal);
+        if ((t = proj_back_b<T>(geo, rT, sT, B, dtype, q)) != CNSF_OK) return t;
+        sumsq_batched<T>(sT, ni, B, w.part, w.scal, 2, q);
+        cglsb_p_kernel<T><<<grid_for(B * ni), 256, 0, q>>>(w.p64, pT, sT, ni, B, w.scal);
+        cglsb_roll_kernel<<<(B + 127) / 128, 128, 0, q>>>(w.scal, B);
+        return CNSF_OK;
+    });
+    if (s != CNSF_OK) return s;
     convert_kernel<double, T><<<grid_for(B * ni), 256, 0, st>>>(x, w.x64, B * ni);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
@@ -577,14 +631,19 @@ __global__ void tv_step_kernel(T *x, const T *__restrict__ d, size_t n, const do
         x[i] -= f * d[i];
 }
 
+// scal[6] counts the iterations done (so that one captured iteration serves them all)
 __global__ void asd_start_kernel(double *scal, double relax)
 {
     scal[0] = relax;
     scal[1] = 0.0;
+    scal[6] = 0.0;
 }
 
 // first iteration: TV step = alpha dp
-__global__ void asd_first_kernel(double *scal, double alpha) { scal[1] = alpha * sqrt(scal[2]); }
+__global__ void asd_first_kernel(double *scal, double alpha)
+{
+    if (scal[6] == 0.0) scal[1] = alpha * sqrt(scal[2]);
+}
 
 // after the TV steps: shrink the TV step when the TV move outgrew the data move (while the
 // data residual is above its tolerance), and relax the data step
@@ -593,6 +652,7 @@ __global__ void asd_adapt_kernel(double *scal, double r_max, double alpha_red, d
     const double dp = sqrt(scal[2]), dd = sqrt(scal[3]), dg = sqrt(scal[5]);
     if (dg > r_max * dp && (data_tol <= 0.0 || dd > data_tol)) scal[1] *= alpha_red;
     scal[0] *= relax_red;
+    scal[6] += 1.0;
 }
 
 template <typename T>
@@ -636,39 +696,43 @@ static int asd_impl(const cnsf_geometry *const *sub, int nsub, const int *rows_h
     asd_start_kernel<<<1, 1, 0, st>>>(w.scal, P.relax);
     const dim3 tvb(16, 16), tvg((g.nx + 15) / 16, (g.ny + 15) / 16);
     const T eta2 = (T)(P.tv_eps * P.tv_eps);
-    for (int it = 0; it < P.iters; ++it) {
-        if ((e = cudaMemcpyAsync(xprev, x, ni * sizeof(T), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return record_cuda_error(e);
-        off = 0;
+    s = run_iterations(P.iters, st, [&](cudaStream_t q) -> int {
+        int t;
+        cudaError_t ce;
+        if ((ce = cudaMemcpyAsync(xprev, x, ni * sizeof(T), cudaMemcpyDeviceToDevice, q)) != cudaSuccess)
+            return record_cuda_error(ce);
+        size_t o = 0;
         for (int k = 0; k < nsub; ++k) {   // data-consistency sweep over the ordered subsets
             const size_t nk = (size_t)sub[k]->gc.nv * g.nd;
-            if ((s = fwd(sub[k], x, rb + off, 1, dtype, st)) != CNSF_OK) return s;
-            sirt_residual_kernel<T><<<grid_for(nk), 256, 0, st>>>(rb + off, ysub + off, R + off, nk);
-            if ((s = bwd(sub[k], rb + off, gr, 1, dtype, st)) != CNSF_OK) return s;
-            asd_update_kernel<T><<<grid_for(ni), 256, 0, st>>>(x, gr, C + k * ni, ni, w.scal, k == nsub - 1);
-            off += nk;
+            if ((t = fwd(sub[k], x, rb + o, 1, dtype, q)) != CNSF_OK) return t;
+            sirt_residual_kernel<T><<<grid_for(nk), 256, 0, q>>>(rb + o, ysub + o, R + o, nk);
+            if ((t = bwd(sub[k], rb + o, gr, 1, dtype, q)) != CNSF_OK) return t;
+            asd_update_kernel<T><<<grid_for(ni), 256, 0, q>>>(x, gr, C + k * ni, ni, w.scal, k == nsub - 1);
+            o += nk;
         }
-        diffsq<T>(x, xprev, ni, w.part, w.scal + 2, st);
+        diffsq<T>(x, xprev, ni, w.part, w.scal + 2, q);
         if (P.data_tol > 0.0) {
-            off = 0;
+            o = 0;
             for (int k = 0; k < nsub; ++k) {
-                if ((s = fwd(sub[k], x, rb + off, 1, dtype, st)) != CNSF_OK) return s;
-                off += (size_t)sub[k]->gc.nv * g.nd;
+                if ((t = fwd(sub[k], x, rb + o, 1, dtype, q)) != CNSF_OK) return t;
+                o += (size_t)sub[k]->gc.nv * g.nd;
             }
-            diffsq<T>(rb, ysub, ns, w.part, w.scal + 3, st);
+            diffsq<T>(rb, ysub, ns, w.part, w.scal + 3, q);
         }
-        if (it == 0) asd_first_kernel<<<1, 1, 0, st>>>(w.scal, P.alpha);
-        if ((e = cudaMemcpyAsync(xdata, x, ni * sizeof(T), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-            return record_cuda_error(e);
+        asd_first_kernel<<<1, 1, 0, q>>>(w.scal, P.alpha);
+        if ((ce = cudaMemcpyAsync(xdata, x, ni * sizeof(T), cudaMemcpyDeviceToDevice, q)) != cudaSuccess)
+            return record_cuda_error(ce);
         for (int m = 0; m < P.tv_steps; ++m) {
-            tv_grad_kernel<T><<<tvg, tvb, 0, st>>>(x, d, g.nx, g.ny, eta2);
-            sumsq_partial_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(d, ni, w.part);
-            sum_final_kernel<<<1, RED_THREADS, 0, st>>>(w.part, w.scal + 4);
-            tv_step_kernel<T><<<grid_for(ni), 256, 0, st>>>(x, d, ni, w.scal);
+            tv_grad_kernel<T><<<tvg, tvb, 0, q>>>(x, d, g.nx, g.ny, eta2);
+            sumsq_partial_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, q>>>(d, ni, w.part);
+            sum_final_kernel<<<1, RED_THREADS, 0, q>>>(w.part, w.scal + 4);
+            tv_step_kernel<T><<<grid_for(ni), 256, 0, q>>>(x, d, ni, w.scal);
         }
-        diffsq<T>(x, xdata, ni, w.part, w.scal + 5, st);
-        asd_adapt_kernel<<<1, 1, 0, st>>>(w.scal, P.r_max, P.alpha_red, P.data_tol, P.relax_red);
-    }
+        diffsq<T>(x, xdata, ni, w.part, w.scal + 5, q);
+        asd_adapt_kernel<<<1, 1, 0, q>>>(w.scal, P.r_max, P.alpha_red, P.data_tol, P.relax_red);
+        return CNSF_OK;
+    });
+    if (s != CNSF_OK) return s;
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }

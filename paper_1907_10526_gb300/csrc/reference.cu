@@ -10,11 +10,12 @@
 // pieces (the nearest singularity of a piece lies many piece-widths away).  FP64 throughout,
 // whatever the dtype of the images and sinograms.
 //
-// Forward: one thread per (view, cell) walks every line of the image along the axis its
-// central ray crosses most steeply and takes the pixels that the cell's wedge (the two rays
-// through the cell edges) reaches on that line.  Back: one thread per pixel takes, for each
-// view, the cells whose bin meets the pixel's shadow [min corner, max corner].  Both use the
-// same entry function, so the two operators are adjoint to rounding.
+// Forward: one warp per (view, cell) walks every line of the image along the axis its
+// central ray crosses most steeply (lane l the lines l, l + 32, ...) and takes the pixels
+// that the cell's wedge (the two rays through the cell edges) reaches on that line.  Back:
+// one thread per pixel takes, for each view, the cells whose bin meets the pixel's shadow
+// [min corner, max corner].  Both use the same entry function, so the two operators are
+// adjoint to rounding.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -142,13 +143,16 @@ __device__ double ref_entry(const GeomConsts &g, double c, double s, double kx, 
     return sum / g.tau;
 }
 
+// One warp per ray: lane l takes the lines l, l + 32, ...; the lanes' sums are combined by
+// a fixed shuffle tree (the result does not depend on scheduling).
 template <typename T>
 __global__ void __launch_bounds__(128) ref_fp_kernel(GeomConsts g, const double *__restrict__ view_cs,
                                                      const T *__restrict__ img, T *__restrict__ sino)
 {
     const int nr = g.nv * g.nd;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nr) return;
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nr) return;   // whole warps leave together
     const long long b = blockIdx.y;
     const int k = q / g.nd, j = q - k * g.nd;
     const double c = view_cs[2 * k], s = view_cs[2 * k + 1];
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(128) ref_fp_kernel(GeomConsts g, const double 
     const int na = tr ? g.ny : g.nx, nb = tr ? g.nx : g.ny;
     const double ca = tr ? g.cy : g.cx, cb = tr ? g.cx : g.cy;
     double acc = 0.0;
-    for (int rb = 0; rb < nb; ++rb) {
+    for (int rb = lane; rb < nb; rb += 32) {
         const double yb = cb + (rb - 0.5 * (nb - 1)) * g.h;
         // a-extent of the wedge within the band |b - yb| <= h/2: its vertices are the edge
         // crossings of the band's two sides, plus the ray origin when it lies in the band
@@ -198,7 +202,9 @@ __global__ void __launch_bounds__(128) ref_fp_kernel(GeomConsts g, const double 
             if (w != 0.0) acc += (double)im[(long long)r * g.nx + i] * w;
         }
     }
-    sino[b * nr + q] = (T)acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) sino[b * nr + q] = (T)acc;
 }
 
 template <typename T>
@@ -238,7 +244,7 @@ int launch_forward_ref(const cnsf_geometry *geo, const void *img, void *sino, in
     if (batch == 0) return CNSF_OK;
     const GeomConsts &g = geo->gc;
     const int nr = g.nv * g.nd;
-    dim3 blk(128), grd((nr + 127) / 128, batch);
+    dim3 blk(128), grd((nr + 3) / 4, batch);   // four rays (warps) per block
     if (dtype == CNSF_F32)
         ref_fp_kernel<float><<<grd, blk, 0, st>>>(g, geo->d_view_cs, (const float *)img, (float *)sino);
     else

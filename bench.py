@@ -433,18 +433,22 @@ def bench_e4_ladder(dev, reps: int = 3):
         c = cnsf.back_project(geom, y)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         fp, bp = [], []
+        calls = 20 if n <= 512 else 3   # back-to-back calls per timing: the device time of a call
         for _ in range(reps):
             torch.cuda.synchronize()
             ev[0].record()
-            cnsf.forward_project(geom, x, out=y)
+            for _ in range(calls):
+                cnsf.forward_project(geom, x, out=y)
             ev[1].record()
-            cnsf.back_project(geom, y, out=c)
+            for _ in range(calls):
+                cnsf.back_project(geom, y, out=c)
             ev[2].record()
             torch.cuda.synchronize()
-            fp.append(ev[0].elapsed_time(ev[1]))
-            bp.append(ev[1].elapsed_time(ev[2]))
+            fp.append(ev[0].elapsed_time(ev[1]) / calls)
+            bp.append(ev[1].elapsed_time(ev[2]) / calls)
         out.append({"n": n, "n_det": n_det, "d_po_d_so_mm": d, "fp_ms": min(fp), "bp_ms": min(bp),
-                    "fp_per_view_ms": min(fp) / 360, "bp_per_view_ms": min(bp) / 360})
+                    "fp_per_view_ms": min(fp) / 360, "bp_per_view_ms": min(bp) / 360,
+                    "calls_per_timing": calls})
         del geom
     return out
 

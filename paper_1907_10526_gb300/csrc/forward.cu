@@ -372,7 +372,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         int nsplit = 1;
-        while (nsplit < 4 && (long long)grd.x * nsplit < 64LL * std::max(sms, 1)) nsplit *= 2;
+        while (nsplit < 4 && (long long)grd.x * nsplit < 128LL * std::max(sms, 1)) nsplit *= 2;
         float *partial = nullptr;
         const long long nout = (long long)nr * batch;
         if (nsplit > 1) {

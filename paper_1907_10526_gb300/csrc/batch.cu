@@ -122,13 +122,14 @@ __global__ void __launch_bounds__(128) fp_batch_kernel(const int *__restrict__ o
 {
     const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
     if (q >= nr) return;
-    const RayF R = rays[q];
+    RayF R = rays[q];
     Acc<NB4> acc;
     acc.zero();
     if (R.nrows > 0) {
         const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
         const float p = bx.x, qiC = bx.y, iC = bx.z, hC = bx.w;
         const float B = 2.f * (p + hC);
+        tighten_window(R, p, hC, B);
         const bool tr = (R.flags & 1) != 0;
         const int pitch = tr ? pitchT : pitchP;
         const float4 *base = (tr ? Tt : P) + ((long long)R.r0 * pitch + pad) * NB4;

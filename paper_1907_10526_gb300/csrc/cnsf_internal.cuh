@@ -227,6 +227,25 @@ struct RayF {
 };
 static_assert(sizeof(RayF) == 48, "RayF layout");
 
+// The table's candidate window covers the blur at the deepest point of the whole image.
+// For the lines this thread walks, the blur is at most e_max = max(e at the first and the
+// last line) plus |kap| per unit offset, so every non-zero entry satisfies
+// |u| < ((B + C)/2 + e_max)/(B - |kap|): shrink the window to that (when narrower), moving
+// its fixed-point start by the same amount, and walk fewer candidates per line.
+#ifdef __CUDACC__
+__device__ __forceinline__ void tighten_window(RayF &R, float p, float hC, float B)
+{
+    const float emax = fmaxf(R.e0, fmaf((float)(R.nrows - 1), R.de, R.e0));
+    const float hw = (p + 2.f * hC + emax) / (B - fabsf(R.kap)) + 1e-3f;
+    if (hw < R.hw) {
+        const long long D = (long long)((double)(R.hw - hw) * 4294967296.0);   // >= 0, 32.32
+        R.A0 += D;
+        R.hw -= (float)((double)D * (1.0 / 4294967296.0));
+        R.kc = min(R.kc, (int)floorf(2.f * R.hw) + 1);
+    }
+}
+#endif
+
 // Per-(view, cell) trapezoid constants of the FP32 kernels: box_B * box_C (Eq. 16 widths)
 // as p = (B - C)/2, q/C, 1/C (clamped for C = 0) and C/2.  B = 2(p + C/2); the
 // normalisation of Eq. (18) with the pixel area is h^2/(2B).

@@ -177,23 +177,6 @@ __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ b
     return acc + part;
 }
 
-// The table's candidate window covers the blur at the deepest point of the whole image.
-// For the lines this thread walks, the blur is at most e_max = max(e at the first and the
-// last line) plus |kap| per unit offset, so every non-zero entry satisfies
-// |u| < ((B + C)/2 + e_max)/(B - |kap|): shrink the window to that (when narrower), moving
-// its fixed-point start by the same amount, and walk fewer candidates per line.
-__device__ __forceinline__ void tighten_window(RayF &R, float p, float hC, float B)
-{
-    const float emax = fmaxf(R.e0, fmaf((float)(R.nrows - 1), R.de, R.e0));
-    const float hw = (p + 2.f * hC + emax) / (B - fabsf(R.kap)) + 1e-3f;
-    if (hw < R.hw) {
-        const long long D = (long long)((double)(R.hw - hw) * 4294967296.0);   // >= 0, 32.32
-        R.A0 += D;
-        R.hw -= (float)((double)D * (1.0 / 4294967296.0));
-        R.kc = min(R.kc, (int)floorf(2.f * R.hw) + 1);
-    }
-}
-
 template <bool COUNT>
 __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
                                                      const BoxF *__restrict__ box, float h2q,

@@ -53,6 +53,54 @@ __device__ __forceinline__ float bp_sigma(const TV &T, float di, float dr, float
 // one cell at each end; those cells lie outside the window, which bounds the support with
 // margin, so their entries are exactly 0 (a padding cell past n_det has sinogram value 0).
 // The normalisation h^2/(2B) = h^2/(4(p + C/2)) is folded into the division by tau'.
+// The FP32 per-(tile, view) coefficients from the FP64 projection of the tile centre.
+__device__ __forceinline__ void tile_view_f32(const GeomConsts &g, double c, double s, double it, double rt,
+                                              TileViewS<float> &T, int &J)
+{
+    double Dt, yt, a1, b1, rho, phi, hc, hs;
+    tile_view_double(g, c, s, it, rt, &Dt, &yt, &a1, &b1, &rho, &phi, &J, &hc, &hs);
+    T.Dt = (float)Dt; T.yt = (float)yt; T.a1 = (float)a1; T.b1 = (float)b1;
+    T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)hc; T.hs = (float)hs;
+}
+
+// Geometry-time table of those coefficients for every (tile, view): two float4 and J.
+__global__ void tile_view_table_kernel(GeomConsts g, const double *__restrict__ view_cs, int ntx, int ntiles,
+                                       float4 *__restrict__ tab, int *__restrict__ jtab)
+{
+    const long long n = (long long)ntiles * g.nv;
+    const double ctr = 0.5 * (BP_T - 1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int tile = (int)(t / g.nv), v = (int)(t - (long long)tile * g.nv);
+        TileViewS<float> T;
+        int J;
+        tile_view_f32(g, view_cs[2 * v], view_cs[2 * v + 1], (tile % ntx) * BP_T + ctr, (tile / ntx) * BP_T + ctr, T, J);
+        tab[2 * t] = make_float4(T.Dt, T.yt, T.a1, T.b1);
+        tab[2 * t + 1] = make_float4(T.rho, T.phi, T.hc, T.hs);
+        jtab[t] = J;
+    }
+}
+
+int build_tile_view_table(cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
+    const long long n = (long long)ntx * nty * g.nv;
+    if (n * 36 > (256LL << 20)) return CNSF_OK;   // large geometries compute it in the kernel
+    cudaError_t e = cudaMalloc((void **)&geo->d_tv, (size_t)n * 2 * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&geo->d_tj, (size_t)n * sizeof(int));
+    if (e != cudaSuccess) {
+        if (geo->d_tv) cudaFree(geo->d_tv);
+        geo->d_tv = nullptr;
+        geo->d_tj = nullptr;
+        return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    }
+    tile_view_table_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256>>>(g, geo->d_view_cs, ntx,
+                                                                                          ntx * nty, geo->d_tv,
+                                                                                          geo->d_tj);
+    e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
 // Arc detector: |s'| = R sin(dg d) for a cell d cells from the pixel's projection, R the
 // pixel's distance from the source; with dg d below ~0.05 rad, R dg d (1 - (dg d)^2/6) is
 // that sine to ~1e-9 relative (the next term of the series).
@@ -110,7 +158,8 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
                                                      const float *__restrict__ cell2,
                                                      const float2 *__restrict__ y2, float *__restrict__ img,
                                                      BpArgs a, const int *__restrict__ order, int ntx, int nsplit,
-                                                     float *__restrict__ partial)
+                                                     float *__restrict__ partial, const float4 *__restrict__ tvtab,
+                                                     const int *__restrict__ tjtab)
 {
     __shared__ TileViewS<float> tv[BP_CHUNK];
     __shared__ int tj[BP_CHUNK];
@@ -135,15 +184,17 @@ __global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double 
         const int nvc = min(BP_CHUNK, vend - v0);
         __syncthreads();
         if (tid < nvc) {
-            double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
-            double Dt, yt, a1, b1, rho, phi, hc, hs;
-            int J;
-            tile_view_double(g, c, s, it + (double)ctr, rt + (double)ctr, &Dt, &yt, &a1, &b1, &rho, &phi, &J, &hc, &hs);
-            TileViewS<float> T;
-            T.Dt = (float)Dt; T.yt = (float)yt; T.a1 = (float)a1; T.b1 = (float)b1;
-            T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)hc; T.hs = (float)hs;
-            tv[tid] = T;
-            tj[tid] = J;
+            if (tvtab) {   // precomputed with the geometry
+                const long long t = (long long)tile * g.nv + v0 + tid;
+                const float4 u0 = __ldg(tvtab + 2 * t), u1 = __ldg(tvtab + 2 * t + 1);
+                TileViewS<float> T;
+                T.Dt = u0.x; T.yt = u0.y; T.a1 = u0.z; T.b1 = u0.w; T.rho = u1.x; T.phi = u1.y; T.hc = u1.z; T.hs = u1.w;
+                tv[tid] = T;
+                tj[tid] = __ldg(tjtab + t);
+            } else {
+                tile_view_f32(g, view_cs[2 * (v0 + tid)], view_cs[2 * (v0 + tid) + 1], it + (double)ctr,
+                              rt + (double)ctr, tv[tid], tj[tid]);
+            }
         }
         __syncthreads();
         if (inside) {
@@ -308,7 +359,7 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         auto kern = g.arc ? bp_f32_kernel<true> : bp_f32_kernel<false>;
         kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_T * BP_T), 0, st>>>(
             g, geo->d_view_cs, geo->d_box2, geo->d_cell2, y2, (float *)img, a, geo->d_bp_order,
-            (int)grd.x, nsplit, partial);
+            (int)grd.x, nsplit, partial, geo->d_tv, geo->d_tj);
         if (copy) cudaFreeAsync(copy, st);
         if (nsplit > 1) {
             bp_sum_parts_kernel<<<(unsigned)std::min<long long>((nimg + 255) / 256, 4096), 256, 0, st>>>(

@@ -14,6 +14,8 @@ int record_cuda_error(cudaError_t e = cudaGetLastError());
 
 int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out);
 void destroy_geometry(cnsf_geometry *geo);
+// Precompute the back projector's per-(tile, view) coefficients when they fit 256 MB (back.cu).
+int build_tile_view_table(cnsf_geometry *geo);
 
 // Kernel launchers (arguments already validated by the C ABI layer).
 int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,

@@ -278,6 +278,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { destroy_geometry(geo); return record_cuda_error(e); }
     }
+    st = build_tile_view_table(geo);
+    if (st != CNSF_OK) { destroy_geometry(geo); return st; }
     *out = geo;
     return CNSF_OK;
 }
@@ -286,7 +288,7 @@ void destroy_geometry(cnsf_geometry *geo)
 {
     if (!geo) return;
     void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray,
-                    geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2};
+                    geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2, geo->d_tv, geo->d_tj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete geo;

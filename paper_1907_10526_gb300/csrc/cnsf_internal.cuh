@@ -238,9 +238,9 @@ __device__ __forceinline__ void tighten_window(RayF &R, float p, float hC, float
     const float emax = fmaxf(R.e0, fmaf((float)(R.nrows - 1), R.de, R.e0));
     const float hw = (p + 2.f * hC + emax) / (B - fabsf(R.kap)) + 1e-3f;
     if (hw < R.hw) {
-        const long long D = (long long)((double)(R.hw - hw) * 4294967296.0);   // >= 0, 32.32
+        const long long D = __float2ll_rz((R.hw - hw) * 4294967296.0f);   // >= 0, in 32.32 units
         R.A0 += D;
-        R.hw -= (float)((double)D * (1.0 / 4294967296.0));
+        R.hw -= __ll2float_rn(D) * (1.0f / 4294967296.0f);
         R.kc = min(R.kc, (int)floorf(2.f * R.hw) + 1);
     }
 }

@@ -257,12 +257,20 @@ def run_cnsf(args):
     back_host = torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory()
     img_dev = torch.empty_like(img)
 
+    copy_stream = torch.cuda.Stream(dev)
+
     def e2e_step():
+        # the sinogram's download overlaps the back projection (side stream)
         img_dev.copy_(img_host, non_blocking=True)
         cnsf.forward_project(geom, img_dev, out=sino)
+        fp_done = torch.cuda.Event()
+        fp_done.record()
         cnsf.back_project(geom, sino, out=back)
-        sino_host.copy_(sino, non_blocking=True)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(fp_done)
+            sino_host.copy_(sino, non_blocking=True)
         back_host.copy_(back, non_blocking=True)
+        torch.cuda.current_stream(dev).wait_stream(copy_stream)
 
     for _ in range(3):
         e2e_step()

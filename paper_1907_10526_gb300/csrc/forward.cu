@@ -106,9 +106,9 @@ __device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, c
 __device__ __forceinline__ void fx_window(long long A, int &ilo, float &rho)
 {
     // first candidate ilo = ceil(f - hw); rho = ilo - (f - hw) in [0, 1) from the low word
+    // (an integer-to-float conversion on the XU pipe instead of bit operations on the ALU pipe)
     ilo = (int)(A >> 32) + (((unsigned)A) != 0u ? 1 : 0);
-    unsigned nl = 0u - (unsigned)A;
-    rho = __uint_as_float(0x3f800000u | (nl >> 9)) - 1.0f;
+    rho = __uint2float_rn(0u - (unsigned)A) * (1.0f / 4294967296.0f);
 }
 
 template <int KC>

@@ -229,3 +229,27 @@ def test_e4_ladder_smallest_rung(cnsf, dt):
     y_ref = oracle.forward(g, img)
     assert rel(_fwd(cnsf, geom, img, dt), y_ref) < TOL[dt]
     assert rel(_bwd(cnsf, geom, y_ref, dt), oracle.back(g, y_ref)) < TOL[dt]
+
+
+@pytest.mark.parametrize("which", ["config3_2048", "ladder_2048"])
+def test_largest_workloads_sampled(cnsf, which):
+    """The largest sizes the bench runs, FP32, in its launch configuration: the 2048^2 x 1440
+    x 1536 reconstruction geometry and the 2048 mm / 6499-cell rung of the run-time ladder;
+    sampled rays and pixels against the oracle, and the adjoint identity on the full
+    arrays."""
+    from synth import e4_geometry
+    g = config_geometry(3) if which == "config3_2048" else e4_geometry(2048)
+    geom = cnsf.Geometry(g)
+    img = ellipse_phantom(2048, 20, 2.0, seed=33)
+    c = torch.tensor(img, dtype=torch.float32, device="cuda")
+    y = cnsf.forward_project(geom, c)
+    rng = np.random.default_rng(9)
+    views, cells = rng.integers(0, g.n_views, 150), rng.integers(0, g.n_det, 150)
+    assert rel(y.double().cpu().numpy()[views, cells], oracle.forward_rays(g, img, views, cells)) < 1e-5
+    s = torch.tensor(rng.uniform(0, 1, (g.n_views, g.n_det)), dtype=torch.float32, device="cuda")
+    x = cnsf.back_project(geom, s)
+    pix = rng.integers(0, g.nx * g.ny, 100)
+    assert rel(x.double().cpu().numpy().ravel()[pix], oracle.back_pixels(g, s.double().cpu().numpy(), pix)) < 1e-5
+    lhs = float((y.double() * s.double()).sum())
+    rhs = float((c.double() * x.double()).sum())
+    assert abs(lhs - rhs) / abs(lhs) < 1e-5

@@ -103,19 +103,22 @@ __device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, c
     return s;
 }
 
-__device__ __forceinline__ void fx_window(long long A, int &ilo, float &rho)
+// The walk state is Bc = A + 2^32 - 1, A the 32.32 fixed point of f - hw: its high word is
+// the first candidate ilo = ceil(f - hw) and its low word l gives rho = ilo - (f - hw) =
+// 1 - (l + 1)/2^32 (to 2^-32; 0 when f - hw is an integer), so a line's window costs no
+// ALU-pipe instruction: the high word is a register of the pair, the low word goes through
+// an integer-to-float conversion (XU pipe) and one FMA.
+__device__ __forceinline__ void fx_window(long long Bc, int &ilo, float &rho)
 {
-    // first candidate ilo = ceil(f - hw); rho = ilo - (f - hw) in [0, 1) from the low word
-    // (an integer-to-float conversion on the XU pipe instead of bit operations on the ALU pipe)
-    ilo = (int)(A >> 32) + (((unsigned)A) != 0u ? 1 : 0);
-    rho = __uint2float_rn(0u - (unsigned)A) * (1.0f / 4294967296.0f);
+    ilo = (int)(Bc >> 32);
+    rho = fmaf(__uint2float_rn((unsigned)Bc), -1.0f / 4294967296.0f, 1.0f);
 }
 
 template <int KC>
 __device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ base, int pitch, float B,
                                        float p, float qiC, float iC, float hC)
 {
-    long long A = R.A0;
+    long long A = R.A0 + 0xFFFFFFFFLL;   // ceil-ready walk state (fx_window)
     const long long G = R.G;
     float2 er2 = make_float2(R.e0, R.e0 + R.de);
     const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);

@@ -70,6 +70,18 @@ def test_asd_pocs_ref_projector_fp64(cnsf):
     assert rel(got, ref) < 1e-9
 
 
+def test_asd_pocs_data_tolerance_fp64(cnsf):
+    """With a data tolerance the TV step shrinks only while |A x - y| exceeds it (an extra
+    forward projection per iteration); the same decisions as the oracle's."""
+    g = G48
+    geom = cnsf.Geometry(g)
+    y = oracle.forward(g, _phantom(48))
+    for tol in (1.0, 1e3):   # below and above the residuals reached: both branches taken
+        ref = oracle.asd_pocs(g, y, 6, subsets=4, tv_eps=0.1, data_tol=tol)
+        got = cnsf.asd_pocs(geom, torch.tensor(y, device="cuda"), 6, subsets=4, tv_eps=0.1, data_tol=tol)
+        assert rel(got.cpu().numpy(), ref) < 1e-9
+
+
 def test_asd_pocs_fp32_and_determinism(cnsf):
     g = G48
     geom = cnsf.Geometry(g)

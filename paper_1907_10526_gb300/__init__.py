@@ -19,7 +19,7 @@ from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, AsdPocsParams, CnsfError, G
 
 __all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
            "count_nonzeros", "forward_project_noalloc", "asd_pocs",
-           "sirt", "cgls", "cgls_batched", "SolverWorkspace", "BatchedSolverWorkspace", "Projector", "project",
+           "sirt", "cgls", "cgls_batched", "SolverWorkspace", "BatchedSolverWorkspace", "Projector", "ReferenceProjector", "project",
            "CnsfError"]
 
 
@@ -223,7 +223,21 @@ class SolverWorkspace:
         self.nbytes = n
 
 
+def _on_host(run, geom: Geometry, sino: torch.Tensor, x0: Optional[torch.Tensor]):
+    """Host (CPU) tensors: copy to the geometry's device, run there, copy the image back
+    (into x0 when it was given)."""
+    xd = None if x0 is None else x0.to(geom.device)
+    out = run(sino.to(geom.device), xd)
+    res = out.cpu()
+    if x0 is not None:
+        x0.copy_(res)
+        return x0
+    return res
+
+
 def _solver(name, fn, geom, sino, iters, x0, ws, stream, extra):
+    if sino.device.type != "cuda":
+        return _on_host(lambda sd, xd: _solver(name, fn, geom, sd, iters, xd, ws, stream, extra), geom, sino, x0)
     if sino.shape != geom.sino_shape:
         raise ValueError(f"{name}: sinogram shape {tuple(sino.shape)}, expected {geom.sino_shape}")
     sino = sino.contiguous()
@@ -271,6 +285,8 @@ def cgls_batched(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[to
     """CGLS on a batch of sinograms [B, n_views, n_det] of one geometry (device); x0
     [B, ny, nx] (updated in place) or zeros.  Each image's iterates do not depend on the
     other members of the batch."""
+    if sino.device.type != "cuda":
+        return _on_host(lambda sd, xd: cgls_batched(geom, sd, iters, xd, ws, resume, stream), geom, sino, x0)
     if sino.dim() != 3 or tuple(sino.shape[1:]) != geom.sino_shape:
         raise ValueError(f"cgls_batched: sinograms {tuple(sino.shape)}, expected [B, {geom.sino_shape}]")
     B = int(sino.shape[0])
@@ -304,6 +320,9 @@ def asd_pocs(geom: Geometry, sino: torch.Tensor, iters: int, x0: Optional[torch.
     unknown = set(params) - set(p)
     if unknown:
         raise TypeError(f"asd_pocs: unknown parameters {sorted(unknown)}")
+    if sino.device.type != "cuda":
+        return _on_host(lambda sd, xd: asd_pocs(geom, sd, iters, xd, subsets, projector, stream, **params), geom,
+                        sino, x0)
     p.update(params)
     if sino.shape != geom.sino_shape:
         raise ValueError(f"asd_pocs: sinogram shape {tuple(sino.shape)}, expected {geom.sino_shape}")
@@ -348,6 +367,21 @@ class Projector(torch.autograd.Function):
         return back_project(ctx.geom, grad_y.contiguous()), None
 
 
-def project(geom: Geometry, image: torch.Tensor) -> torch.Tensor:
-    """Differentiable forward projection (see Projector)."""
-    return Projector.apply(image, geom)
+class ReferenceProjector(torch.autograd.Function):
+    """y = A_ref c with the reference projector's exact entries, differentiable the same way
+    (backward = the reference back projection, its exact adjoint)."""
+
+    @staticmethod
+    def forward(ctx, image, geom):
+        ctx.geom = geom
+        return forward_project_ref(geom, image)
+
+    @staticmethod
+    def backward(ctx, grad_y):
+        return back_project_ref(ctx.geom, grad_y.contiguous()), None
+
+
+def project(geom: Geometry, image: torch.Tensor, exact: bool = False) -> torch.Tensor:
+    """Differentiable forward projection (see Projector); ``exact=True`` uses the reference
+    projector's bin-averaged exact chords instead of the CNSF entries."""
+    return (ReferenceProjector if exact else Projector).apply(image, geom)

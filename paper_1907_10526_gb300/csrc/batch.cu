@@ -60,22 +60,25 @@ struct Acc {
 #pragma unroll
         for (int k = 0; k < NB4; ++k) v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    // packed FP32x2 (FFMA2/FADD2): two images per instruction, the same rounding per image
     __device__ __forceinline__ void fma_from(float w, const float4 *__restrict__ p)
     {
+        const float2 w2 = make_float2(w, w);
 #pragma unroll
         for (int k = 0; k < NB4; ++k) {
             const float4 c = __ldg(p + k);
-            v[k].x = fmaf(w, c.x, v[k].x);
-            v[k].y = fmaf(w, c.y, v[k].y);
-            v[k].z = fmaf(w, c.z, v[k].z);
-            v[k].w = fmaf(w, c.w, v[k].w);
+            const float2 lo = __ffma2_rn(w2, make_float2(c.x, c.y), make_float2(v[k].x, v[k].y));
+            const float2 hi = __ffma2_rn(w2, make_float2(c.z, c.w), make_float2(v[k].z, v[k].w));
+            v[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
     }
     __device__ __forceinline__ void add(const Acc &o)
     {
 #pragma unroll
         for (int k = 0; k < NB4; ++k) {
-            v[k].x += o.v[k].x; v[k].y += o.v[k].y; v[k].z += o.v[k].z; v[k].w += o.v[k].w;
+            const float2 lo = __fadd2_rn(make_float2(v[k].x, v[k].y), make_float2(o.v[k].x, o.v[k].y));
+            const float2 hi = __fadd2_rn(make_float2(v[k].z, v[k].w), make_float2(o.v[k].z, o.v[k].w));
+            v[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
     }
 };
@@ -85,14 +88,13 @@ template <int KC, int NB4>
 __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__restrict__ base, int pitch4, float B,
                                               float p, float qiC, float iC, float hC, Acc<NB4> &acc)
 {
-    long long A = R.A0;
+    long long A = R.A0 + 0xFFFFFFFFLL;   // ceil-ready: high word = ceil(f - hw)
     float er = R.e0;
     Acc<NB4> part;
     part.zero();
     for (int rr = 0; rr < R.nrows; ++rr) {
-        const int ilo = (int)(A >> 32) + (((unsigned)A) != 0u ? 1 : 0);
-        const unsigned nl = 0u - (unsigned)A;
-        const float u0 = (__uint_as_float(0x3f800000u | (nl >> 9)) - 1.0f) - R.hw;
+        const int ilo = (int)(A >> 32);
+        const float u0 = fmaf(__uint2float_rn((unsigned)A), -1.0f / 4294967296.0f, 1.0f) - R.hw;
         const float4 *rp = base + (long long)ilo * NB4;
 #pragma unroll
         for (int m = 0; m < KC; ++m) {

@@ -92,3 +92,30 @@ def test_batch16_finite_differences_fp64(cnsf, batch16):
         rm = cnsf.forward_project(geom, cm) - y[b]
         fd = float(((rp - rm) * (rp + rm)).sum()) / (2 * eps)    # L(c+) - L(c-) without cancellation
         assert fd == pytest.approx(float(grad[b, r, i]), rel=1e-8, abs=1e-8)
+
+
+def test_exact_projector_gradient(cnsf):
+    """project(..., exact=True): the reference projector with its adjoint as backward;
+    gradient of ||A_ref c - y||^2 against central differences (FP64) and against the
+    oracle's A_ref^T of the residual."""
+    g = FanGeometry(nx=20, ny=20, n_views=12, n_det=40, d_po=60.0, d_ps=130.0)
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(13)
+    c0 = torch.tensor(rng.uniform(0, 1, (20, 20)), device="cuda")
+    y = torch.tensor(rng.uniform(0, 10, (12, 40)), device="cuda")
+    c = c0.clone().requires_grad_(True)
+    r = cnsf.project(geom, c, exact=True) - y
+    (grad,) = torch.autograd.grad((r * r).sum(), c)
+    res = (oracle.forward_ref(g, c0.cpu().numpy(), 20) - y.cpu().numpy())
+    want = 2.0 * oracle.back_ref(g, res, 20)
+    assert np.linalg.norm(grad.cpu().numpy() - want) / np.linalg.norm(want) < 1e-11
+    eps = 1e-3
+    for _ in range(8):
+        rr, i = int(rng.integers(20)), int(rng.integers(20))
+        cp, cm = c0.clone(), c0.clone()
+        cp[rr, i] += eps
+        cm[rr, i] -= eps
+        rp = cnsf.forward_project_ref(geom, cp) - y
+        rm = cnsf.forward_project_ref(geom, cm) - y
+        fd = float(((rp - rm) * (rp + rm)).sum()) / (2 * eps)
+        assert fd == pytest.approx(float(grad[rr, i]), rel=1e-8, abs=1e-10)

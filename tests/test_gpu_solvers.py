@@ -140,3 +140,22 @@ def test_cgls_reduces_error(cnsf, downscale):
         x = cnsf.cgls(geom, yt, it).cpu().numpy()
         errs.append(np.linalg.norm(x - img) / np.linalg.norm(img))
     assert errs[0] > errs[1] > errs[2]
+
+
+def test_solvers_accept_host_tensors():
+    """CPU sinograms go through the device and the image comes back (the same result as
+    device tensors), for every driver."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1907_10526_gb300 as cnsf
+    from synth import FanGeometry
+    g = FanGeometry(nx=32, ny=32, n_views=24, n_det=64, d_po=100.0, d_ps=220.0)
+    geom = cnsf.Geometry(g)
+    y = torch.rand(24, 64, dtype=torch.float64)
+    for fn in (lambda s: cnsf.sirt(geom, s, 3), lambda s: cnsf.cgls(geom, s, 3),
+               lambda s: cnsf.asd_pocs(geom, s, 2, subsets=3, tv_eps=0.1)):
+        xh = fn(y)
+        xd = fn(y.cuda())
+        assert xh.device.type == "cpu" and torch.equal(xh, xd.cpu())
+    xb = cnsf.cgls_batched(geom, torch.stack([y, 2 * y]), 3)
+    assert xb.device.type == "cpu" and xb.shape == (2, 32, 32)

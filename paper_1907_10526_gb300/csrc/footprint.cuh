@@ -11,8 +11,9 @@
 // with p = (B - C)/2, q = (B + C)/2.  The C/(2C) ramps carry their own factor C, so
 // no step divides a difference by a small width: the 1/(zeta1 zeta2 tau') of the
 // literal divided-difference form of Eq. (18) never appears, and C = 0 (axis-aligned
-// rays, M_0 = delta) needs no branch (v is then 0 or 1).  window_diff returns
-// B * 2e * M(x) for x = |s'|.
+// rays, M_0 = delta) needs no branch (v is then 0 or 1).  The one remaining difference
+// G(x + e) - G(x - e) ~ 2e T(x) loses about log2(B / 2e) bits (a few at the blur widths
+// of fan-beam CT).  window_diff returns B * 2e * M(x) for x = |s'|.
 #pragma once
 
 #include <cuda_runtime.h>

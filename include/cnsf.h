@@ -252,6 +252,24 @@ CNSF_API int cnsf_asd_pocs(const cnsf_geometry *const *subsets, int32_t n_subset
 CNSF_API int cnsf_forward_project_noalloc(const cnsf_geometry *geom, const void *image, void *sino,
                                           int32_t batch, int32_t dtype, void *stream);
 
+/* Projection plans (the paper has no counterpart: a host-side convenience for iterative
+ * use).  A plan captures one projection call -- op CNSF_OP_FORWARD, CNSF_OP_BACK,
+ * CNSF_OP_FORWARD_REF or CNSF_OP_BACK_REF with the fixed device buffers `in` and `out`,
+ * batch and dtype, as for the corresponding cnsf_*_project* call -- into a CUDA graph on
+ * the current device; cnsf_plan_launch replays it on `stream` with one graph launch
+ * (asynchronous, the same result as the direct call; the buffers' contents are read and
+ * written at replay time, their addresses are fixed at creation).  The geometry and the
+ * buffers must outlive the plan.  A plan is replayed by one stream at a time (its
+ * scratch allocations belong to the graph).  Creation is synchronous with respect to the
+ * host and launches nothing; errors as the corresponding call, CNSF_ERR_INVALID for an
+ * unknown op or a launch from another device. */
+typedef struct cnsf_plan cnsf_plan;
+typedef enum { CNSF_OP_FORWARD = 0, CNSF_OP_BACK = 1, CNSF_OP_FORWARD_REF = 2, CNSF_OP_BACK_REF = 3 } cnsf_op;
+CNSF_API int cnsf_plan_create(const cnsf_geometry *geom, int32_t op, const void *in, void *out, int32_t batch,
+                              int32_t dtype, cnsf_plan **plan);
+CNSF_API int cnsf_plan_launch(const cnsf_plan *plan, void *stream);
+CNSF_API void cnsf_plan_destroy(cnsf_plan *plan);   /* NULL is allowed; no replay may be pending */
+
 /* Status code to a static English string. */
 CNSF_API const char *cnsf_status_string(int status);
 

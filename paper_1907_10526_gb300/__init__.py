@@ -18,7 +18,7 @@ import torch
 from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, AsdPocsParams, CnsfError, GeometryDesc, check, lib  # noqa: F401
 
 __all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
-           "count_nonzeros", "forward_project_noalloc", "asd_pocs",
+           "count_nonzeros", "forward_project_noalloc", "asd_pocs", "Plan",
            "sirt", "cgls", "cgls_batched", "SolverWorkspace", "BatchedSolverWorkspace", "Projector", "ReferenceProjector", "project",
            "CnsfError"]
 
@@ -207,6 +207,55 @@ def count_nonzeros(geom: Geometry, stream: Optional[torch.cuda.Stream] = None) -
                                       ctypes.c_void_p(_stream_ptr(stream, geom.device))),
               "cnsf_count_nonzeros")
     return int(n.value)
+
+
+class Plan:
+    """One projection call captured into a CUDA graph for repeated use on fixed buffers.
+
+    ``op`` is "forward", "back", "forward_ref" or "back_ref"; ``src`` and ``dst`` are the
+    device tensors of that call (shapes and dtype as for the direct function, batch from
+    the leading dimensions).  ``run()`` replays the call on ``stream`` (default: current
+    stream) with one graph launch and returns ``dst``; it reads ``src``'s contents at
+    replay time.  Keep ``src``/``dst`` alive and at the same addresses while the plan is
+    used; one stream at a time.
+    """
+
+    _OPS = {"forward": 0, "back": 1, "forward_ref": 2, "back_ref": 3}
+
+    def __init__(self, geom: Geometry, op: str, src: torch.Tensor, dst: torch.Tensor):
+        if op not in self._OPS:
+            raise ValueError(f"Plan: op is one of {sorted(self._OPS)}")
+        fwd = op.startswith("forward")
+        in_shape, out_shape = (geom.image_shape, geom.sino_shape) if fwd else (geom.sino_shape, geom.image_shape)
+        lead, batch = _prep(src, in_shape, "Plan")
+        if src.device.type != "cuda" or dst.device != src.device or src.device != geom.device:
+            raise ValueError("Plan: src and dst must be device tensors on the geometry's device")
+        if (not src.is_contiguous() or not dst.is_contiguous() or dst.dtype != src.dtype
+                or tuple(dst.shape) != tuple(lead) + out_shape):
+            raise ValueError("Plan: bad src/dst")
+        self.geom, self.src, self.dst = geom, src, dst
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(geom.device):
+            check(lib.cnsf_plan_create(geom.handle, self._OPS[op], ctypes.c_void_p(src.data_ptr()),
+                                       ctypes.c_void_p(dst.data_ptr()), batch, _dtype_code(src.dtype),
+                                       ctypes.byref(self._h)), "cnsf_plan_create")
+
+    def run(self, stream=None) -> torch.Tensor:
+        with torch.cuda.device(self.geom.device):
+            check(lib.cnsf_plan_launch(self._h, ctypes.c_void_p(_stream_ptr(stream, self.geom.device))),
+                  "cnsf_plan_launch")
+        return self.dst
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.cnsf_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class SolverWorkspace:

@@ -255,6 +255,39 @@ int cnsf_asd_pocs(const cnsf_geometry *const *subsets, int32_t n_subsets, const 
     }
 }
 
+int cnsf_plan_create(const cnsf_geometry *geom, int32_t op, const void *in, void *out, int32_t batch, int32_t dtype,
+                     cnsf_plan **plan)
+{
+    try {
+        if (!plan) return CNSF_ERR_INVALID;
+        *plan = nullptr;
+        if (op < CNSF_OP_FORWARD || op > CNSF_OP_BACK_REF) return CNSF_ERR_INVALID;
+        int s = check_call(geom, in, out, batch, dtype);
+        if (s != CNSF_OK) return s;
+        return plan_create(geom, op, in, out, batch, dtype, plan);
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
+int cnsf_plan_launch(const cnsf_plan *plan, void *stream)
+{
+    try {
+        if (!plan) return CNSF_ERR_INVALID;
+        return plan_launch(plan, (cudaStream_t)stream);
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
+void cnsf_plan_destroy(cnsf_plan *plan)
+{
+    try {
+        plan_destroy(plan);
+    } catch (...) {
+    }
+}
+
 const char *cnsf_status_string(int status)
 {
     switch (status) {

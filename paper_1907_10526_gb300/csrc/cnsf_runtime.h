@@ -30,6 +30,11 @@ int launch_forward_ref(const cnsf_geometry *geo, const void *img, void *sino, in
 int launch_back_ref(const cnsf_geometry *geo, const void *sino, void *img, int batch, int dtype,
                     cudaStream_t stream);
 
+// Projection plans (plan.cu): op 0 forward, 1 back, 2 reference forward, 3 reference back.
+int plan_create(const cnsf_geometry *geo, int op, const void *in, void *out, int batch, int dtype, cnsf_plan **res);
+int plan_launch(const cnsf_plan *p, cudaStream_t stream);
+void plan_destroy(cnsf_plan *p);
+
 // Forward projection into caller-provided scratch (bytes from forward_scratch_bytes).
 size_t forward_scratch_bytes(const cnsf_geometry *geo, int batch, int dtype);
 int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,

@@ -97,7 +97,7 @@ typedef struct {
  * lengths and, for the fan beams, d_ps <= d_po and images that reach within two
  * pixels of the source circle (the footprint model needs every pixel in front of the
  * source), and arcs that reach 80 degrees from -u; CNSF_ERR_UNSUPPORTED for an unknown
- * detector kind.
+ * detector kind or n_views * n_det or n_x * n_y of 2^31 or more.
  * On success *out owns device memory until cnsf_geometry_destroy. */
 CNSF_API int cnsf_geometry_create(const cnsf_geometry_desc *desc, cnsf_geometry **out);
 

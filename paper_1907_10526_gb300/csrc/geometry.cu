@@ -31,6 +31,9 @@ static int validate(const cnsf_geometry_desc *d)
     if (d->n_x > (1 << 16) || d->n_y > (1 << 16) || d->n_det > (1 << 20) || d->n_views > (1 << 20))
         return CNSF_ERR_INVALID;
     if (!(d->pixel_mm > 0) || !(d->det_spacing_mm > 0) || !(d->det_width_mm > 0)) return CNSF_ERR_INVALID;
+    // rays and pixels are indexed with 32-bit integers in the kernels
+    if ((long long)d->n_views * d->n_det >= (1LL << 31) || (long long)d->n_x * d->n_y >= (1LL << 31))
+        return CNSF_ERR_UNSUPPORTED;
     if (!std::isfinite(d->center_x_mm) || !std::isfinite(d->center_y_mm) || !std::isfinite(d->det_offset_mm))
         return CNSF_ERR_INVALID;
     if (d->detector != CNSF_DETECTOR_FLAT && d->detector != CNSF_DETECTOR_ARC &&

@@ -43,6 +43,8 @@ def test_invalid_geometries_refused_without_gpu():
     for d in bad:
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
     from paper_1907_10526_gb300._lib import CNSF_ERR_UNSUPPORTED
+    big = GeometryDesc(8, 8, 1.0, 0, 0, 1 << 20, None, 1 << 12, 1, 1, 0, 30, 60, 0)   # 2^32 rays
+    assert lib.cnsf_geometry_create(ctypes.byref(big), ctypes.byref(h)) == CNSF_ERR_UNSUPPORTED
     for kind in (3, -1):   # flat (0) and arc (1) fan beams and parallel beam (2) are built
         d = GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 30, 60, kind)
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_UNSUPPORTED

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -50,3 +52,17 @@ def test_invalid_geometries_refused_without_gpu():
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_UNSUPPORTED
     assert lib.cnsf_forward_project(None, None, None, 1, 0, None) == CNSF_ERR_INVALID
     assert lib.cnsf_status_string(0) == b"ok"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the built library the package does not load."""
+    from paper_1907_10526_gb300 import _lib
+    with pytest.raises(ImportError):
+        _lib.load(str(tmp_path / "absent.so"))
+
+
+def test_every_python_signature_is_exported():
+    from paper_1907_10526_gb300 import _lib
+    lib = ctypes.CDLL(_lib.LIB_PATH)
+    for name in _lib._SIGNATURES:
+        assert hasattr(lib, name), name

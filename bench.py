@@ -332,6 +332,7 @@ def run_cnsf(args):
         line["e4_ladder"] = bench_e4_ladder(dev)
         line["reference_projector"] = bench_reference(dev)
         line["asd_pocs_limited_view"] = bench_asd_pocs(dev)
+        line["detector_kinds_512x720"] = bench_detector_kinds(dev)
         line["p50_recon_latency_s"] = line["serving"]["batched"].get("p50_s")
         line["p99_recon_latency_s"] = line["serving"]["batched"].get("p99_s")
     if rank == 0 and not args.no_cpu_baseline:
@@ -500,6 +501,35 @@ def bench_reference(dev):
         out[f"{n}mm_{n_det}cells_tau0.5_D{int(d)}"] = {
             "max_abs_err": float((ya - yr).abs().max()), "peak": float(yr.abs().max()),
             "rel_l2": float((ya - yr).norm() / yr.norm())}
+    return out
+
+
+def bench_detector_kinds(dev, reps: int = 5):
+    """The headline workload (512^2, 720 views, 888 cells of 1 mm) with the arc detector and
+    with parallel rays: FP32 forward and back times, best of ``reps``."""
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import config_geometry, phantom_for_config
+    out = {}
+    x = torch.tensor(phantom_for_config(2), dtype=torch.float32, device=dev)
+    for kind in ("flat", "arc", "parallel"):
+        g = config_geometry(2).with_(detector=kind)
+        geom = cnsf.Geometry(g)
+        y = cnsf.forward_project(geom, x)
+        c = cnsf.back_project(geom, y)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fp, bp = [], []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev[0].record()
+            cnsf.forward_project(geom, x, out=y)
+            ev[1].record()
+            cnsf.back_project(geom, y, out=c)
+            ev[2].record()
+            torch.cuda.synchronize()
+            fp.append(ev[0].elapsed_time(ev[1]))
+            bp.append(ev[1].elapsed_time(ev[2]))
+        out[kind] = {"fp_ms": min(fp), "bp_ms": min(bp), "nonzeros": cnsf.count_nonzeros(geom)}
     return out
 
 

@@ -267,3 +267,14 @@ def test_thin_cells(cnsf, tau):
     for dt in (torch.float64, torch.float32):
         assert rel(_fwd(cnsf, geom, img, dt), y_ref) < TOL[dt]
         assert rel(_bwd(cnsf, geom, y_ref, dt), oracle.back(g, y_ref)) < TOL[dt]
+
+
+def test_config2_full_arrays_fp32(cnsf, cfg2):
+    """The 512^2 x 720 x 888 workload compared element by element over the whole sinogram
+    and the whole back projection (the oracle takes a few seconds per direction on the
+    host cores)."""
+    g, geom, img, y = cfg2
+    y_ref = oracle.forward(g, img)
+    assert rel(y.double().cpu().numpy(), y_ref) < 1e-5
+    x = cnsf.back_project(geom, torch.tensor(y_ref, dtype=torch.float32, device="cuda"))
+    assert rel(x.double().cpu().numpy(), oracle.back(g, y_ref)) < 1e-5

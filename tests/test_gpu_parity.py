@@ -278,3 +278,24 @@ def test_config2_full_arrays_fp32(cnsf, cfg2):
     assert rel(y.double().cpu().numpy(), y_ref) < 1e-5
     x = cnsf.back_project(geom, torch.tensor(y_ref, dtype=torch.float32, device="cuda"))
     assert rel(x.double().cpu().numpy(), oracle.back(g, y_ref)) < 1e-5
+
+
+def test_one_geometry_on_concurrent_streams(cnsf):
+    """A geometry is read-only after creation: projections issued on four streams at once
+    give the results of one-at-a-time calls, bitwise."""
+    g = RAGGED
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(17)
+    xs = [torch.tensor(rng.uniform(0, 1, (g.ny, g.nx)), dtype=torch.float32, device="cuda") for _ in range(4)]
+    want_f = [cnsf.forward_project(geom, x) for x in xs]
+    want_b = [cnsf.back_project(geom, y) for y in want_f]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    got_f, got_b = [None] * 4, [None] * 4
+    torch.cuda.synchronize()
+    for k in range(4):
+        with torch.cuda.stream(streams[k]):
+            got_f[k] = cnsf.forward_project(geom, xs[k], stream=streams[k])
+            got_b[k] = cnsf.back_project(geom, got_f[k], stream=streams[k])
+    torch.cuda.synchronize()
+    for k in range(4):
+        assert torch.equal(got_f[k], want_f[k]) and torch.equal(got_b[k], want_b[k])

@@ -101,3 +101,21 @@ def test_cgls_batched_matches_single_problems():
             assert torch.equal(xb[k], xk)
             xs = cnsf.cgls(geom, yb[k].clone(), it)
             assert float((xb[k] - xs).norm() / xs.norm()) < tol
+
+
+def test_batched_admission_by_footprint(served):
+    """Continuous batching under a tight HBM budget: batches shrink to what fits, the
+    budget is never exceeded, and every request is served or rejected by its own size."""
+    serve, server, reqs = served
+    burst = [serve.ReconRequest(r.rid, 1e-6 * k, r.n, r.n_views, r.sino, r.iters) for k, r in enumerate(reqs)]
+    small = min(burst, key=lambda r: r.n * r.n_views)
+    budget = int(server.batch_footprint(small.n, small.n_views, 2) * 1.2)
+    tight = serve.ReconServer(hbm_budget_bytes=budget, max_active=4)
+    res = tight.run(burst, mode="batched")
+    assert tight.max_used <= budget
+    for r, x in zip(burst, res):
+        if tight.batch_footprint(r.n, r.n_views, 1) > budget:
+            assert x.status.startswith("rejected")
+        else:
+            assert x.status == "ok"
+    assert any(x.status == "ok" for x in res)

@@ -159,3 +159,18 @@ def test_solvers_accept_host_tensors():
         assert xh.device.type == "cpu" and torch.equal(xh, xd.cpu())
     xb = cnsf.cgls_batched(geom, torch.stack([y, 2 * y]), 3)
     assert xb.device.type == "cpu" and xb.shape == (2, 32, 32)
+
+
+def test_cgls_batched_resume_continues():
+    """cgls_batched(k) then resume(m) equals cgls_batched(k + m), bitwise (the state lives in
+    the workspace)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1907_10526_gb300 as cnsf
+    g = FanGeometry(nx=40, ny=40, n_views=30, n_det=80, d_po=120.0, d_ps=260.0)
+    geom = cnsf.Geometry(g)
+    y = torch.rand(3, 30, 80, device="cuda")
+    ws = cnsf.BatchedSolverWorkspace(geom, 3, torch.float32)
+    x = cnsf.cgls_batched(geom, y, 4, ws=ws)
+    x = cnsf.cgls_batched(geom, y, 3, x0=x, ws=ws, resume=True)
+    assert torch.equal(x, cnsf.cgls_batched(geom, y, 7))

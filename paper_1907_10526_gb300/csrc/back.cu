@@ -7,7 +7,8 @@
 // remainder, so that FP32 carries the sub-cell position of every pixel to ~1e-6 cells;
 // the per-pixel work is then a handful of FP32 FMAs and one reciprocal.  The cell window
 // is bounded per pixel from the footprint widths of the ray through the pixel centre
-// (BpWindow), so few cells outside the support are visited.
+// (BpWindow), so few cells outside the support are visited.  In FP32 a thread owns a 2 x 2
+// pixel quad and gathers it as two pixel pairs, each pair sharing its cell-table loads.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +22,7 @@ namespace cnsf {
 
 constexpr int BP_T = 16;        // tile side (pixels)
 constexpr int BP_CHUNK = 256;   // views whose tile coefficients are staged at once
+constexpr int BP_QUAD_THREADS = BP_T * BP_T / 4;   // FP32 kernel: one thread per 2 x 2 pixel quad
 
 template <typename T>
 struct alignas(16) TileViewS {
@@ -48,11 +50,6 @@ __device__ __forceinline__ float bp_sigma(const TV &T, float di, float dr, float
     return fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);
 }
 
-// One view of the pixel's gather in FP32, two cells (2m, 2m + 1) per step with packed FP32x2
-// arithmetic on even-aligned pair tables.  Aligning the window to even cells adds at most
-// one cell at each end; those cells lie outside the window, which bounds the support with
-// margin, so their entries are exactly 0 (a padding cell past n_det has sinogram value 0).
-// The normalisation h^2/(2B) = h^2/(4(p + C/2)) is folded into the division by tau'.
 // The FP32 per-(tile, view) coefficients from the FP64 projection of the tile centre.
 __device__ __forceinline__ void tile_view_f32(const GeomConsts &g, double c, double s, double it, double rt,
                                               TileViewS<float> &T, int &J)
@@ -101,122 +98,185 @@ int build_tile_view_table(cnsf_geometry *geo)
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
-// Arc detector: |s'| = R sin(dg d) for a cell d cells from the pixel's projection, R the
-// pixel's distance from the source; with dg d below ~0.05 rad, R dg d (1 - (dg d)^2/6) is
-// that sine to ~1e-9 relative (the next term of the series).
+// Per-(pixel, view) set-up of the gather: depth, detector coordinate, cell coordinate and
+// the pixel's cell window [g0, g1] (empty, as [BIG, -BIG], for a pixel outside the image or
+// whose window misses the detector).
+struct BpPixel {
+    float Dn, yp, sig, G;
+    int g0, g1;
+};
+
+constexpr int BP_EMPTY = 1 << 29;
+
 template <bool ARC>
-__device__ __forceinline__ float2 bp_view_f32(const TileViewS<float> &T, int J, float di, float dr,
-                                              const BpArgs &a, int nd, const float2 *__restrict__ y2row,
-                                              const float *__restrict__ boxrow, const float *__restrict__ cell2)
+__device__ __forceinline__ BpPixel bp_pixel_f32(const TileViewS<float> &T, int J, float di, float dr, bool in,
+                                                const BpArgs &a, int nd)
 {
-    const float Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));   // depth along u
-    const float yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));    // coordinate along w
-    const float rD = rcp_approx(Dn);
-    const float sig = bp_sigma<ARC>(T, di, dr, Dn, yp, rD, a.kscale);   // cell coordinate - J
-    // footprint widths of the ray through the pixel centre: h(|n_x| + |n_y|) * rho
-    const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
+    BpPixel P;
+    P.Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
+    P.yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
+    const float rD = rcp_approx(P.Dn);
+    P.sig = bp_sigma<ARC>(T, di, dr, P.Dn, P.yp, rD, a.kscale);
+    const float za = fmaf(P.yp, T.hc, -P.Dn * T.hs), zb = fmaf(P.yp, T.hs, P.Dn * T.hc);
     const float zs = fabsf(za) + fabsf(zb);
     const float hwc = fmaf(a.kz * zs * rD * rD, fmaf(a.h2, rD, 1.02f), a.ke);
-    const int g0 = J + max((int)ceilf(sig - hwc), -J);               // first and last cell, global
-    const int g1 = J + min((int)floorf(sig + hwc), nd - 1 - J);
-    float2 acc = make_float2(0.f, 0.f);
-    const float2 Dn2 = make_float2(Dn, Dn), yp2 = make_float2(yp, yp);
-    const float2 ne1 = make_float2(-1.f, -1.f), m2 = make_float2(-2.f, -2.f);
-    float2 G2 = Dn2, k2 = make_float2(0.f, 0.f);
-    if (ARC) {
-        const float G = sqrtf(fmaf(Dn, Dn, yp * yp)) * a.dg;
-        G2 = make_float2(G, G);
-        k2 = make_float2(a.nk6, a.nk6);
-    }
-    const int m0 = g0 >> 1, m1 = g1 >> 1;
-    const float d0 = sig - (float)(2 * m0 - J);
-    float2 d = make_float2(d0, d0 - 1.f);
+    const int g0 = J + max((int)ceilf(P.sig - hwc), -J);
+    const int g1 = J + min((int)floorf(P.sig + hwc), nd - 1 - J);
+    const bool live = in && g0 <= g1;
+    P.g0 = live ? g0 : BP_EMPTY;
+    P.g1 = live ? g1 : -BP_EMPTY;
+    P.G = ARC ? sqrtf(fmaf(P.Dn, P.Dn, P.yp * P.yp)) * a.dg : 0.f;
+    return P;
+}
+
+// The two entries of cell pair (2m, 2m + 1) for one pixel in packed FP32x2 arithmetic,
+// divided by the normalising widths (the sinogram weights are applied by the caller): the
+// normalisation h^2/(2B) = h^2/(4(p + C/2)) is folded into the division by tau'.  d holds
+// the two cells' offsets from the pixel's projection, in cells.  Arc detector: |s'| =
+// R sin(dg d), R the pixel's distance from the source; with dg d below ~0.05 rad,
+// R dg d (1 - (dg d)^2/6) is that sine to ~1e-9 relative (the next term of the series).
+template <bool ARC>
+__device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const float (&A)[8], const float (&C)[8],
+                                              float nk6)
+{
+    const float2 ne1 = make_float2(-1.f, -1.f);
+    float2 xs;
+    if (ARC)
+        xs = __fmul2_rn(__fmul2_rn(make_float2(P.G, P.G), d),
+                        __ffma2_rn(__fmul2_rn(d, d), make_float2(nk6, nk6), make_float2(1.f, 1.f)));
+    else
+        xs = __fmul2_rn(__fmul2_rn(make_float2(P.Dn, P.Dn), make_float2(C[0], C[1])), d);
+    const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
+    const float2 e = __ffma2_rn(make_float2(P.Dn, P.Dn), make_float2(C[2], C[3]),
+                                __fmul2_rn(make_float2(P.yp, P.yp), make_float2(C[4], C[5])));
+    const float2 p = make_float2(A[0], A[1]), nhC = make_float2(A[6], A[7]);
+    const float2 w = window_diff2p(x, e, ne1, p, make_float2(A[2], A[3]), make_float2(A[4], A[5]), nhC);
+    const float2 den = __fmul2_rn(__ffma2_rn(nhC, ne1, p), e);                              // (p + C/2) e
+    return make_float2(w.x * rcp_approx(den.x), w.y * rcp_approx(den.y));
+}
+
+// One view of the gather for two pixels a and b of a thread, over the union of their cell
+// windows, two cells (2m, 2m + 1) per step on the even-aligned pair tables.  Each cell pair's
+// constants and sinogram values are loaded once and serve both pixels (the L1 path carries
+// every loaded byte to each lane, so sharing the loads halves that traffic).  A cell of the
+// union outside one pixel's own window, or added by aligning the window to even cells, lies
+// outside that pixel's support (the window bounds the support with margin), so its entry
+// for that pixel is exactly 0; a padding cell past n_det has sinogram value 0.  Returns the
+// two pixels' sums.
+template <bool ARC>
+__device__ __forceinline__ float2 bp_view2_f32(const TileViewS<float> &T, int J, float dia, float dra, bool ina,
+                                               float dib, float drb, bool inb, const BpArgs &a, int nd,
+                                               const float2 *__restrict__ y2row, const float *__restrict__ boxrow,
+                                               const float *__restrict__ cell2)
+{
+    const BpPixel Pa = bp_pixel_f32<ARC>(T, J, dia, dra, ina, a, nd);
+    const BpPixel Pb = bp_pixel_f32<ARC>(T, J, dib, drb, inb, a, nd);
+    const int m0 = min(Pa.g0, Pb.g0) >> 1, m1 = max(Pa.g1, Pb.g1) >> 1;
+    const float off = (float)(2 * m0 - J);
+    float2 da = make_float2(Pa.sig - off, Pa.sig - off - 1.f), db = make_float2(Pb.sig - off, Pb.sig - off - 1.f);
+    const float2 m2 = make_float2(-2.f, -2.f);
+    float2 acca = make_float2(0.f, 0.f), accb = make_float2(0.f, 0.f);
     for (int m = m0; m <= m1; ++m) {
         float A[8], C[8];
         ldg256(boxrow + 8 * m, A);    // p | q/C | 1/C | -C/2, pairs
         ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
         const float2 yv = __ldg(y2row + m);
-        float2 xs;
-        if (ARC)
-            xs = __fmul2_rn(__fmul2_rn(G2, d), __ffma2_rn(__fmul2_rn(d, d), k2, make_float2(1.f, 1.f)));
-        else
-            xs = __fmul2_rn(__fmul2_rn(Dn2, make_float2(C[0], C[1])), d);
-        const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
-        const float2 e = __ffma2_rn(Dn2, make_float2(C[2], C[3]), __fmul2_rn(yp2, make_float2(C[4], C[5])));
-        const float2 p = make_float2(A[0], A[1]), nhC = make_float2(A[6], A[7]);
-        const float2 w = window_diff2p(x, e, ne1, p, make_float2(A[2], A[3]), make_float2(A[4], A[5]), nhC);
-        const float2 den = __fmul2_rn(__ffma2_rn(nhC, ne1, p), e);                              // (p + C/2) e
-        acc = __ffma2_rn(yv, make_float2(w.x * rcp_approx(den.x), w.y * rcp_approx(den.y)), acc);
-        d = __fadd2_rn(d, m2);
+        acca = __ffma2_rn(yv, bp_pair_f32<ARC>(Pa, da, A, C, a.nk6), acca);
+        accb = __ffma2_rn(yv, bp_pair_f32<ARC>(Pb, db, A, C, a.nk6), accb);
+        da = __fadd2_rn(da, m2);
+        db = __fadd2_rn(db, m2);
     }
-    return acc;
+    return make_float2(acca.x + acca.y, accb.x + accb.y);
 }
 
+// FP32 back projection with a 2 x 2 pixel quad per thread (64 threads per 16 x 16 tile, a
+// warp covering 16 x 8 pixels), views in chunks of BP_CHUNK whose tile coefficients are
+// staged in shared memory.  For each (tile, view) the quad is gathered as two pixel pairs
+// along the image axis whose unit step moves the projection least (columns when
+// |d sigma/d row| <= |d sigma/d column|), so the two pixels of a pair reach nearly the same
+// cells and their union window adds little.
 template <bool ARC>
-__global__ void __launch_bounds__(256) bp_f32_kernel(GeomConsts g, const double *__restrict__ view_cs,
-                                                     const float *__restrict__ box2,
-                                                     const float *__restrict__ cell2,
-                                                     const float2 *__restrict__ y2, float *__restrict__ img,
-                                                     BpArgs a, const int *__restrict__ order, int ntx, int nsplit,
-                                                     float *__restrict__ partial, const float4 *__restrict__ tvtab,
-                                                     const int *__restrict__ tjtab)
+__global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts g, const double *__restrict__ view_cs,
+                                                                 const float *__restrict__ box2,
+                                                                 const float *__restrict__ cell2,
+                                                                 const float2 *__restrict__ y2,
+                                                                 float *__restrict__ img, BpArgs a,
+                                                                 const int *__restrict__ order, int ntx, int nsplit,
+                                                                 float *__restrict__ partial,
+                                                                 const float4 *__restrict__ tvtab,
+                                                                 const int *__restrict__ tjtab)
 {
     __shared__ TileViewS<float> tv[BP_CHUNK];
     __shared__ int tj[BP_CHUNK];
-    // 8 warps, each an 8 x 4 patch of the 16 x 16 tile: compact patches project onto few
-    // cells, so a warp's loads of the cell tables touch few cache lines.
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
+    const int tx = 2 * (lane & 7), ty = 8 * warp + 2 * (lane >> 3);
     const int tile = order[blockIdx.x];   // tiles with the most work first
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
-    // blockIdx.y: which part of the views this block gathers (the parts of a tile are summed
-    // afterwards in a fixed order, so the result does not depend on scheduling)
     const long long b = blockIdx.z;
     const int vbeg = (int)((long long)g.nv * blockIdx.y / nsplit), vend = (int)((long long)g.nv * (blockIdx.y + 1) / nsplit);
     const int i = it + tx, r = rt + ty;
-    const bool inside = i < g.nx && r < g.ny;
+    // quad pixels: 0 (i, r), 1 (i + 1, r), 2 (i, r + 1), 3 (i + 1, r + 1)
+    const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
+    const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
     const int ndh = (g.nd + 1) >> 1;
     const float2 *y = y2 + b * (long long)g.nv * ndh;
     const float ctr = 0.5f * (BP_T - 1);
     const float di = (float)tx - ctr, dr = (float)ty - ctr;
-    float2 acc = make_float2(0.f, 0.f);
+    float part[4] = {0.f, 0.f, 0.f, 0.f}, acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int v0 = vbeg; v0 < vend; v0 += BP_CHUNK) {
         const int nvc = min(BP_CHUNK, vend - v0);
         __syncthreads();
-        if (tid < nvc) {
+        for (int k = tid; k < nvc; k += BP_QUAD_THREADS) {
             if (tvtab) {   // precomputed with the geometry
-                const long long t = (long long)tile * g.nv + v0 + tid;
+                const long long t = (long long)tile * g.nv + v0 + k;
                 const float4 u0 = __ldg(tvtab + 2 * t), u1 = __ldg(tvtab + 2 * t + 1);
                 TileViewS<float> T;
                 T.Dt = u0.x; T.yt = u0.y; T.a1 = u0.z; T.b1 = u0.w; T.rho = u1.x; T.phi = u1.y; T.hc = u1.z; T.hs = u1.w;
-                tv[tid] = T;
-                tj[tid] = __ldg(tjtab + t);
+                tv[k] = T;
+                tj[k] = __ldg(tjtab + t);
             } else {
-                tile_view_f32(g, view_cs[2 * (v0 + tid)], view_cs[2 * (v0 + tid) + 1], it + (double)ctr,
-                              rt + (double)ctr, tv[tid], tj[tid]);
+                tile_view_f32(g, view_cs[2 * (v0 + k)], view_cs[2 * (v0 + k) + 1], it + (double)ctr,
+                              rt + (double)ctr, tv[k], tj[k]);
             }
         }
         __syncthreads();
-        if (inside) {
-            float2 part = make_float2(0.f, 0.f);
+        if (in0) {
             for (int vv = 0; vv < nvc; ++vv) {
                 const int v = v0 + vv;
-                part = __fadd2_rn(part, bp_view_f32<ARC>(tv[vv], tj[vv], di, dr, a, g.nd, y + (long long)v * ndh,
-                                                         box2 + 8 * (long long)v * ndh, cell2));
+                const TileViewS<float> T = tv[vv];
+                const int J = tj[vv];
+                const bool col = fabsf(T.b1) <= fabsf(T.a1);   // pairs along a column
+                const float2 *yrow = y + (long long)v * ndh;
+                const float *brow = box2 + 8 * (long long)v * ndh;
+                const float2 s1 = bp_view2_f32<ARC>(T, J, di, dr, in0, col ? di : di + 1.f, col ? dr + 1.f : dr,
+                                                    col ? in2 : in1, a, g.nd, yrow, brow, cell2);
+                const float2 s2 = bp_view2_f32<ARC>(T, J, col ? di + 1.f : di, col ? dr : dr + 1.f, col ? in1 : in2,
+                                                    di + 1.f, dr + 1.f, in3, a, g.nd, yrow, brow, cell2);
+                part[0] += s1.x;
+                part[1] += col ? s2.x : s1.y;
+                part[2] += col ? s1.y : s2.x;
+                part[3] += s2.y;
                 if ((vv & 15) == 15) {   // blocked summation over groups of 16 views
-                    acc = __fadd2_rn(acc, part);
-                    part = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        acc[q] += part[q];
+                        part[q] = 0.f;
+                    }
                 }
             }
-            acc = __fadd2_rn(acc, part);
         }
     }
-    const float accs = acc.x + acc.y;
-    if (inside) {
-        if (nsplit == 1)
-            img[(b * g.ny + r) * g.nx + i] = accs * a.h2q;
-        else
-            partial[((blockIdx.y * (long long)gridDim.z + b) * g.ny + r) * g.nx + i] = accs * a.h2q;
+    if (in0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int iq = i + (q & 1), rq = r + (q >> 1);
+            if (iq >= g.nx || rq >= g.ny) continue;
+            const float val = (acc[q] + part[q]) * a.h2q;
+            if (nsplit == 1)
+                img[(b * g.ny + rq) * g.nx + iq] = val;
+            else
+                partial[((blockIdx.y * (long long)gridDim.z + b) * g.ny + rq) * g.nx + iq] = val;
+        }
     }
 }
 
@@ -326,14 +386,15 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         const double dg = g.arc ? g.ds / g.dps : 0.0;
         BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(0.25 * g.h * g.h),
                  (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0)};
-        // Enough blocks for several waves: split each tile's views when the tiles alone give
-        // fewer than ~32 blocks per SM (partial images, then a fixed-order sum).
+        // Enough blocks for several waves: split each tile's views (up to 32 parts of at least
+        // 16 views) when the tiles alone give fewer than ~32 blocks per SM (partial images,
+        // then a fixed-order sum).
         int sms = 0, dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const long long blocks = (long long)grd.x * grd.y * batch;
         int nsplit = 1;
-        while (nsplit < 8 && blocks * nsplit < 32LL * std::max(sms, 1) && g.nv / (2 * nsplit) >= 32) nsplit *= 2;
+        while (nsplit < 32 && blocks * nsplit < 32LL * std::max(sms, 1) && g.nv / (2 * nsplit) >= 16) nsplit *= 2;
         float *partial = nullptr;
         const long long nimg = (long long)batch * g.nx * g.ny;
         if (nsplit > 1) {
@@ -357,7 +418,7 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
             y2 = copy;
         }
         auto kern = g.arc ? bp_f32_kernel<true> : bp_f32_kernel<false>;
-        kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_T * BP_T), 0, st>>>(
+        kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_QUAD_THREADS), 0, st>>>(
             g, geo->d_view_cs, geo->d_box2, geo->d_cell2, y2, (float *)img, a, geo->d_bp_order,
             (int)grd.x, nsplit, partial, geo->d_tv, geo->d_tj);
         if (copy) cudaFreeAsync(copy, st);

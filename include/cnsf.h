@@ -268,6 +268,14 @@ typedef enum { CNSF_OP_FORWARD = 0, CNSF_OP_BACK = 1, CNSF_OP_FORWARD_REF = 2, C
 CNSF_API int cnsf_plan_create(const cnsf_geometry *geom, int32_t op, const void *in, void *out, int32_t batch,
                               int32_t dtype, cnsf_plan **plan);
 CNSF_API int cnsf_plan_launch(const cnsf_plan *plan, void *stream);
+
+/* Device bytes that one projection call (op as for cnsf_plan_create) with this batch
+ * and dtype allocates stream-ordered, all held at once -- an upper bound that callers
+ * budgeting device memory add to their buffers.  Launches nothing, needs no current
+ * device.  *bytes is a host pointer.  CNSF_ERR_INVALID for a NULL argument, a negative
+ * batch, an unknown op or dtype. */
+CNSF_API int cnsf_projection_scratch_bytes(const cnsf_geometry *geom, int32_t op, int32_t batch, int32_t dtype,
+                                           size_t *bytes);
 CNSF_API void cnsf_plan_destroy(cnsf_plan *plan);   /* NULL is allowed; no replay may be pending */
 
 /* Status code to a static English string. */

@@ -106,6 +106,16 @@ class Geometry:
     def sino_shape(self):
         return (self.n_views, self.n_det)
 
+    def scratch_bytes(self, op: str, batch: int = 1, dtype: torch.dtype = torch.float32) -> int:
+        """Device bytes one projection call ("forward", "back", "forward_ref", "back_ref")
+        of this batch and dtype allocates stream-ordered (all held at once)."""
+        if op not in Plan._OPS:
+            raise ValueError(f"scratch_bytes: op is one of {sorted(Plan._OPS)}")
+        n = ctypes.c_size_t()
+        check(lib.cnsf_projection_scratch_bytes(self.handle, Plan._OPS[op], int(batch), _dtype_code(dtype),
+                                                ctypes.byref(n)), "cnsf_projection_scratch_bytes")
+        return int(n.value)
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib.cnsf_geometry_destroy(self._h)

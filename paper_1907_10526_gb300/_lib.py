@@ -63,6 +63,8 @@ _SIGNATURES = {
     "cnsf_plan_create": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(_P)]),
     "cnsf_plan_launch": (ctypes.c_int, [_P, _P]),
+    "cnsf_projection_scratch_bytes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                     ctypes.POINTER(ctypes.c_size_t)]),
     "cnsf_plan_destroy": (None, [_P]),
     "cnsf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cnsf_last_cuda_error": (ctypes.c_char_p, []),

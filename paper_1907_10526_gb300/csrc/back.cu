@@ -152,7 +152,7 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
     const float2 p = make_float2(A[0], A[1]), nhC = make_float2(A[6], A[7]);
     const float2 w = window_diff2p(x, e, ne1, p, make_float2(A[2], A[3]), make_float2(A[4], A[5]), nhC);
     const float2 den = __fmul2_rn(__ffma2_rn(nhC, ne1, p), e);                              // (p + C/2) e
-    return make_float2(w.x * rcp_approx(den.x), w.y * rcp_approx(den.y));
+    return __fmul2_rn(w, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
 }
 
 // One view of the gather for two pixels a and b of a thread, over the union of their cell
@@ -376,6 +376,31 @@ __global__ void sino_pairs_kernel(const float *__restrict__ y, float2 *__restric
     }
 }
 
+// View parts per tile of the FP32 single-image gather: enough blocks for several waves, so
+// each tile's views are split (up to 32 parts of at least 16 views) when the tiles alone
+// give fewer than ~32 blocks per SM (partial images, then a fixed-order sum).
+static int bp_view_parts(const cnsf_geometry *geo, int batch)
+{
+    const GeomConsts &g = geo->gc;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geo->device);
+    const long long blocks = (long long)((g.nx + BP_T - 1) / BP_T) * ((g.ny + BP_T - 1) / BP_T) * batch;
+    int nsplit = 1;
+    while (nsplit < 32 && blocks * nsplit < 32LL * std::max(sms, 1) && g.nv / (2 * nsplit) >= 16) nsplit *= 2;
+    return nsplit;
+}
+
+size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
+{
+    if (batch <= 0 || dtype != CNSF_F32) return 0;
+    if (batch >= 2) return back_batch_alloc_bytes(geo);
+    const GeomConsts &g = geo->gc;
+    const int nsplit = bp_view_parts(geo, batch);
+    const size_t npair = (size_t)batch * g.nv * ((g.nd + 1) / 2);
+    // the padded sinogram copy is counted whether or not the call's pointer needs it
+    return (nsplit > 1 ? (size_t)nsplit * batch * g.nx * g.ny * sizeof(float) : 0) + npair * sizeof(float2);
+}
+
 int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch, int dtype, cudaStream_t st)
 {
     if (batch == 0) return CNSF_OK;
@@ -386,15 +411,7 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         const double dg = g.arc ? g.ds / g.dps : 0.0;
         BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(0.25 * g.h * g.h),
                  (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0)};
-        // Enough blocks for several waves: split each tile's views (up to 32 parts of at least
-        // 16 views) when the tiles alone give fewer than ~32 blocks per SM (partial images,
-        // then a fixed-order sum).
-        int sms = 0, dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const long long blocks = (long long)grd.x * grd.y * batch;
-        int nsplit = 1;
-        while (nsplit < 32 && blocks * nsplit < 32LL * std::max(sms, 1) && g.nv / (2 * nsplit) >= 16) nsplit *= 2;
+        const int nsplit = bp_view_parts(geo, batch);
         float *partial = nullptr;
         const long long nimg = (long long)batch * g.nx * g.ny;
         if (nsplit > 1) {

@@ -251,14 +251,27 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
 // ------------------------------------------------------------------ launchers
 static int chunk_nb4(int left) { return left > 8 ? 4 : (left > 4 ? 2 : 1); }
 
+// Interleaved copies of a chunk of up to 16 images (both padded layouts).
+size_t forward_batch_alloc_bytes(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    const size_t per = (size_t)g.ny * (g.nx + 2 * geo->pad) + (size_t)g.nx * (g.ny + 2 * geo->pad);
+    return per * 16 * sizeof(float);
+}
+
+// Interleaved copy of a chunk of up to 16 sinograms.
+size_t back_batch_alloc_bytes(const cnsf_geometry *geo)
+{
+    return (size_t)geo->gc.nv * geo->gc.nd * 16 * sizeof(float);
+}
+
 int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t st)
 {
     const GeomConsts &g = geo->gc;
     const int nr = g.nv * g.nd, pad = geo->pad;
     const int pitchP = g.nx + 2 * pad, pitchT = g.ny + 2 * pad;
-    const size_t per = (size_t)g.ny * pitchP + (size_t)g.nx * pitchT;   // pixels of both copies
     float *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, per * 16 * sizeof(float), st);
+    cudaError_t e = cudaMallocAsync((void **)&buf, forward_batch_alloc_bytes(geo), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     for (int b0 = 0; b0 < batch;) {
         const int nb4 = chunk_nb4(batch - b0), NB = 4 * nb4, used = std::min(NB, batch - b0);
@@ -289,7 +302,7 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
     const GeomConsts &g = geo->gc;
     const long long nvd = (long long)g.nv * g.nd;
     float *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)nvd * 16 * sizeof(float), st);
+    cudaError_t e = cudaMallocAsync((void **)&buf, back_batch_alloc_bytes(geo), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     const int ntx = (g.nx + BPB_T - 1) / BPB_T, nty = (g.ny + BPB_T - 1) / BPB_T;
     dim3 blk(BPB_T * BPB_T), grd(ntx * nty);

@@ -270,6 +270,24 @@ int cnsf_plan_create(const cnsf_geometry *geom, int32_t op, const void *in, void
     }
 }
 
+int cnsf_projection_scratch_bytes(const cnsf_geometry *geom, int32_t op, int32_t batch, int32_t dtype,
+                                  size_t *bytes)
+{
+    try {
+        if (!geom || !bytes || batch < 0) return CNSF_ERR_INVALID;
+        if (dtype != CNSF_F32 && dtype != CNSF_F64) return CNSF_ERR_INVALID;
+        switch (op) {
+        case CNSF_OP_FORWARD: *bytes = forward_alloc_bytes(geom, batch, dtype); return CNSF_OK;
+        case CNSF_OP_BACK: *bytes = back_alloc_bytes(geom, batch, dtype); return CNSF_OK;
+        case CNSF_OP_FORWARD_REF:
+        case CNSF_OP_BACK_REF: *bytes = 0; return CNSF_OK;
+        default: return CNSF_ERR_INVALID;
+        }
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
 int cnsf_plan_launch(const cnsf_plan *plan, void *stream)
 {
     try {

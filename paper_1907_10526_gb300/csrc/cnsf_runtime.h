@@ -40,6 +40,13 @@ size_t forward_scratch_bytes(const cnsf_geometry *geo, int batch, int dtype);
 int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype,
                                 void *scratch, size_t scratch_bytes, cudaStream_t stream);
 
+// Device bytes a projection call allocates stream-ordered, all held at once (forward.cu,
+// back.cu, batch.cu).
+size_t forward_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype);
+size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype);
+size_t forward_batch_alloc_bytes(const cnsf_geometry *geo);
+size_t back_batch_alloc_bytes(const cnsf_geometry *geo);
+
 // Batches of FP32 images (batch.cu): each entry evaluated once per chunk of <= 16 images.
 int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t stream);
 int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t stream);

@@ -340,6 +340,30 @@ static int make_padded(const cnsf_geometry *geo, const T *img, int batch, int on
     return CNSF_OK;
 }
 
+// Line parts per ray of the FP32 single-image walk: several when the rays alone give fewer
+// than 128 blocks (of 128 rays) per SM.
+static int fp_line_parts(const cnsf_geometry *geo)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geo->device);
+    const long long blocks = ((long long)geo->gc.nv * geo->gc.nd + 127) / 128;
+    int nsplit = 1;
+    while (nsplit < 4 && blocks * nsplit < 128LL * std::max(sms, 1)) nsplit *= 2;
+    return nsplit;
+}
+
+size_t forward_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
+{
+    if (batch <= 0) return 0;
+    if (dtype == CNSF_F32 && batch >= 2) return forward_batch_alloc_bytes(geo);
+    size_t bytes = forward_scratch_bytes(geo, batch, dtype);   // padded copies
+    if (dtype == CNSF_F32) {
+        const int nsplit = fp_line_parts(geo);
+        if (nsplit > 1) bytes += (size_t)nsplit * batch * geo->gc.nv * geo->gc.nd * sizeof(float);
+    }
+    return bytes;
+}
+
 int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype, cudaStream_t st)
 {
     if (batch == 0) return CNSF_OK;
@@ -353,12 +377,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
         float *buf = nullptr;
         int s = make_padded<float>(geo, (const float *)img, batch, 0, st, &buf, &pitchP, &pitchT, &strideP, &strideT);
         if (s != CNSF_OK) return s;
-        // several line parts per ray when the rays alone give fewer than ~64 blocks per SM
-        int sms = 0, dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int nsplit = 1;
-        while (nsplit < 4 && (long long)grd.x * nsplit < 128LL * std::max(sms, 1)) nsplit *= 2;
+        const int nsplit = fp_line_parts(geo);
         float *partial = nullptr;
         const long long nout = (long long)nr * batch;
         if (nsplit > 1) {

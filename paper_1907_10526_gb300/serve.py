@@ -88,11 +88,11 @@ class ReconServer:
 
     def footprint(self, n: int, n_views: int) -> int:
         """Device bytes a request holds while active: sinogram, image, solver workspace
-        and the forward projector's padded image copies."""
+        and the larger of the two projections' stream-ordered scratch (they run one after
+        the other on the job's stream)."""
         g = self.geometry(n, n_views)
         ws = int(_lib.lib.cnsf_solver_workspace_bytes(g.handle, CNSF_F32))
-        pad = 16
-        scratch = 2 * n * (n + 2 * pad) * 4
+        scratch = max(g.scratch_bytes("forward"), g.scratch_bytes("back"))
         return g.n_views * g.n_det * 4 + n * n * 4 + ws + 256 + scratch
 
     def batch_footprint(self, n: int, n_views: int, batch: int) -> int:
@@ -100,8 +100,8 @@ class ReconServer:
         batched projectors' interleaved copies (chunks of up to 16 images)."""
         g = self.geometry(n, n_views)
         ws = int(_lib.lib.cnsf_cgls_batched_workspace_bytes(g.handle, batch, CNSF_F32))
-        pad = 16
-        chunk = 16 * 4 * max(2 * n * (n + 2 * pad), g.n_views * g.n_det)
+        # batched CGLS projects through the batched kernels whatever the batch
+        chunk = max(g.scratch_bytes("forward", 2), g.scratch_bytes("back", 2))
         return batch * (g.n_views * g.n_det * 4 + n * n * 4) + ws + 512 + chunk
 
     # ------------------------------------------------------------------ serving

@@ -37,19 +37,6 @@ struct BpArgs {
     float nk6;          // arc detector: -dg^2 / 6 (sine series)
 };
 
-// Cell coordinate (minus J) of the pixel's projection.  Flat or parallel detector: the ratio
-// of two affine functions of the pixel offset (perspective division, Eq. 4).  Arc detector:
-// the angle from the tile centre's ray, atan of (y' Dt - yt D_n)/(D_n Dt + y' yt), in cells.
-template <bool ARC, typename TV>
-__device__ __forceinline__ float bp_sigma(const TV &T, float di, float dr, float Dn, float yp, float rD, float kscale)
-{
-    if (ARC) {
-        const float den = fmaf(Dn, T.Dt, yp * T.yt);
-        return fmaf(atanf(fmaf(T.a1, di, T.b1 * dr) * rcp_approx(den)), kscale, T.phi);
-    }
-    return fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);
-}
-
 // The FP32 per-(tile, view) coefficients from the FP64 projection of the tile centre.
 __device__ __forceinline__ void tile_view_f32(const GeomConsts &g, double c, double s, double it, double rt,
                                               TileViewS<float> &T, int &J)
@@ -98,34 +85,31 @@ int build_tile_view_table(cnsf_geometry *geo)
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
-// Per-(pixel, view) set-up of the gather: depth, detector coordinate, cell coordinate and
-// the pixel's cell window [g0, g1] (empty, as [BIG, -BIG], for a pixel outside the image or
-// whose window misses the detector).
+// Per-(pixel, view) set-up of the gather from the pixel's depth D_n, detector coordinate y'
+// and the numerator of its cell coordinate (affine in the pixel offset, so a neighbour's
+// values are one addition away): the cell coordinate sigma (minus J), the half-width hwc of
+// the cell window around it (footprint widths of the ray through the pixel centre), and
+// for the arc detector the sine-series factor G.  Flat or parallel detector: sigma is the
+// ratio of two affine functions of the pixel offset (perspective division, Eq. 4).  Arc
+// detector: the angle from the tile centre's ray, atan of (y' Dt - yt D_n)/(D_n Dt + y' yt)
+// (a numerator without constant term), in cells.
 struct BpPixel {
-    float Dn, yp, sig, G;
-    int g0, g1;
+    float Dn, yp, sig, hwc, G;
 };
 
-constexpr int BP_EMPTY = 1 << 29;
-
 template <bool ARC>
-__device__ __forceinline__ BpPixel bp_pixel_f32(const TileViewS<float> &T, int J, float di, float dr, bool in,
-                                                const BpArgs &a, int nd)
+__device__ __forceinline__ BpPixel bp_pixel_f32(const TileViewS<float> &T, float Dn, float yp, float num,
+                                                const BpArgs &a)
 {
     BpPixel P;
-    P.Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
-    P.yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
-    const float rD = rcp_approx(P.Dn);
-    P.sig = bp_sigma<ARC>(T, di, dr, P.Dn, P.yp, rD, a.kscale);
-    const float za = fmaf(P.yp, T.hc, -P.Dn * T.hs), zb = fmaf(P.yp, T.hs, P.Dn * T.hc);
+    P.Dn = Dn;
+    P.yp = yp;
+    const float rD = rcp_approx(Dn);
+    P.sig = ARC ? fmaf(atanf(num * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))), a.kscale, T.phi) : fmaf(num, rD, T.phi);
+    const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
     const float zs = fabsf(za) + fabsf(zb);
-    const float hwc = fmaf(a.kz * zs * rD * rD, fmaf(a.h2, rD, 1.02f), a.ke);
-    const int g0 = J + max((int)ceilf(P.sig - hwc), -J);
-    const int g1 = J + min((int)floorf(P.sig + hwc), nd - 1 - J);
-    const bool live = in && g0 <= g1;
-    P.g0 = live ? g0 : BP_EMPTY;
-    P.g1 = live ? g1 : -BP_EMPTY;
-    P.G = ARC ? sqrtf(fmaf(P.Dn, P.Dn, P.yp * P.yp)) * a.dg : 0.f;
+    P.hwc = fmaf(a.kz * zs * rD * rD, fmaf(a.h2, rD, 1.02f), a.ke);
+    P.G = ARC ? sqrtf(fmaf(Dn, Dn, yp * yp)) * a.dg : 0.f;
     return P;
 }
 
@@ -156,22 +140,21 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
 }
 
 // One view of the gather for two pixels a and b of a thread, over the union of their cell
-// windows, two cells (2m, 2m + 1) per step on the even-aligned pair tables.  Each cell pair's
-// constants and sinogram values are loaded once and serve both pixels (the L1 path carries
-// every loaded byte to each lane, so sharing the loads halves that traffic).  A cell of the
-// union outside one pixel's own window, or added by aligning the window to even cells, lies
-// outside that pixel's support (the window bounds the support with margin), so its entry
-// for that pixel is exactly 0; a padding cell past n_det has sinogram value 0.  Returns the
-// two pixels' sums.
+// windows [ceil(min sigma - hwc), floor(max sigma + hwc)] clipped to the detector, two cells
+// (2m, 2m + 1) per step on the even-aligned pair tables.  Each cell pair's constants and
+// sinogram values are loaded once and serve both pixels (the L1 path carries every loaded
+// byte to each lane, so sharing the loads halves that traffic).  A cell of the union outside
+// one pixel's own window, or added by aligning the window to even cells, lies outside that
+// pixel's support (the window bounds the support with margin), so its entry for that pixel
+// is exactly 0; a padding cell past n_det has sinogram value 0.  Returns the two pixels' sums.
 template <bool ARC>
-__device__ __forceinline__ float2 bp_view2_f32(const TileViewS<float> &T, int J, float dia, float dra, bool ina,
-                                               float dib, float drb, bool inb, const BpArgs &a, int nd,
+__device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel &Pb, int J, const BpArgs &a, int nd,
                                                const float2 *__restrict__ y2row, const float *__restrict__ boxrow,
                                                const float *__restrict__ cell2)
 {
-    const BpPixel Pa = bp_pixel_f32<ARC>(T, J, dia, dra, ina, a, nd);
-    const BpPixel Pb = bp_pixel_f32<ARC>(T, J, dib, drb, inb, a, nd);
-    const int m0 = min(Pa.g0, Pb.g0) >> 1, m1 = max(Pa.g1, Pb.g1) >> 1;
+    const float lo = fminf(Pa.sig - Pa.hwc, Pb.sig - Pb.hwc), hi = fmaxf(Pa.sig + Pa.hwc, Pb.sig + Pb.hwc);
+    const int g0 = J + max((int)ceilf(lo), -J), g1 = J + min((int)floorf(hi), nd - 1 - J);
+    const int m0 = g0 >> 1, m1 = g1 >> 1;   // m0 > m1 when the window misses the detector
     const float off = (float)(2 * m0 - J);
     float2 da = make_float2(Pa.sig - off, Pa.sig - off - 1.f), db = make_float2(Pb.sig - off, Pb.sig - off - 1.f);
     const float2 m2 = make_float2(-2.f, -2.f);
@@ -248,10 +231,24 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
                 const bool col = fabsf(T.b1) <= fabsf(T.a1);   // pairs along a column
                 const float2 *yrow = y + (long long)v * ndh;
                 const float *brow = box2 + 8 * (long long)v * ndh;
-                const float2 s1 = bp_view2_f32<ARC>(T, J, di, dr, in0, col ? di : di + 1.f, col ? dr + 1.f : dr,
-                                                    col ? in2 : in1, a, g.nd, yrow, brow, cell2);
-                const float2 s2 = bp_view2_f32<ARC>(T, J, col ? di + 1.f : di, col ? dr : dr + 1.f, col ? in1 : in2,
-                                                    di + 1.f, dr + 1.f, in3, a, g.nd, yrow, brow, cell2);
+                // pixel 0, then its neighbours by the per-pixel steps of D_n, y' and the
+                // numerator: down a column (-hs, hc, b1), along a row (-hc, -hs, a1)
+                const float Dn0 = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
+                const float yp0 = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
+                const float nu0 = ARC ? fmaf(T.a1, di, T.b1 * dr) : fmaf(T.a1, di, fmaf(T.b1, dr, T.rho));
+                const float sDn = col ? -T.hs : -T.hc, syp = col ? T.hc : -T.hs, snu = col ? T.b1 : T.a1;   // pair step
+                const float oDn = col ? -T.hc : -T.hs, oyp = col ? -T.hs : T.hc, onu = col ? T.a1 : T.b1;   // other step
+                const BpPixel P0 = bp_pixel_f32<ARC>(T, Dn0, yp0, nu0, a);
+                BpPixel P1 = bp_pixel_f32<ARC>(T, Dn0 + sDn, yp0 + syp, nu0 + snu, a);
+                BpPixel P2 = bp_pixel_f32<ARC>(T, Dn0 + oDn, yp0 + oyp, nu0 + onu, a);
+                BpPixel P3 = bp_pixel_f32<ARC>(T, Dn0 + oDn + sDn, yp0 + oyp + syp, nu0 + onu + snu, a);
+                // a pixel outside the image takes pixel 0's window (its sums are not stored)
+                const bool inP1 = col ? in2 : in1, inP2 = col ? in1 : in2;
+                if (!inP1) { P1.sig = P0.sig; P1.hwc = P0.hwc; }
+                if (!inP2) { P2.sig = P0.sig; P2.hwc = P0.hwc; }
+                if (!in3) { P3.sig = P0.sig; P3.hwc = P0.hwc; }
+                const float2 s1 = bp_view2_f32<ARC>(P0, P1, J, a, g.nd, yrow, brow, cell2);
+                const float2 s2 = bp_view2_f32<ARC>(P2, P3, J, a, g.nd, yrow, brow, cell2);
                 part[0] += s1.x;
                 part[1] += col ? s2.x : s1.y;
                 part[2] += col ? s1.y : s2.x;

@@ -31,6 +31,7 @@ struct alignas(16) TileViewS {
 
 struct BpArgs {
     float kz, ke, h2;   // window constants; h2 = 2h
+    float h2sq;         // 2 h^2
     float h2q;          // h^2 / 4
     float kscale;       // arc detector: cells per radian, D_ps / ds
     float dg;           // arc detector: radians per cell, ds / D_ps
@@ -87,14 +88,13 @@ int build_tile_view_table(cnsf_geometry *geo)
 
 // Per-(pixel, view) set-up of the gather from the pixel's depth D_n, detector coordinate y'
 // and the numerator of its cell coordinate (affine in the pixel offset, so a neighbour's
-// values are one addition away): the cell coordinate sigma (minus J), the half-width hwc of
-// the cell window around it (footprint widths of the ray through the pixel centre), and
-// for the arc detector the sine-series factor G.  Flat or parallel detector: sigma is the
-// ratio of two affine functions of the pixel offset (perspective division, Eq. 4).  Arc
-// detector: the angle from the tile centre's ray, atan of (y' Dt - yt D_n)/(D_n Dt + y' yt)
-// (a numerator without constant term), in cells.
+// values are one addition away): the cell coordinate sigma (minus J) and, for the arc
+// detector, the sine-series factor G.  Flat or parallel detector: sigma is the ratio of
+// two affine functions of the pixel offset (perspective division, Eq. 4).  Arc detector:
+// the angle from the tile centre's ray, atan of (y' Dt - yt D_n)/(D_n Dt + y' yt) (a
+// numerator without constant term), in cells.
 struct BpPixel {
-    float Dn, yp, sig, hwc, G;
+    float Dn, yp, sig, G;
 };
 
 template <bool ARC>
@@ -104,13 +104,26 @@ __device__ __forceinline__ BpPixel bp_pixel_f32(const TileViewS<float> &T, float
     BpPixel P;
     P.Dn = Dn;
     P.yp = yp;
-    const float rD = rcp_approx(Dn);
-    P.sig = ARC ? fmaf(atanf(num * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))), a.kscale, T.phi) : fmaf(num, rD, T.phi);
-    const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
-    const float zs = fabsf(za) + fabsf(zb);
-    P.hwc = fmaf(a.kz * zs * rD * rD, fmaf(a.h2, rD, 1.02f), a.ke);
+    P.sig = ARC ? fmaf(atanf(num * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))), a.kscale, T.phi)
+                : fmaf(num, rcp_approx(Dn), T.phi);
     P.G = ARC ? sqrtf(fmaf(Dn, Dn, yp * yp)) * a.dg : 0.f;
     return P;
+}
+
+// Half-width (cells) of a cell window that holds the footprint of every pixel of a 2 x 2
+// quad, from pixel 0's depth D_n and detector coordinate y'.  For one pixel the window is
+// kz zs / D_n^2 (1.02 + 2h / D_n) + ke with zs = |y' hc - D_n hs| + |y' hs + D_n hc| (the
+// footprint widths of the ray through its centre, with margin for the perspective across
+// the pixel); it grows with zs and 1/D_n.  A step along a row changes the second term of zs
+// by -h^2 and leaves the first; a step down a column changes the first by h^2 and leaves the
+// second: over the quad zs is at most zs_0 + 2h^2, and D_n at least D_n,0 - max(hc, 0) -
+// max(hs, 0).
+__device__ __forceinline__ float bp_quad_hwc(const TileViewS<float> &T, float Dn0, float yp0, const BpArgs &a)
+{
+    const float za = fmaf(yp0, T.hc, -Dn0 * T.hs), zb = fmaf(yp0, T.hs, Dn0 * T.hc);
+    const float zs = fabsf(za) + fabsf(zb) + a.h2sq;
+    const float rD = rcp_approx(Dn0 - fmaxf(T.hc, 0.f) - fmaxf(T.hs, 0.f));
+    return fmaf(a.kz * zs * rD * rD, fmaf(a.h2, rD, 1.02f), a.ke);
 }
 
 // The two entries of cell pair (2m, 2m + 1) for one pixel in packed FP32x2 arithmetic,
@@ -140,7 +153,8 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
 }
 
 // One view of the gather for two pixels a and b of a thread, over the union of their cell
-// windows [ceil(min sigma - hwc), floor(max sigma + hwc)] clipped to the detector, two cells
+// windows [ceil(min sigma - hwc), floor(max sigma + hwc)] (hwc bounding both pixels'
+// half-widths) clipped to the detector, two cells
 // (2m, 2m + 1) per step on the even-aligned pair tables.  Each cell pair's constants and
 // sinogram values are loaded once and serve both pixels (the L1 path carries every loaded
 // byte to each lane, so sharing the loads halves that traffic).  A cell of the union outside
@@ -148,11 +162,11 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
 // pixel's support (the window bounds the support with margin), so its entry for that pixel
 // is exactly 0; a padding cell past n_det has sinogram value 0.  Returns the two pixels' sums.
 template <bool ARC>
-__device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel &Pb, int J, const BpArgs &a, int nd,
-                                               const float2 *__restrict__ y2row, const float *__restrict__ boxrow,
-                                               const float *__restrict__ cell2)
+__device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel &Pb, float hwc, int J, const BpArgs &a,
+                                               int nd, const float2 *__restrict__ y2row,
+                                               const float *__restrict__ boxrow, const float *__restrict__ cell2)
 {
-    const float lo = fminf(Pa.sig - Pa.hwc, Pb.sig - Pb.hwc), hi = fmaxf(Pa.sig + Pa.hwc, Pb.sig + Pb.hwc);
+    const float lo = fminf(Pa.sig, Pb.sig) - hwc, hi = fmaxf(Pa.sig, Pb.sig) + hwc;
     const int g0 = J + max((int)ceilf(lo), -J), g1 = J + min((int)floorf(hi), nd - 1 - J);
     const int m0 = g0 >> 1, m1 = g1 >> 1;   // m0 > m1 when the window misses the detector
     const float off = (float)(2 * m0 - J);
@@ -244,11 +258,12 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
                 BpPixel P3 = bp_pixel_f32<ARC>(T, Dn0 + oDn + sDn, yp0 + oyp + syp, nu0 + onu + snu, a);
                 // a pixel outside the image takes pixel 0's window (its sums are not stored)
                 const bool inP1 = col ? in2 : in1, inP2 = col ? in1 : in2;
-                if (!inP1) { P1.sig = P0.sig; P1.hwc = P0.hwc; }
-                if (!inP2) { P2.sig = P0.sig; P2.hwc = P0.hwc; }
-                if (!in3) { P3.sig = P0.sig; P3.hwc = P0.hwc; }
-                const float2 s1 = bp_view2_f32<ARC>(P0, P1, J, a, g.nd, yrow, brow, cell2);
-                const float2 s2 = bp_view2_f32<ARC>(P2, P3, J, a, g.nd, yrow, brow, cell2);
+                if (!inP1) P1.sig = P0.sig;
+                if (!inP2) P2.sig = P0.sig;
+                if (!in3) P3.sig = P0.sig;
+                const float hwc = bp_quad_hwc(T, Dn0, yp0, a);
+                const float2 s1 = bp_view2_f32<ARC>(P0, P1, hwc, J, a, g.nd, yrow, brow, cell2);
+                const float2 s2 = bp_view2_f32<ARC>(P2, P3, hwc, J, a, g.nd, yrow, brow, cell2);
                 part[0] += s1.x;
                 part[1] += col ? s2.x : s1.y;
                 part[2] += col ? s1.y : s2.x;
@@ -406,7 +421,8 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
     dim3 blk(BP_T, BP_T), grd((g.nx + BP_T - 1) / BP_T, (g.ny + BP_T - 1) / BP_T, batch);
     if (dtype == CNSF_F32) {
         const double dg = g.arc ? g.ds / g.dps : 0.0;
-        BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(0.25 * g.h * g.h),
+        BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h),
+                 (float)(0.25 * g.h * g.h),
                  (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0)};
         const int nsplit = bp_view_parts(geo, batch);
         float *partial = nullptr;

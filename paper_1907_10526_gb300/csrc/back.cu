@@ -127,14 +127,15 @@ __device__ __forceinline__ float bp_quad_hwc(const TileViewS<float> &T, float Dn
 }
 
 // The two entries of cell pair (2m, 2m + 1) for one pixel in packed FP32x2 arithmetic,
-// divided by the normalising widths (the sinogram weights are applied by the caller): the
-// normalisation h^2/(2B) = h^2/(4(p + C/2)) is folded into the division by tau'.  d holds
-// the two cells' offsets from the pixel's projection, in cells.  Arc detector: |s'| =
-// R sin(dg d), R the pixel's distance from the source; with dg d below ~0.05 rad,
-// R dg d (1 - (dg d)^2/6) is that sine to ~1e-9 relative (the next term of the series).
+// without the factor 2/B of the normalisation h^2/(2B) (the caller folds it into the
+// sinogram weights, once for both pixels of a pair) and without h^2/4 (applied to the sum):
+// the window difference divided by tau'.  d holds the two cells' offsets from the pixel's
+// projection, in cells; qiC = q/C.  Arc detector: |s'| = R sin(dg d), R the pixel's
+// distance from the source; with dg d below ~0.05 rad, R dg d (1 - (dg d)^2/6) is that sine
+// to ~1e-9 relative (the next term of the series).
 template <bool ARC>
 __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const float (&A)[8], const float (&C)[8],
-                                              float nk6)
+                                              float2 qiC, float nk6)
 {
     const float2 ne1 = make_float2(-1.f, -1.f);
     float2 xs;
@@ -146,10 +147,9 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
     const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
     const float2 e = __ffma2_rn(make_float2(P.Dn, P.Dn), make_float2(C[2], C[3]),
                                 __fmul2_rn(make_float2(P.yp, P.yp), make_float2(C[4], C[5])));
-    const float2 p = make_float2(A[0], A[1]), nhC = make_float2(A[6], A[7]);
-    const float2 w = window_diff2p(x, e, ne1, p, make_float2(A[2], A[3]), make_float2(A[4], A[5]), nhC);
-    const float2 den = __fmul2_rn(__ffma2_rn(nhC, ne1, p), e);                              // (p + C/2) e
-    return __fmul2_rn(w, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    const float2 w = window_diff2p(x, e, ne1, make_float2(A[0], A[1]), qiC, make_float2(A[4], A[5]),
+                                   make_float2(A[6], A[7]));
+    return __fmul2_rn(w, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
 }
 
 // One view of the gather for two pixels a and b of a thread, over the union of their cell
@@ -175,11 +175,12 @@ __device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel 
     float2 acca = make_float2(0.f, 0.f), accb = make_float2(0.f, 0.f);
     for (int m = m0; m <= m1; ++m) {
         float A[8], C[8];
-        ldg256(boxrow + 8 * m, A);    // p | q/C | 1/C | -C/2, pairs
+        ldg256(boxrow + 8 * m, A);    // p | 2/B | 1/C | -C/2, pairs
         ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
-        const float2 yv = __ldg(y2row + m);
-        acca = __ffma2_rn(yv, bp_pair_f32<ARC>(Pa, da, A, C, a.nk6), acca);
-        accb = __ffma2_rn(yv, bp_pair_f32<ARC>(Pb, db, A, C, a.nk6), accb);
+        const float2 yb = __fmul2_rn(__ldg(y2row + m), make_float2(A[2], A[3]));         // y 2/B
+        const float2 qiC = __ffma2_rn(make_float2(A[0], A[1]), make_float2(A[4], A[5]), make_float2(1.f, 1.f));
+        acca = __ffma2_rn(yb, bp_pair_f32<ARC>(Pa, da, A, C, qiC, a.nk6), acca);
+        accb = __ffma2_rn(yb, bp_pair_f32<ARC>(Pb, db, A, C, qiC, a.nk6), accb);
         da = __fadd2_rn(da, m2);
         db = __fadd2_rn(db, m2);
     }

@@ -167,8 +167,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     // even-aligned cell pairs for the back projector
     const int ndh = (nd + 1) / 2;
     // 32 bytes per cell pair (read with one 256-bit load): trapezoid constants
-    // (p, p, q/C, q/C, 1/C, 1/C, -C/2, -C/2) per (view, pair); cell slopes
-    // (ds/L, ds/L, c1, c1, c2, c2, 0, 0) per pair
+    // (p, p, 2/B, 2/B, 1/C, 1/C, -C/2, -C/2) per (view, pair) (q/C = p/C + 1 is formed in
+    // the kernel); cell slopes (ds/L, ds/L, c1, c1, c2, c2, 0, 0) per pair
     const size_t npairs = (size_t)nv * ndh;
     std::vector<float> box2(8 * npairs);
     std::vector<float> cell2(8 * (size_t)ndh, 0.0f);
@@ -177,7 +177,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
             float *A = &box2[8 * ((size_t)k * ndh + m)];
             for (int h = 0; h < 2; ++h) {
                 const BoxF &b = box[(size_t)k * nd + std::min(2 * m + h, nd - 1)];
-                A[h] = b.p; A[2 + h] = b.qiC; A[4 + h] = b.iC; A[6 + h] = -b.hC;
+                A[h] = b.p; A[2 + h] = (float)(1.0 / ((double)b.p + (double)b.hC)); A[4 + h] = b.iC; A[6 + h] = -b.hC;
             }
         }
     for (int m = 0; m < ndh; ++m)

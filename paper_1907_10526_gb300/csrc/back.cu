@@ -70,7 +70,7 @@ int build_tile_view_table(cnsf_geometry *geo)
     const GeomConsts &g = geo->gc;
     const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
     const long long n = (long long)ntx * nty * g.nv;
-    if (n * 36 > (256LL << 20)) return CNSF_OK;   // large geometries compute it in the kernel
+    if (n * 36 > (1LL << 30)) return CNSF_OK;   // larger geometries compute it in the kernel
     cudaError_t e = cudaMalloc((void **)&geo->d_tv, (size_t)n * 2 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc((void **)&geo->d_tj, (size_t)n * sizeof(int));
     if (e != cudaSuccess) {

@@ -295,7 +295,7 @@ struct cnsf_geometry {
     // launch orders, heaviest blocks first (so that the tail of the grid is short work)
     int *d_fp_order;          // [ceil(nv*nd/128)] forward blocks of 128 rays
     int *d_bp_order;          // [ceil(nx/16)*ceil(ny/16)] back-projection tiles
-    float4 *d_tv;             // [tiles][nv][2] FP32 back-projection tile coefficients (small geometries), or null
+    float4 *d_tv;             // [tiles][nv][2] FP32 back-projection tile coefficients (when <= 1 GiB), or null
     int *d_tj;                // [tiles][nv] their integer cell offsets
     cnsf::RayF *d_ray;        // [nv][nd]
 };

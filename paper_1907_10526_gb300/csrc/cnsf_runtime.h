@@ -14,7 +14,7 @@ int record_cuda_error(cudaError_t e = cudaGetLastError());
 
 int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out);
 void destroy_geometry(cnsf_geometry *geo);
-// Precompute the back projector's per-(tile, view) coefficients when they fit 256 MB (back.cu).
+// Precompute the back projector's per-(tile, view) coefficients when they fit 1 GiB (back.cu).
 int build_tile_view_table(cnsf_geometry *geo);
 
 // Kernel launchers (arguments already validated by the C ABI layer).

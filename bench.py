@@ -325,7 +325,7 @@ def run_cnsf(args):
         "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "fp_sum_parts_kernel",
                              "bp_f32_kernel", "bp_sum_parts_kernel"],
     }
-    if rank == 0 and not args.no_extras:
+    if world == 1 and not args.no_extras:   # the extra lines are single-GPU measurements
         line["serving"] = bench_serving(args, dev)
         line["reconstruction_2048"] = bench_solvers(dev)
         line["batch16_512x360"] = bench_batch16(dev)
@@ -335,7 +335,7 @@ def run_cnsf(args):
         line["detector_kinds_512x720"] = bench_detector_kinds(dev)
         line["p50_recon_latency_s"] = line["serving"]["batched"].get("p50_s")
         line["p99_recon_latency_s"] = line["serving"]["batched"].get("p99_s")
-    if rank == 0 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         r, dt, thr, desc = oracle_sample_rate(720)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
                                 "seconds": dt}
@@ -391,7 +391,14 @@ def bench_solvers(dev, iters: int = 50):
     noisy, _ = poisson_counts(clean.double().cpu().numpy(), seed=3)
     y = torch.tensor(noisy, dtype=torch.float32, device=dev)
     ws = cnsf.SolverWorkspace(geom, torch.float32)
-    out = {"workload": "2048^2, 1536 cells, 1440 views, 50 iterations, FP32 projections"}
+    # the disk every view covers: radius D_po sin(gamma_max), tan(gamma_max) = half detector / D_ps
+    half = 0.5 * g.n_det * g.det_spacing
+    r_fov = g.d_po * half / np.hypot(g.d_ps, half)
+    cx = (np.arange(g.nx) - 0.5 * (g.nx - 1)) * g.pixel
+    cy = (np.arange(g.ny) - 0.5 * (g.ny - 1)) * g.pixel
+    fov = (cx[None, :] ** 2 + cy[:, None] ** 2) <= r_fov ** 2
+    out = {"workload": "2048^2, 1536 cells, 1440 views, 50 iterations, FP32 projections",
+           "fov_disk_radius_mm": r_fov}
     for name, fn in (("sirt", lambda x: cnsf.sirt(geom, y, iters, x0=x, ws=ws)),
                      ("cgls", lambda x: cnsf.cgls(geom, y, iters, x0=x, ws=ws))):
         x = torch.zeros((g.ny, g.nx), dtype=torch.float32, device=dev)
@@ -404,7 +411,9 @@ def bench_solvers(dev, iters: int = 50):
         torch.cuda.synchronize()
         xe = x.double().cpu().numpy()
         err = float(np.linalg.norm(xe - img) / np.linalg.norm(img))
-        out[name] = {"ms_per_iter": t0.elapsed_time(t1) / iters, "rel_error_to_phantom": err}
+        err_fov = float(np.linalg.norm((xe - img)[fov]) / np.linalg.norm(img[fov]))
+        out[name] = {"ms_per_iter": t0.elapsed_time(t1) / iters, "rel_error_to_phantom": err,
+                     "rel_error_in_fov_disk": err_fov}
     return out
 
 
@@ -577,7 +586,7 @@ def main():
     ap.add_argument("--impl", default="cnsf", choices=["cnsf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip serving / reconstruction / batch lines")
-    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-requests", type=int, default=500)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

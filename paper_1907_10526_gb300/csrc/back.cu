@@ -48,17 +48,22 @@ __device__ __forceinline__ void tile_view_f32(const GeomConsts &g, double c, dou
     T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)hc; T.hs = (float)hs;
 }
 
+// Reference point of a tile's coefficients, as offsets from its first pixel: the centre of
+// the part of the tile that lies in the image.  A tile that overhangs the image edge keeps
+// its reference on image pixels, in front of the source (validated for the image only).
+__host__ __device__ inline double tile_ref(int t0, int n) { return 0.5 * ((n - t0 < BP_T ? n - t0 : BP_T) - 1); }
+
 // Geometry-time table of those coefficients for every (tile, view): two float4 and J.
 __global__ void tile_view_table_kernel(GeomConsts g, const double *__restrict__ view_cs, int ntx, int ntiles,
                                        float4 *__restrict__ tab, int *__restrict__ jtab)
 {
     const long long n = (long long)ntiles * g.nv;
-    const double ctr = 0.5 * (BP_T - 1);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int tile = (int)(t / g.nv), v = (int)(t - (long long)tile * g.nv);
+        const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
         TileViewS<float> T;
         int J;
-        tile_view_f32(g, view_cs[2 * v], view_cs[2 * v + 1], (tile % ntx) * BP_T + ctr, (tile / ntx) * BP_T + ctr, T, J);
+        tile_view_f32(g, view_cs[2 * v], view_cs[2 * v + 1], it + tile_ref(it, g.nx), rt + tile_ref(rt, g.ny), T, J);
         tab[2 * t] = make_float4(T.Dt, T.yt, T.a1, T.b1);
         tab[2 * t + 1] = make_float4(T.rho, T.phi, T.hc, T.hs);
         jtab[t] = J;
@@ -218,8 +223,8 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
     const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
     const int ndh = (g.nd + 1) >> 1;
     const float2 *y = y2 + b * (long long)g.nv * ndh;
-    const float ctr = 0.5f * (BP_T - 1);
-    const float di = (float)tx - ctr, dr = (float)ty - ctr;
+    const double refx = tile_ref(it, g.nx), refy = tile_ref(rt, g.ny);
+    const float di = (float)(tx - refx), dr = (float)(ty - refy);
     float part[4] = {0.f, 0.f, 0.f, 0.f}, acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int v0 = vbeg; v0 < vend; v0 += BP_CHUNK) {
         const int nvc = min(BP_CHUNK, vend - v0);
@@ -233,8 +238,8 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
                 tv[k] = T;
                 tj[k] = __ldg(tjtab + t);
             } else {
-                tile_view_f32(g, view_cs[2 * (v0 + k)], view_cs[2 * (v0 + k) + 1], it + (double)ctr,
-                              rt + (double)ctr, tv[k], tj[k]);
+                tile_view_f32(g, view_cs[2 * (v0 + k)], view_cs[2 * (v0 + k) + 1], it + refx, rt + refy, tv[k],
+                              tj[k]);
             }
         }
         __syncthreads();
@@ -320,8 +325,8 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
     const int i = it + tx, r = rt + ty;
     const bool inside = i < g.nx && r < g.ny;
     const double *y = sino + b * (long long)g.nv * g.nd;
-    const double ctr = 0.5 * (BP_T - 1);
-    const double di = tx - ctr, dr = ty - ctr;
+    const double refx = tile_ref(it, g.nx), refy = tile_ref(rt, g.ny);
+    const double di = tx - refx, dr = ty - refy;
     double acc = 0.0;
     for (int v0 = 0; v0 < g.nv; v0 += chunk) {
         const int nvc = min(chunk, g.nv - v0);
@@ -330,7 +335,7 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
             double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
             TileViewS<double> T;
             int J;
-            tile_view_double(g, c, s, it + ctr, rt + ctr, &T.Dt, &T.yt, &T.a1, &T.b1, &T.rho, &T.phi, &J, &T.hc,
+            tile_view_double(g, c, s, it + refx, rt + refy, &T.Dt, &T.yt, &T.a1, &T.b1, &T.rho, &T.phi, &J, &T.hc,
                              &T.hs);
             tv[tid] = T;
             tj[tid] = J;

@@ -183,8 +183,9 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
     const int it = (tile % ntx) * BPB_T, rt = (tile / ntx) * BPB_T;
     const int i = it + tx, r = rt + ty;
     const bool inside = i < g.nx && r < g.ny;
-    const float ctr = 0.5f * (BPB_T - 1);
-    const float di = (float)tx - ctr, dr = (float)ty - ctr;
+    // reference point: the centre of the tile's part inside the image (in front of the source)
+    const double refx = 0.5 * (min(BPB_T, g.nx - it) - 1), refy = 0.5 * (min(BPB_T, g.ny - rt) - 1);
+    const float di = (float)(tx - refx), dr = (float)(ty - refy);
     Acc<NB4> acc;
     acc.zero();
     for (int v0 = 0; v0 < g.nv; v0 += BPB_CHUNK) {
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const doubl
             double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
             double Dt, yt, a1, b1, rho, phi, hc, hs;
             int J;
-            tile_view_double(g, c, s, it + (double)ctr, rt + (double)ctr, &Dt, &yt, &a1, &b1, &rho, &phi, &J, &hc, &hs);
+            tile_view_double(g, c, s, it + refx, rt + refy, &Dt, &yt, &a1, &b1, &rho, &phi, &J, &hc, &hs);
             TileViewB T;
             T.Dt = (float)Dt; T.yt = (float)yt; T.a1 = (float)a1; T.b1 = (float)b1;
             T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)hc; T.hs = (float)hs;

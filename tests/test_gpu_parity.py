@@ -68,6 +68,33 @@ def test_ragged_multi_tile(cnsf, dt):
     assert rel(_bwd(cnsf, geom, sino, dt), oracle.back(g, sino)) < TOL[dt]
 
 
+# The source just outside the image's bounding circle (the validator's 2h margin plus
+# 0.3 mm), and 33 x 33 pixels: the last tile row and column hold one image row or column,
+# so those tiles reach far past the image, some of their area behind the source.
+NEAR = FanGeometry(nx=33, ny=33, n_views=48, n_det=240, d_po=math.hypot(16.5, 16.5) + 2.3, d_ps=60.0,
+                   det_spacing=1.3, det_width=1.2)
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nb", [None, 3])
+def test_source_near_image_overhanging_tiles(cnsf, dt, nb):
+    g = NEAR
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(23)
+    lead = () if nb is None else (nb,)
+    img = rng.uniform(0, 1, lead + (g.ny, g.nx))
+    sino = rng.uniform(0, 1, lead + (g.n_views, g.n_det))
+    for b in range(1 if nb is None else nb):
+        ib = img if nb is None else img[b]
+        sb = sino if nb is None else sino[b]
+        got_y = _fwd(cnsf, geom, img, dt)
+        got_c = _bwd(cnsf, geom, sino, dt)
+        if nb is not None:
+            got_y, got_c = got_y[b], got_c[b]
+        assert rel(got_y, oracle.forward(g, ib)) < TOL[dt]
+        assert rel(got_c, oracle.back(g, sb)) < TOL[dt]
+
+
 @pytest.mark.parametrize("dt", [torch.float64, torch.float32])
 def test_degenerate_angles(cnsf, dt):
     """Axis-aligned and near-axis views (one footprint width -> 0, M_0 = delta) and 45 deg."""

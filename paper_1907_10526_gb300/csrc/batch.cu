@@ -72,6 +72,17 @@ struct Acc {
             v[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
     }
+    // the same with the chunk's values already in registers
+    __device__ __forceinline__ void fma_with(float w, const float4 (&c)[NB4])
+    {
+        const float2 w2 = make_float2(w, w);
+#pragma unroll
+        for (int k = 0; k < NB4; ++k) {
+            const float2 lo = __ffma2_rn(w2, make_float2(c[k].x, c[k].y), make_float2(v[k].x, v[k].y));
+            const float2 hi = __ffma2_rn(w2, make_float2(c[k].z, c[k].w), make_float2(v[k].z, v[k].w));
+            v[k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+    }
     __device__ __forceinline__ void add(const Acc &o)
     {
 #pragma unroll
@@ -161,91 +172,131 @@ __global__ void __launch_bounds__(128) fp_batch_kernel(const int *__restrict__ o
 // ------------------------------------------------------------------ back
 constexpr int BPB_T = 16;
 constexpr int BPB_CHUNK = 256;
+constexpr int BPB_THREADS = BPB_T * BPB_T / 2;   // one thread per pair of pixels
 
 struct alignas(16) TileViewB {
     float Dt, yt, a1, b1, rho, phi, hc, hs;
 };
 
+// Two pixels per thread, rows r and r + 1 of one column (128 threads per 16 x 16 tile, a
+// warp covering 8 x 8 pixels), gathered per view over the union of their cell windows:
+// each cell's constants and the chunk's sinogram values are loaded once for both pixels (the
+// loads, 16 + 16 + 16 NB4 bytes per lane and cell, are what bounds this kernel).  A cell of
+// the union outside one pixel's own window lies outside its support: its entry is exactly 0.
+// The pixel below takes the per-pixel values by one addition (D_n, y' and the numerator of
+// sigma are affine in the offset).  Per-view sums are added to the accumulators in shared
+// memory every 16 views (blocked summation), in the same order for every chunk size, so an
+// image's result does not depend on the batch it is projected in.
 template <int NB4>
-__global__ void __launch_bounds__(256) bp_batch_kernel(GeomConsts g, const double *__restrict__ view_cs,
-                                                       const float4 *__restrict__ box,
-                                                       const float4 *__restrict__ cell,
-                                                       const float4 *__restrict__ Y, float *__restrict__ img,
-                                                       float kz, float ke, float h2, float h2q, int b0,
-                                                       int nb_used, const int *__restrict__ order, int ntx,
-                                                       float kscale, float dg, float nk6)
+__global__ void __launch_bounds__(BPB_THREADS) bp_batch_kernel(GeomConsts g, const double *__restrict__ view_cs,
+                                                               const float4 *__restrict__ box,
+                                                               const float4 *__restrict__ cell,
+                                                               const float4 *__restrict__ Y, float *__restrict__ img,
+                                                               float kz, float ke, float h2, float h2q, int b0,
+                                                               int nb_used, const int *__restrict__ order, int ntx,
+                                                               float kscale, float dg, float nk6)
 {
     __shared__ TileViewB tv[BPB_CHUNK];
     __shared__ int tj[BPB_CHUNK];
+    __shared__ float4 accs[2 * NB4][BPB_THREADS];   // blocked-summation accumulators
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 4 + (lane >> 3);
+    const int tx = (warp & 1) * 8 + (lane & 7), ty = (warp >> 1) * 8 + 2 * (lane >> 3);
     const int tile = order[blockIdx.x];   // heaviest tiles first
     const int it = (tile % ntx) * BPB_T, rt = (tile / ntx) * BPB_T;
     const int i = it + tx, r = rt + ty;
-    const bool inside = i < g.nx && r < g.ny;
+    const bool in0 = i < g.nx && r < g.ny, in1 = i < g.nx && r + 1 < g.ny;
     // reference point: the centre of the tile's part inside the image (in front of the source)
     const double refx = 0.5 * (min(BPB_T, g.nx - it) - 1), refy = 0.5 * (min(BPB_T, g.ny - rt) - 1);
     const float di = (float)(tx - refx), dr = (float)(ty - refy);
-    Acc<NB4> acc;
-    acc.zero();
+#pragma unroll
+    for (int k = 0; k < 2 * NB4; ++k) accs[k][tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int v0 = 0; v0 < g.nv; v0 += BPB_CHUNK) {
         const int nvc = min(BPB_CHUNK, g.nv - v0);
         __syncthreads();
-        if (tid < nvc) {
-            double c = view_cs[2 * (v0 + tid)], s = view_cs[2 * (v0 + tid) + 1];
+        for (int k = tid; k < nvc; k += BPB_THREADS) {
+            double c = view_cs[2 * (v0 + k)], s = view_cs[2 * (v0 + k) + 1];
             double Dt, yt, a1, b1, rho, phi, hc, hs;
             int J;
             tile_view_double(g, c, s, it + refx, rt + refy, &Dt, &yt, &a1, &b1, &rho, &phi, &J, &hc, &hs);
             TileViewB T;
             T.Dt = (float)Dt; T.yt = (float)yt; T.a1 = (float)a1; T.b1 = (float)b1;
             T.rho = (float)rho; T.phi = (float)phi; T.hc = (float)hc; T.hs = (float)hs;
-            tv[tid] = T;
-            tj[tid] = J;
+            tv[k] = T;
+            tj[k] = J;
         }
         __syncthreads();
-        if (!inside) continue;
-        Acc<NB4> part;
-        part.zero();
+        if (!in0) continue;
+        Acc<NB4> part0, part1;
+        part0.zero();
+        part1.zero();
         for (int vv = 0; vv < nvc; ++vv) {
             const TileViewB T = tv[vv];
             const int J = tj[vv];
             const long long vrow = (long long)(v0 + vv) * g.nd;
-            const float Dn = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
-            const float yp = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
-            const float rD = rcp_approx(Dn);
+            const float Dn0 = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
+            const float yp0 = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
+            const float nu0 = g.arc ? fmaf(T.a1, di, T.b1 * dr) : fmaf(T.a1, di, fmaf(T.b1, dr, T.rho));
+            const float Dn1 = Dn0 - T.hs, yp1 = yp0 + T.hc, nu1 = nu0 + T.b1;   // one row down
+            const float rD0 = rcp_approx(Dn0), rD1 = rcp_approx(Dn1);
             // cell coordinate - J: perspective ratio (flat, parallel) or angle (arc detector)
-            const float sig = g.arc ? fmaf(atanf(fmaf(T.a1, di, T.b1 * dr) * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))),
-                                           kscale, T.phi)
-                                    : fmaf(fmaf(T.a1, di, fmaf(T.b1, dr, T.rho)), rD, T.phi);
+            const float sig0 = g.arc ? fmaf(atanf(nu0 * rcp_approx(fmaf(Dn0, T.Dt, yp0 * T.yt))), kscale, T.phi)
+                                     : fmaf(nu0, rD0, T.phi);
+            float sig1 = g.arc ? fmaf(atanf(nu1 * rcp_approx(fmaf(Dn1, T.Dt, yp1 * T.yt))), kscale, T.phi)
+                               : fmaf(nu1, rD1, T.phi);
             // arc: |s'| = R sin(dg d) ~ R dg d (1 - (dg d)^2/6)
-            const float G = g.arc ? sqrtf(fmaf(Dn, Dn, yp * yp)) * dg : 0.f;
-            const float za = fmaf(yp, T.hc, -Dn * T.hs), zb = fmaf(yp, T.hs, Dn * T.hc);
-            const float hwc = fmaf(kz * (fabsf(za) + fabsf(zb)) * rD * rD, fmaf(h2, rD, 1.02f), ke);
-            const int jlo = max((int)ceilf(sig - hwc), -J);
-            const int jhi = min((int)floorf(sig + hwc), g.nd - 1 - J);
-            float d = sig - (float)jlo;
+            const float G0 = g.arc ? sqrtf(fmaf(Dn0, Dn0, yp0 * yp0)) * dg : 0.f;
+            const float G1 = g.arc ? sqrtf(fmaf(Dn1, Dn1, yp1 * yp1)) * dg : 0.f;
+            const float za0 = fmaf(yp0, T.hc, -Dn0 * T.hs), zb0 = fmaf(yp0, T.hs, Dn0 * T.hc);
+            const float za1 = fmaf(yp1, T.hc, -Dn1 * T.hs), zb1 = fmaf(yp1, T.hs, Dn1 * T.hc);
+            const float hwc0 = fmaf(kz * (fabsf(za0) + fabsf(zb0)) * rD0 * rD0, fmaf(h2, rD0, 1.02f), ke);
+            float hwc1 = fmaf(kz * (fabsf(za1) + fabsf(zb1)) * rD1 * rD1, fmaf(h2, rD1, 1.02f), ke);
+            if (!in1) { sig1 = sig0; hwc1 = hwc0; }   // a pixel below the image takes the window above
+            const int jlo = max((int)ceilf(fminf(sig0 - hwc0, sig1 - hwc1)), -J);
+            const int jhi = min((int)floorf(fmaxf(sig0 + hwc0, sig1 + hwc1)), g.nd - 1 - J);
+            float d0 = sig0 - (float)jlo, d1 = sig1 - (float)jlo;
             for (int jl = jlo; jl <= jhi; ++jl) {
                 const long long q = vrow + J + jl;
                 const float4 A = __ldg(box + q);
                 const float4 C = __ldg(cell + J + jl);
-                const float x = g.arc ? fabsf(G * d * fmaf(d * d, nk6, 1.f)) : fabsf(Dn * C.x * d);
-                const float e = fmaf(Dn, C.y, yp * C.z);
-                const float w = window_diff(x, e, A.x, A.y, A.z, A.w);
-                part.fma_from(w * rcp_approx((A.x + A.w) * e), Y + q * NB4);
-                d -= 1.f;
+                float4 yv[NB4];
+#pragma unroll
+                for (int k = 0; k < NB4; ++k) yv[k] = __ldg(Y + q * NB4 + k);
+                const float x0 = g.arc ? fabsf(G0 * d0 * fmaf(d0 * d0, nk6, 1.f)) : fabsf(Dn0 * C.x * d0);
+                const float x1 = g.arc ? fabsf(G1 * d1 * fmaf(d1 * d1, nk6, 1.f)) : fabsf(Dn1 * C.x * d1);
+                const float e0 = fmaf(Dn0, C.y, yp0 * C.z), e1 = fmaf(Dn1, C.y, yp1 * C.z);
+                const float w0 = window_diff(x0, e0, A.x, A.y, A.z, A.w);
+                const float w1 = window_diff(x1, e1, A.x, A.y, A.z, A.w);
+                part0.fma_with(w0 * rcp_approx((A.x + A.w) * e0), yv);
+                part1.fma_with(w1 * rcp_approx((A.x + A.w) * e1), yv);
+                d0 -= 1.f;
+                d1 -= 1.f;
             }
-            if ((vv & 15) == 15) {
-                acc.add(part);
-                part.zero();
+            if ((vv & 15) == 15 || vv == nvc - 1) {   // blocked summation over groups of 16 views
+#pragma unroll
+                for (int k = 0; k < NB4; ++k) {
+                    float4 u = accs[k][tid], w = accs[NB4 + k][tid];
+                    const float2 u0 = __fadd2_rn(make_float2(u.x, u.y), make_float2(part0.v[k].x, part0.v[k].y));
+                    const float2 u1 = __fadd2_rn(make_float2(u.z, u.w), make_float2(part0.v[k].z, part0.v[k].w));
+                    const float2 w0 = __fadd2_rn(make_float2(w.x, w.y), make_float2(part1.v[k].x, part1.v[k].y));
+                    const float2 w1 = __fadd2_rn(make_float2(w.z, w.w), make_float2(part1.v[k].z, part1.v[k].w));
+                    accs[k][tid] = make_float4(u0.x, u0.y, u1.x, u1.y);
+                    accs[NB4 + k][tid] = make_float4(w0.x, w0.y, w1.x, w1.y);
+                }
+                part0.zero();
+                part1.zero();
             }
         }
-        acc.add(part);
     }
-    if (inside) {
-        const float *a = reinterpret_cast<const float *>(acc.v);
+    if (in0) {
 #pragma unroll
-        for (int k = 0; k < 4 * NB4; ++k)
-            if (k < nb_used) img[((long long)(b0 + k) * g.ny + r) * g.nx + i] = a[k] * h2q;
+        for (int k = 0; k < 4 * NB4; ++k) {
+            if (k >= nb_used) continue;
+            const float4 u = accs[k >> 2][tid], w = accs[NB4 + (k >> 2)][tid];
+            const float a0 = (k & 3) == 0 ? u.x : (k & 3) == 1 ? u.y : (k & 3) == 2 ? u.z : u.w;
+            const float a1 = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
+            img[((long long)(b0 + k) * g.ny + r) * g.nx + i] = a0 * h2q;
+            if (in1) img[((long long)(b0 + k) * g.ny + r + 1) * g.nx + i] = a1 * h2q;
+        }
     }
 }
 
@@ -306,7 +357,7 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
     cudaError_t e = cudaMallocAsync((void **)&buf, back_batch_alloc_bytes(geo), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     const int ntx = (g.nx + BPB_T - 1) / BPB_T, nty = (g.ny + BPB_T - 1) / BPB_T;
-    dim3 blk(BPB_T * BPB_T), grd(ntx * nty);
+    dim3 blk(BPB_THREADS), grd(ntx * nty);
     const float kz = (float)geo->bw.kz, ke = (float)geo->bw.ke, h2 = (float)(2.0 * g.h), h2q = (float)(0.25 * g.h * g.h);
     const double dgd = g.arc ? g.ds / g.dps : 0.0;
     const float kscale = (float)(g.arc ? g.dps / g.ds : 0.0), dg = (float)dgd, nk6 = (float)(-dgd * dgd / 6.0);

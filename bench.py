@@ -321,9 +321,9 @@ def run_cnsf(args):
                        "image -> pinned host; host clock around each step, synchronised"},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "fp_sum_parts_kernel",
-                             "bp_f32_kernel", "bp_sum_parts_kernel"],
+                             "sino_pairs_kernel", "bp_f32_kernel", "bp_sum_parts_kernel"],
     }
     if world == 1 and not args.no_extras:   # the extra lines are single-GPU measurements
         line["serving"] = bench_serving(args, dev)

@@ -119,11 +119,11 @@ CNSF_API int cnsf_forward_project(const cnsf_geometry *geom, const void *image, 
 
 /* Back projection c = A^T y, the exact adjoint of cnsf_forward_project (same
  * entries), pixel-driven gather without atomics.  sino: device
- * [batch][n_views][n_det]; image: device [batch][n_y][n_x], overwritten.  FP32 may
- * allocate scratch stream-ordered on `stream` (partial images of groups of views,
- * summed in a fixed order; a padded copy of the sinogram when n_det is odd or the
- * pointer is not 8-byte aligned; interleaved copies for batch >= 2) and frees it the
- * same way.  FP64 uses no scratch. */
+ * [batch][n_views][n_det]; image: device [batch][n_y][n_x], overwritten.  FP32
+ * allocates scratch stream-ordered on `stream` (the sinogram as odd-aligned cell pairs,
+ * and as even-aligned pairs too when n_det is odd or the pointer is not 8-byte aligned;
+ * partial images of groups of views, summed in a fixed order; interleaved copies for
+ * batch >= 2) and frees it the same way.  FP64 uses no scratch. */
 CNSF_API int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch,
                       int32_t dtype, void *stream);
 

@@ -36,6 +36,8 @@ struct BpArgs {
     float kscale;       // arc detector: cells per radian, D_ps / ds
     float dg;           // arc detector: radians per cell, ds / D_ps
     float nk6;          // arc detector: -dg^2 / 6 (sine series)
+    long long box_odd;  // offsets (floats) of the odd-aligned pair tables: 8 nv ceil(n_det/2)
+    int cell_odd;       // and 8 ceil(n_det/2)
 };
 
 // The FP32 per-(tile, view) coefficients from the FP64 projection of the tile centre.
@@ -157,24 +159,32 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
     return __fmul2_rn(w, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
 }
 
-// One view of the gather for two pixels a and b of a thread, over the union of their cell
-// windows [ceil(min sigma - hwc), floor(max sigma + hwc)] (hwc bounding both pixels'
-// half-widths) clipped to the detector, two cells
-// (2m, 2m + 1) per step on the even-aligned pair tables.  Each cell pair's constants and
-// sinogram values are loaded once and serve both pixels (the L1 path carries every loaded
-// byte to each lane, so sharing the loads halves that traffic).  A cell of the union outside
-// one pixel's own window, or added by aligning the window to even cells, lies outside that
-// pixel's support (the window bounds the support with margin), so its entry for that pixel
-// is exactly 0; a padding cell past n_det has sinogram value 0.  Returns the two pixels' sums.
+// One view of the gather for two pixels a and b of a thread, over the union [g0, g1] of
+// their cell windows [sigma - hwc, sigma + hwc] (hwc bounding both pixels' half-widths)
+// clipped to the detector, two cells per step.  The steps start at g0 whatever its parity
+// (pair tables and sinogram pairs exist in both alignments), so a window of L cells takes
+// ceil(L/2) steps.  Each cell pair's constants and sinogram values are loaded once and serve
+// both pixels (the L1 path carries every loaded byte to each lane, so sharing the loads
+// halves that traffic).  A cell of the union outside one pixel's own window, or the cell
+// past g1 of an odd-length window, lies outside that pixel's support (the window bounds the
+// support with margin), so its entry for that pixel is exactly 0; a cell past n_det has
+// sinogram value 0.  Returns the two pixels' sums.
 template <bool ARC>
 __device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel &Pb, float hwc, int J, const BpArgs &a,
                                                int nd, const float2 *__restrict__ y2row,
-                                               const float *__restrict__ boxrow, const float *__restrict__ cell2)
+                                               const float2 *__restrict__ y2orow, const float *__restrict__ boxrow,
+                                               const float *__restrict__ cell2)
 {
     const float lo = fminf(Pa.sig, Pb.sig) - hwc, hi = fmaxf(Pa.sig, Pb.sig) + hwc;
     const int g0 = J + max((int)ceilf(lo), -J), g1 = J + min((int)floorf(hi), nd - 1 - J);
-    const int m0 = g0 >> 1, m1 = g1 >> 1;   // m0 > m1 when the window misses the detector
-    const float off = (float)(2 * m0 - J);
+    const int odd = g0 & 1;
+    const int m0 = g0 >> 1, m1 = (g1 - odd) >> 1;   // m0 > m1 when the window misses the detector
+    if (odd) {   // pairs (2m + 1, 2m + 2)
+        boxrow += a.box_odd;
+        cell2 += a.cell_odd;
+        y2row = y2orow;
+    }
+    const float off = (float)(2 * m0 + odd - J);
     float2 da = make_float2(Pa.sig - off, Pa.sig - off - 1.f), db = make_float2(Pb.sig - off, Pb.sig - off - 1.f);
     const float2 m2 = make_float2(-2.f, -2.f);
     float2 acca = make_float2(0.f, 0.f), accb = make_float2(0.f, 0.f);
@@ -203,6 +213,7 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
                                                                  const float *__restrict__ box2,
                                                                  const float *__restrict__ cell2,
                                                                  const float2 *__restrict__ y2,
+                                                                 const float2 *__restrict__ y2o,
                                                                  float *__restrict__ img, BpArgs a,
                                                                  const int *__restrict__ order, int ntx, int nsplit,
                                                                  float *__restrict__ partial,
@@ -222,7 +233,7 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
     const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
     const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
     const int ndh = (g.nd + 1) >> 1;
-    const float2 *y = y2 + b * (long long)g.nv * ndh;
+    const float2 *y = y2 + b * (long long)g.nv * ndh, *yo = y2o + b * (long long)g.nv * ndh;
     const double refx = tile_ref(it, g.nx), refy = tile_ref(rt, g.ny);
     const float di = (float)(tx - refx), dr = (float)(ty - refy);
     float part[4] = {0.f, 0.f, 0.f, 0.f}, acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -268,8 +279,9 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
                 if (!inP2) P2.sig = P0.sig;
                 if (!in3) P3.sig = P0.sig;
                 const float hwc = bp_quad_hwc(T, Dn0, yp0, a);
-                const float2 s1 = bp_view2_f32<ARC>(P0, P1, hwc, J, a, g.nd, yrow, brow, cell2);
-                const float2 s2 = bp_view2_f32<ARC>(P2, P3, hwc, J, a, g.nd, yrow, brow, cell2);
+                const float2 *yorow = yo + (long long)v * ndh;
+                const float2 s1 = bp_view2_f32<ARC>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2);
+                const float2 s2 = bp_view2_f32<ARC>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2);
                 part[0] += s1.x;
                 part[1] += col ? s2.x : s1.y;
                 part[2] += col ? s1.y : s2.x;
@@ -381,16 +393,17 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
     if (inside) img[(b * g.ny + r) * g.nx + i] = acc;
 }
 
-// y2[b][v][m] = (y[b][v][2m], y[b][v][2m + 1]) with 0 for the padding cell of odd n_det.
-__global__ void sino_pairs_kernel(const float *__restrict__ y, float2 *__restrict__ y2, long long nrows, int nd)
+// The sinogram as cell pairs of parity o: y2[b][v][m] = (y[b][v][2m + o], y[b][v][2m + o + 1]),
+// 0 for cells past n_det.
+__global__ void sino_pairs_kernel(const float *__restrict__ y, float2 *__restrict__ y2, long long nrows, int nd, int o)
 {
     const int ndh = (nd + 1) >> 1;
     const long long n = nrows * ndh;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const long long row = t / ndh;
-        const int j = 2 * (int)(t - row * ndh);
+        const int j = 2 * (int)(t - row * ndh) + o;
         const float *yr = y + row * nd;
-        y2[t] = make_float2(yr[j], j + 1 < nd ? yr[j + 1] : 0.f);
+        y2[t] = make_float2(j < nd ? yr[j] : 0.f, j + 1 < nd ? yr[j + 1] : 0.f);
     }
 }
 
@@ -415,8 +428,8 @@ size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
     const GeomConsts &g = geo->gc;
     const int nsplit = bp_view_parts(geo, batch);
     const size_t npair = (size_t)batch * g.nv * ((g.nd + 1) / 2);
-    // the padded sinogram copy is counted whether or not the call's pointer needs it
-    return (nsplit > 1 ? (size_t)nsplit * batch * g.nx * g.ny * sizeof(float) : 0) + npair * sizeof(float2);
+    // odd-aligned sinogram pairs, and the even-aligned copy whether or not the call's pointer needs it
+    return (nsplit > 1 ? (size_t)nsplit * batch * g.nx * g.ny * sizeof(float) : 0) + 2 * npair * sizeof(float2);
 }
 
 int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch, int dtype, cudaStream_t st)
@@ -429,7 +442,8 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         const double dg = g.arc ? g.ds / g.dps : 0.0;
         BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h),
                  (float)(0.25 * g.h * g.h),
-                 (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0)};
+                 (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0),
+                 8LL * g.nv * ((g.nd + 1) / 2), 8 * ((g.nd + 1) / 2)};
         const int nsplit = bp_view_parts(geo, batch);
         float *partial = nullptr;
         const long long nimg = (long long)batch * g.nx * g.ny;
@@ -437,25 +451,26 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
             cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nimg * sizeof(float), st);
             if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
         }
-        // the sinogram read as cell pairs: directly when n_det is even and the pointer 8-byte
-        // aligned, otherwise through a padded copy
+        // the sinogram as cell pairs: odd-aligned pairs from a copy; even-aligned pairs
+        // directly when n_det is even and the pointer 8-byte aligned, otherwise from a copy
         const bool direct = (g.nd % 2 == 0) && (((uintptr_t)sino & 7u) == 0);
-        const float2 *y2 = reinterpret_cast<const float2 *>(sino);
+        const long long nrows = (long long)batch * g.nv, npair = nrows * ((g.nd + 1) / 2);
         float2 *copy = nullptr;
+        cudaError_t e = cudaMallocAsync((void **)&copy, (size_t)(direct ? 1 : 2) * npair * sizeof(float2), st);
+        if (e != cudaSuccess) {
+            if (partial) cudaFreeAsync(partial, st);
+            return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+        }
+        const unsigned pblocks = (unsigned)std::min<long long>((npair + 255) / 256, 8192);
+        sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, copy, nrows, g.nd, 1);
+        const float2 *y2 = reinterpret_cast<const float2 *>(sino);
         if (!direct) {
-            const long long nrows = (long long)batch * g.nv, n = nrows * ((g.nd + 1) / 2);
-            cudaError_t e = cudaMallocAsync((void **)&copy, (size_t)n * sizeof(float2), st);
-            if (e != cudaSuccess) {
-                if (partial) cudaFreeAsync(partial, st);
-                return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
-            }
-            sino_pairs_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(
-                (const float *)sino, copy, nrows, g.nd);
-            y2 = copy;
+            sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, copy + npair, nrows, g.nd, 0);
+            y2 = copy + npair;
         }
         auto kern = g.arc ? bp_f32_kernel<true> : bp_f32_kernel<false>;
         kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_QUAD_THREADS), 0, st>>>(
-            g, geo->d_view_cs, geo->d_box2, geo->d_cell2, y2, (float *)img, a, geo->d_bp_order,
+            g, geo->d_view_cs, geo->d_box2, geo->d_cell2, y2, copy, (float *)img, a, geo->d_bp_order,
             (int)grd.x, nsplit, partial, geo->d_tv, geo->d_tj);
         if (copy) cudaFreeAsync(copy, st);
         if (nsplit > 1) {

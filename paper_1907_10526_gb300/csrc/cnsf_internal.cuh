@@ -259,12 +259,13 @@ struct alignas(16) CellF {
     float g1, c1, c2, pad;   // ds/L_j, cos(g_j) dtan_j/2, sin(g_j) dtan_j/2 (flat: cos = D_ps/L_j)
 };
 
-// Pair constants of the FP32 back projector: entry m holds cells 2m and 2m + 1 side by
-// side, so the two cells' values come as FP32 pairs for the packed (FFMA2) arithmetic.
-// n_det is padded to even; a padding cell repeats the last cell's constants (its sinogram
-// value is 0).  Each entry is 32 bytes, read with one 256-bit load: per (view, pair) the
+// Pair constants of the FP32 back projector: entry m of parity o holds cells 2m + o and
+// 2m + o + 1 side by side, so the two cells' values come as FP32 pairs for the packed
+// (FFMA2) arithmetic, and a window can start its pairs at any cell.  A cell past n_det
+// repeats the last cell's constants (its sinogram value is 0).  Each entry is 32 bytes,
+// read with one 256-bit load: per (parity, view, pair) the
 // trapezoid constants (p, 2/B, 1/C, -C/2 of both cells; q/C = p/C + 1 is formed in the
-// kernel), per pair the view-independent
+// kernel), per (parity, pair) the view-independent
 // cell slopes (ds/L_j, cos(g_j) dtan_j/2, sin(g_j) dtan_j/2 of both cells), a table of a
 // few KB that stays in L1 across views.
 
@@ -291,8 +292,8 @@ struct cnsf_geometry {
     double *d_cell_d;         // [nd][4] sin(g_j), cos(g_j), dtan_j, s_j (FP64; parallel: 0, 1, 0, s_j)
     cnsf::BoxF *d_box;        // [nv][nd]
     cnsf::CellF *d_cellf;     // [nd]
-    float *d_box2;            // [nv][ceil(n_det/2)][8]: p, 2/B, 1/C, -C/2 of cells 2m, 2m + 1
-    float *d_cell2;           // [ceil(n_det/2)][8]: ds/L, c1, c2 of cells 2m, 2m + 1, 0, 0
+    float *d_box2;            // [2][nv][ceil(n_det/2)][8]: p, 2/B, 1/C, -C/2 of cells 2m + o, 2m + o + 1
+    float *d_cell2;           // [2][ceil(n_det/2)][8]: ds/L, c1, c2 of cells 2m + o, 2m + o + 1, 0, 0
     // launch orders, heaviest blocks first (so that the tail of the grid is short work)
     int *d_fp_order;          // [ceil(nv*nd/128)] forward blocks of 128 rays
     int *d_bp_order;          // [ceil(nx/16)*ceil(ny/16)] back-projection tiles

@@ -164,29 +164,34 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
             F.e0 = (float)(R.e0 + F.r0 * R.de);
         }
     }
-    // even-aligned cell pairs for the back projector
+    // cell pairs for the back projector, in both alignments: pair m of parity o holds cells
+    // 2m + o and 2m + o + 1 (a cell past n_det repeats the last cell's constants; its
+    // sinogram value is 0)
     const int ndh = (nd + 1) / 2;
     // 32 bytes per cell pair (read with one 256-bit load): trapezoid constants
-    // (p, p, 2/B, 2/B, 1/C, 1/C, -C/2, -C/2) per (view, pair) (q/C = p/C + 1 is formed in
-    // the kernel); cell slopes (ds/L, ds/L, c1, c1, c2, c2, 0, 0) per pair
+    // (p, p, 2/B, 2/B, 1/C, 1/C, -C/2, -C/2) per (parity, view, pair) (q/C = p/C + 1 is
+    // formed in the kernel); cell slopes (ds/L, ds/L, c1, c1, c2, c2, 0, 0) per (parity, pair)
     const size_t npairs = (size_t)nv * ndh;
-    std::vector<float> box2(8 * npairs);
-    std::vector<float> cell2(8 * (size_t)ndh, 0.0f);
-    for (int k = 0; k < nv; ++k)
-        for (int m = 0; m < ndh; ++m) {
-            float *A = &box2[8 * ((size_t)k * ndh + m)];
-            for (int h = 0; h < 2; ++h) {
-                const BoxF &b = box[(size_t)k * nd + std::min(2 * m + h, nd - 1)];
-                A[h] = b.p; A[2 + h] = (float)(1.0 / ((double)b.p + (double)b.hC)); A[4 + h] = b.iC; A[6 + h] = -b.hC;
+    std::vector<float> box2(2 * 8 * npairs);
+    std::vector<float> cell2(2 * 8 * (size_t)ndh, 0.0f);
+    for (int o = 0; o < 2; ++o)
+        for (int k = 0; k < nv; ++k)
+            for (int m = 0; m < ndh; ++m) {
+                float *A = &box2[8 * (o * npairs + (size_t)k * ndh + m)];
+                for (int h = 0; h < 2; ++h) {
+                    const BoxF &b = box[(size_t)k * nd + std::min(2 * m + o + h, nd - 1)];
+                    A[h] = b.p; A[2 + h] = (float)(1.0 / ((double)b.p + (double)b.hC)); A[4 + h] = b.iC; A[6 + h] = -b.hC;
+                }
             }
-        }
-    for (int m = 0; m < ndh; ++m)
-        for (int h = 0; h < 2; ++h) {
-            const CellF &c = cellf[std::min(2 * m + h, nd - 1)];
-            cell2[8 * m + h] = c.g1;
-            cell2[8 * m + 2 + h] = c.c1;
-            cell2[8 * m + 4 + h] = c.c2;
-        }
+    for (int o = 0; o < 2; ++o)
+        for (int m = 0; m < ndh; ++m)
+            for (int h = 0; h < 2; ++h) {
+                const CellF &c = cellf[std::min(2 * m + o + h, nd - 1)];
+                float *S = &cell2[8 * ((size_t)o * ndh + m)];
+                S[h] = c.g1;
+                S[2 + h] = c.c1;
+                S[4 + h] = c.c2;
+            }
     int pad = ((kc_max + 1 + 3) / 4) * 4;
     // The walk never leaves [-pad, na-1+pad]: windows that meet [0, na-1] are at most kc wide.
     for (size_t q = 0; q < nr; ++q) {

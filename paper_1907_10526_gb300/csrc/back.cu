@@ -111,7 +111,7 @@ __device__ __forceinline__ BpPixel bp_pixel_f32(const TileViewS<float> &T, float
     BpPixel P;
     P.Dn = Dn;
     P.yp = yp;
-    P.sig = ARC ? fmaf(atanf(num * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))), a.kscale, T.phi)
+    P.sig = ARC ? fmaf(atan_small(num * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))), a.kscale, T.phi)
                 : fmaf(num, rcp_approx(Dn), T.phi);
     P.G = ARC ? sqrtf(fmaf(Dn, Dn, yp * yp)) * a.dg : 0.f;
     return P;

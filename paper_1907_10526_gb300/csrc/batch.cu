@@ -239,9 +239,9 @@ __global__ void __launch_bounds__(BPB_THREADS) bp_batch_kernel(GeomConsts g, con
             const float Dn1 = Dn0 - T.hs, yp1 = yp0 + T.hc, nu1 = nu0 + T.b1;   // one row down
             const float rD0 = rcp_approx(Dn0), rD1 = rcp_approx(Dn1);
             // cell coordinate - J: perspective ratio (flat, parallel) or angle (arc detector)
-            const float sig0 = g.arc ? fmaf(atanf(nu0 * rcp_approx(fmaf(Dn0, T.Dt, yp0 * T.yt))), kscale, T.phi)
+            const float sig0 = g.arc ? fmaf(atan_small(nu0 * rcp_approx(fmaf(Dn0, T.Dt, yp0 * T.yt))), kscale, T.phi)
                                      : fmaf(nu0, rD0, T.phi);
-            float sig1 = g.arc ? fmaf(atanf(nu1 * rcp_approx(fmaf(Dn1, T.Dt, yp1 * T.yt))), kscale, T.phi)
+            float sig1 = g.arc ? fmaf(atan_small(nu1 * rcp_approx(fmaf(Dn1, T.Dt, yp1 * T.yt))), kscale, T.phi)
                                : fmaf(nu1, rD1, T.phi);
             // arc: |s'| = R sin(dg d) ~ R dg d (1 - (dg d)^2/6)
             const float G0 = g.arc ? sqrtf(fmaf(Dn0, Dn0, yp0 * yp0)) * dg : 0.f;

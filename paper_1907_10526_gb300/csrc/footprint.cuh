@@ -47,6 +47,16 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// arctan of a small ratio (the angle between a pixel's ray and its tile's reference ray):
+// the Taylor (Gregory) series x - x^3/3 + x^5/5 - x^7/7 + x^9/9 for |x| < 1/8, where the
+// first omitted term is below 1e-10 relative; atanf beyond.
+__device__ __forceinline__ float atan_small(float x)
+{
+    const float t = x * x;
+    if (!(t < 0.015625f)) return atanf(x);
+    return x * fmaf(fmaf(fmaf(fmaf(t, 1.f / 9.f, -1.f / 7.f), t, 0.2f), t, -1.f / 3.f), t, 1.f);
+}
+
 // 32 bytes from global memory through the read-only path in one 256-bit load (sm_100+);
 // p must be 32-byte aligned.
 __device__ __forceinline__ void ldg256(const float *p, float (&r)[8])

@@ -88,17 +88,17 @@ __device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, c
                                                 float p, float qiC, float iC, float2 hC2, float2 nhC2)
 {
     float2 s = make_float2(0.f, 0.f);
-    const float2 one = make_float2(1.0f, 1.0f);
+    // B u and tau'/2 grow by B and kap per candidate
+    float2 xs = __fmul2_rn(B2, u), e = __ffma2_rn(kap2, u, er2);
 #pragma unroll
     for (int m = 0; m < KC; ++m) {
-        const float2 xs = __fmul2_rn(B2, u);
         const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));
-        const float2 e = __ffma2_rn(kap2, u, er2);
         const float2 d = window_diff2(x, e, ne1, p, qiC, iC, hC2, nhC2);
-        const float2 w = make_float2(d.x * rcp_approx(e.x), d.y * rcp_approx(e.y));
+        const float2 w = __fmul2_rn(d, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
         const float2 c = make_float2(__ldg(rp0 + m), __ldg(rp1 + m));
         s = __ffma2_rn(c, w, s);
-        u = __fadd2_rn(u, one);
+        xs = __fadd2_rn(xs, B2);
+        e = __fadd2_rn(e, kap2);
     }
     return s;
 }

@@ -95,12 +95,15 @@ struct Acc {
 };
 
 // ------------------------------------------------------------------ forward
+// KC candidates per line; KC = 0: R.kc of them (windows wider than 8 pixels, cells much
+// wider than pixels).
 template <int KC, int NB4>
 __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__restrict__ base, int pitch4, float B,
                                               float p, float qiC, float iC, float hC, Acc<NB4> &acc)
 {
     long long A = R.A0 + 0xFFFFFFFFLL;   // ceil-ready: high word = ceil(f - hw)
     float er = R.e0;
+    const int kc = KC > 0 ? KC : R.kc;
     Acc<NB4> part;
     part.zero();
     for (int rr = 0; rr < R.nrows; ++rr) {
@@ -108,7 +111,7 @@ __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__res
         const float u0 = fmaf(__uint2float_rn((unsigned)A), -1.0f / 4294967296.0f, 1.0f) - R.hw;
         const float4 *rp = base + (long long)ilo * NB4;
 #pragma unroll
-        for (int m = 0; m < KC; ++m) {
+        for (int m = 0; m < kc; ++m) {
             const float um = u0 + (float)m;
             const float e = fmaf(R.kap, um, er);
             const float d = window_diff(fabsf(B * um), e, p, qiC, iC, hC);
@@ -155,7 +158,8 @@ __global__ void __launch_bounds__(128) fp_batch_kernel(const int *__restrict__ o
             case 5: fp_batch_walk<5, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
             case 6: fp_batch_walk<6, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
             case 7: fp_batch_walk<7, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            default: fp_batch_walk<8, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            case 8: fp_batch_walk<8, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+            default: fp_batch_walk<0, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
         }
         const float nrm = h2q / (p + hC);
 #pragma unroll

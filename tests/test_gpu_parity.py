@@ -173,6 +173,24 @@ def test_batch_matches_single_and_oracle(cnsf, nb):
         assert rel(bb[k], oracle.back(g, sinos[k])) < 1e-5
 
 
+def test_batch_wide_cells(cnsf):
+    """Cells ten times wider than the pixels: the forward walk's window exceeds 8 candidates
+    per line (the batched kernel's generic-width path); batched, single and oracle agree."""
+    g = FanGeometry(nx=40, ny=36, n_views=20, n_det=24, pixel=0.2, det_spacing=2.0, det_width=2.0,
+                    d_po=30.0, d_ps=60.0)
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(41)
+    imgs = rng.uniform(0, 1, (5, g.ny, g.nx))
+    sinos = rng.uniform(0, 1, (5, g.n_views, g.n_det))
+    fb = cnsf.forward_project(geom, torch.tensor(imgs, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    bb = cnsf.back_project(geom, torch.tensor(sinos, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    for k in (0, 4):
+        fk = _fwd(cnsf, geom, imgs[k], torch.float32)
+        assert rel(fb[k], fk) < 1e-6
+        assert rel(fb[k], oracle.forward(g, imgs[k])) < 1e-5
+        assert rel(bb[k], oracle.back(g, sinos[k])) < 1e-5
+
+
 def test_empty_batch_and_errors(cnsf):
     g = config_geometry(1)
     geom = cnsf.Geometry(g)

@@ -293,14 +293,19 @@ def test_e4_ladder_smallest_rung(cnsf, dt):
     assert rel(_bwd(cnsf, geom, y_ref, dt), oracle.back(g, y_ref)) < TOL[dt]
 
 
-@pytest.mark.parametrize("which", ["config3_2048", "ladder_2048"])
+@pytest.mark.parametrize("which", ["config3_2048", "ladder_2048", "views_1840"])
 def test_largest_workloads_sampled(cnsf, which):
     """The largest sizes the bench runs, FP32, in its launch configuration: the 2048^2 x 1440
     x 1536 reconstruction geometry and the 2048 mm / 6499-cell rung of the run-time ladder;
-    sampled rays and pixels against the oracle, and the adjoint identity on the full
-    arrays."""
+    and 2048^2 with 1840 views, whose back-projection tile coefficients (1.08 GB) exceed the
+    geometry's 1 GiB table, so the kernel forms them itself.  Sampled rays and pixels against
+    the oracle, and the adjoint identity on the full arrays."""
+    import dataclasses
     from synth import e4_geometry
-    g = config_geometry(3) if which == "config3_2048" else e4_geometry(2048)
+    if which == "views_1840":
+        g = dataclasses.replace(config_geometry(3), n_views=1840)
+    else:
+        g = config_geometry(3) if which == "config3_2048" else e4_geometry(2048)
     geom = cnsf.Geometry(g)
     img = ellipse_phantom(2048, 20, 2.0, seed=33)
     c = torch.tensor(img, dtype=torch.float32, device="cuda")

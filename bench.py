@@ -419,26 +419,40 @@ def bench_solvers(dev, iters: int = 50):
 
 def bench_batch16(dev, steps: int = 5):
     """16 FP32 512^2 images (seeds 400-415), 888 cells x 360 views: one batched forward and
-    one batched back projection, pixel*view updates/s."""
+    one batched back projection, pixel*view updates/s, and each direction's time against the
+    FP32 peak with the batch's algorithmic work: per non-zero entry its 19 operations once
+    plus one FMA per image."""
     import torch
     import paper_1907_10526_gb300 as cnsf
     from synth import config_geometry, phantom_for_config
     g = config_geometry(4)
     geom = cnsf.Geometry(g)
-    x = torch.tensor(np.stack([phantom_for_config(4, b) for b in range(16)]), dtype=torch.float32, device=dev)
+    nb = 16
+    x = torch.tensor(np.stack([phantom_for_config(4, b) for b in range(nb)]), dtype=torch.float32, device=dev)
     y = cnsf.forward_project(geom, x)
     c = cnsf.back_project(geom, y)
     torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fp, bp = [], []
     for _ in range(steps):
+        ev[0].record()
         cnsf.forward_project(geom, x, out=y)
+        ev[1].record()
         cnsf.back_project(geom, y, out=c)
-    t1.record()
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1) / steps
-    return {"ms_per_fp_bp": ms, "updates_per_s": 16 * g.nx * g.ny * g.n_views / (ms * 1e-3)}
+        ev[2].record()
+        torch.cuda.synchronize()
+        fp.append(ev[0].elapsed_time(ev[1]))
+        bp.append(ev[1].elapsed_time(ev[2]))
+    fp_ms, bp_ms = statistics.mean(fp), statistics.mean(bp)
+    ms = fp_ms + bp_ms
+    nnz = cnsf.count_nonzeros(geom)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = _measured_peaks().get("sm_max_mhz") or 2070.0
+    peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+    ops = (ALG_OPS_PER_ENTRY + nb) * nnz
+    return {"ms_per_fp_bp": ms, "updates_per_s": nb * g.nx * g.ny * g.n_views / (ms * 1e-3),
+            "fp_ms": fp_ms, "bp_ms": bp_ms, "entries_per_launch": nnz, "ops_per_entry": ALG_OPS_PER_ENTRY + nb,
+            "fp_frac": ops / (fp_ms * 1e-3) / peak_ops, "bp_frac": ops / (bp_ms * 1e-3) / peak_ops}
 
 
 def bench_e4_ladder(dev, reps: int = 3):

@@ -73,3 +73,25 @@ def test_zs_changes_by_h_squared_per_step():
         # column step: (D_n, y') -> (D_n - hs, y' + hc)
         assert np.isclose(za(dn - hs, yp + hc), za(dn, yp) + h * h, atol=1e-9 * 1000)
         assert np.isclose(zb(dn - hs, yp + hc), zb(dn, yp), atol=1e-9 * 1000)
+
+
+def test_pair_steps_cover_the_window():
+    """The pair loop's index arithmetic: pairs of parity o = g0 mod 2 (cells 2m + o,
+    2m + o + 1) for m from g0 >> 1 to (g1 - o) >> 1 cover every cell of [g0, g1], reach at
+    most one cell past g1, take ceil(L/2) steps for a window of L cells, and never index a
+    pair beyond ceil(n_det / 2) - 1 when g1 <= n_det - 1."""
+    for nd in range(1, 40):
+        ndh = (nd + 1) // 2
+        for g0 in range(0, nd):
+            for g1 in range(g0, nd):
+                o = g0 & 1
+                m0, m1 = g0 >> 1, (g1 - o) >> 1
+                cells = {2 * m + o + k for m in range(m0, m1 + 1) for k in (0, 1)}
+                assert set(range(g0, g1 + 1)) <= cells
+                assert max(cells) <= g1 + 1 and min(cells) == g0
+                assert m1 - m0 + 1 == (g1 - g0 + 2) // 2
+                assert 0 <= m0 and m1 <= ndh - 1
+        # a window that misses the detector (g0 > g1 after clipping) takes no step
+        for g0 in range(nd, nd + 3):
+            o = g0 & 1
+            assert (g0 >> 1) > ((nd - 1 - o) >> 1) or nd == 0

@@ -128,49 +128,152 @@ __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__res
     acc.add(part);
 }
 
+// One ray's walk over its lines [l0, l1), a part of [R.r0, R.r0 + R.nrows), added to acc.
 template <int NB4>
-__global__ void __launch_bounds__(128) fp_batch_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
-                                                       const BoxF *__restrict__ box,
-                                                       float h2q, const float4 *__restrict__ P,
-                                                       const float4 *__restrict__ Tt, int pitchP, int pitchT,
-                                                       int pad, int nr, float *__restrict__ sino, int b0,
-                                                       int nb_used)
+__device__ __forceinline__ void fp_batch_walk_lines(RayF R, int l0, int l1, const float4 *__restrict__ P,
+                                                    const float4 *__restrict__ Tt, int pitchP, int pitchT, int pad,
+                                                    float B, float p, float qiC, float iC, float hC, Acc<NB4> &acc)
 {
-    const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
-    if (q >= nr) return;
-    RayF R = rays[q];
-    Acc<NB4> acc;
-    acc.zero();
-    if (R.nrows > 0) {
-        const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
-        const float p = bx.x, qiC = bx.y, iC = bx.z, hC = bx.w;
-        const float B = 2.f * (p + hC);
-        tighten_window(R, p, hC, B);
-        const bool tr = (R.flags & 1) != 0;
-        const int pitch = tr ? pitchT : pitchP;
-        const float4 *base = (tr ? Tt : P) + ((long long)R.r0 * pitch + pad) * NB4;
-        const int p4 = pitch * NB4;
-        switch (R.kc) {
-            case 1: fp_batch_walk<1, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            case 2: fp_batch_walk<2, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            case 3: fp_batch_walk<3, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            case 4: fp_batch_walk<4, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            case 5: fp_batch_walk<5, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            case 6: fp_batch_walk<6, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            case 7: fp_batch_walk<7, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            case 8: fp_batch_walk<8, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-            default: fp_batch_walk<0, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        }
-        const float nrm = h2q / (p + hC);
+    if (l1 <= l0) return;
+    const int k = l0 - R.r0;
+    R.A0 += (long long)k * R.G;
+    R.e0 += (float)k * R.de;
+    R.r0 = l0;
+    R.nrows = l1 - l0;
+    const bool tr = (R.flags & 1) != 0;
+    const int pitch = tr ? pitchT : pitchP;
+    const float4 *base = (tr ? Tt : P) + ((long long)R.r0 * pitch + pad) * NB4;
+    const int p4 = pitch * NB4;
+    switch (R.kc) {
+        case 1: fp_batch_walk<1, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 2: fp_batch_walk<2, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 3: fp_batch_walk<3, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 4: fp_batch_walk<4, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 5: fp_batch_walk<5, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 6: fp_batch_walk<6, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 7: fp_batch_walk<7, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 8: fp_batch_walk<8, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        default: fp_batch_walk<0, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+    }
+}
+
+// Trapezoid constants of one ray (Eq. 16 widths): p, q/C, 1/C, C/2 and B = 2(p + C/2).
+struct RayBox {
+    float p, qiC, iC, hC, B;
+};
+
+// Two adjacent rays of one view (cells j, j + 1) walking the same line family, over the
+// lines both walk: on each line the candidates of the two windows' union are loaded once
+// (the chunk's 16 NB4 bytes per candidate are what bounds this kernel) and evaluated for
+// both rays.  A candidate outside one ray's own window lies outside its support, so its
+// entry for that ray is exactly 0 (image pixels lie in front of the source, so tau'/2 > 0
+// there; padding pixels are 0).  The union lies between the two windows, inside the padded
+// line.
+template <int NB4>
+__device__ __forceinline__ void fp_batch_walk_joint(const RayF &Ra, const RayF &Rb, const RayBox &Xa,
+                                                    const RayBox &Xb, int j0, int j1, const float4 *__restrict__ base,
+                                                    int p4, Acc<NB4> &acca, Acc<NB4> &accb)
+{
+    long long Aa = Ra.A0 + (long long)(j0 - Ra.r0) * Ra.G + 0xFFFFFFFFLL;   // ceil-ready states
+    long long Ab = Rb.A0 + (long long)(j0 - Rb.r0) * Rb.G + 0xFFFFFFFFLL;
+    float era = Ra.e0 + (float)(j0 - Ra.r0) * Ra.de, erb = Rb.e0 + (float)(j0 - Rb.r0) * Rb.de;
+    Acc<NB4> parta, partb;
+    parta.zero();
+    partb.zero();
+    for (int L = j0; L < j1; ++L) {
+        const int ia = (int)(Aa >> 32), ib = (int)(Ab >> 32);
+        const float ua0 = fmaf(__uint2float_rn((unsigned)Aa), -1.0f / 4294967296.0f, 1.0f) - Ra.hw;
+        const float ub0 = fmaf(__uint2float_rn((unsigned)Ab), -1.0f / 4294967296.0f, 1.0f) - Rb.hw;
+        const int lo = min(ia, ib), hi = max(ia + Ra.kc, ib + Rb.kc);
+        for (int c = lo; c < hi; ++c) {
+            float4 v[NB4];
 #pragma unroll
-        for (int k = 0; k < NB4; ++k) {
-            acc.v[k].x *= nrm; acc.v[k].y *= nrm; acc.v[k].z *= nrm; acc.v[k].w *= nrm;
+            for (int k = 0; k < NB4; ++k) v[k] = __ldg(base + (long long)c * NB4 + k);
+            const float ua = ua0 + (float)(c - ia), ub = ub0 + (float)(c - ib);
+            const float ea = fmaf(Ra.kap, ua, era), eb = fmaf(Rb.kap, ub, erb);
+            const float da = window_diff(fabsf(Xa.B * ua), ea, Xa.p, Xa.qiC, Xa.iC, Xa.hC);
+            const float db = window_diff(fabsf(Xb.B * ub), eb, Xb.p, Xb.qiC, Xb.iC, Xb.hC);
+            parta.fma_with(da * rcp_approx(ea), v);
+            partb.fma_with(db * rcp_approx(eb), v);
+        }
+        Aa += Ra.G;
+        Ab += Rb.G;
+        era += Ra.de;
+        erb += Rb.de;
+        base += p4;
+        if (((L - j0) & 15) == 15) {   // blocked summation: partial sums of 16 lines
+            acca.add(parta);
+            accb.add(partb);
+            parta.zero();
+            partb.zero();
         }
     }
-    const float *a = reinterpret_cast<const float *>(acc.v);
+    acca.add(parta);
+    accb.add(partb);
+}
+
+// Two rays per thread: rays 2t and 2t + 1 of a block's 128 (64 threads), walked jointly
+// over their common lines when they are adjacent cells of one view with the same walk axis,
+// each alone over the rest of its lines; otherwise each alone.  The pairing does not depend
+// on the batch, so neither does any image's result.
+template <int NB4>
+__global__ void __launch_bounds__(64) fp_batch_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
+                                                      const BoxF *__restrict__ box,
+                                                      float h2q, const float4 *__restrict__ P,
+                                                      const float4 *__restrict__ Tt, int pitchP, int pitchT,
+                                                      int pad, int nr, int nd, float *__restrict__ sino, int b0,
+                                                      int nb_used)
+{
+    const int q = order[blockIdx.x] * 128 + 2 * threadIdx.x;   // longest walks first
+    if (q >= nr) return;
+    const bool has1 = q + 1 < nr;
+    RayF R[2];
+    RayBox X[2];
+    Acc<NB4> acc[2];
 #pragma unroll
-    for (int k = 0; k < 4 * NB4; ++k)
-        if (k < nb_used) sino[(long long)(b0 + k) * nr + q] = a[k];
+    for (int s = 0; s < 2; ++s) {
+        R[s] = rays[s == 0 || !has1 ? q : q + 1];
+        const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + (s == 0 || !has1 ? q : q + 1)));
+        X[s].p = bx.x; X[s].qiC = bx.y; X[s].iC = bx.z; X[s].hC = bx.w;
+        X[s].B = 2.f * (bx.x + bx.w);
+        if (R[s].nrows > 0) tighten_window(R[s], X[s].p, X[s].hC, X[s].B);
+        acc[s].zero();
+    }
+    const int la0 = R[0].r0, la1 = R[0].r0 + max(R[0].nrows, 0);
+    const int lb0 = R[1].r0, lb1 = R[1].r0 + max(R[1].nrows, 0);
+    const int j0 = max(la0, lb0), j1 = min(la1, lb1);
+    const bool joint = has1 && (q + 1) % nd != 0 && R[0].nrows > 0 && R[1].nrows > 0 &&
+                       (R[0].flags & 1) == (R[1].flags & 1) && j0 < j1;
+    if (joint) {
+        // each ray alone before and after the common lines, then both together
+        fp_batch_walk_lines<NB4>(R[0], la0, j0, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].p, X[0].qiC, X[0].iC,
+                                 X[0].hC, acc[0]);
+        fp_batch_walk_lines<NB4>(R[0], j1, la1, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].p, X[0].qiC, X[0].iC,
+                                 X[0].hC, acc[0]);
+        fp_batch_walk_lines<NB4>(R[1], lb0, j0, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].p, X[1].qiC, X[1].iC,
+                                 X[1].hC, acc[1]);
+        fp_batch_walk_lines<NB4>(R[1], j1, lb1, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].p, X[1].qiC, X[1].iC,
+                                 X[1].hC, acc[1]);
+        const bool tr = (R[0].flags & 1) != 0;
+        const int pitch = tr ? pitchT : pitchP;
+        const float4 *base = (tr ? Tt : P) + ((long long)j0 * pitch + pad) * NB4;
+        fp_batch_walk_joint<NB4>(R[0], R[1], X[0], X[1], j0, j1, base, pitch * NB4, acc[0], acc[1]);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+            if ((s == 0 || has1) && R[s].nrows > 0)
+                fp_batch_walk_lines<NB4>(R[s], R[s].r0, R[s].r0 + R[s].nrows, P, Tt, pitchP, pitchT, pad, X[s].B,
+                                         X[s].p, X[s].qiC, X[s].iC, X[s].hC, acc[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        if (s == 1 && !has1) break;
+        const float nrm = R[s].nrows > 0 ? h2q / (X[s].p + X[s].hC) : 0.f;
+        const float *a = reinterpret_cast<const float *>(acc[s].v);
+#pragma unroll
+        for (int k = 0; k < 4 * NB4; ++k)
+            if (k < nb_used) sino[(long long)(b0 + k) * nr + q + s] = a[k] * nrm;
+    }
 }
 
 // ------------------------------------------------------------------ back
@@ -337,15 +440,15 @@ int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino
             img, P, g.nx, g.ny, pad, pitchP, b0, used, NB, 0);
         pad_interleave_kernel<<<(unsigned)std::min<long long>((nT + 255) / 256, 8192), 256, 0, st>>>(
             img, Tt, g.nx, g.ny, pad, pitchT, b0, used, NB, 1);
-        dim3 blk(128), grd((nr + 127) / 128);
+        dim3 blk(64), grd((nr + 127) / 128);   // two rays per thread, 128 per block
         const float h2q = (float)(0.25 * g.h * g.h);
         const float4 *P4 = reinterpret_cast<const float4 *>(P), *T4 = reinterpret_cast<const float4 *>(Tt);
         if (nb4 == 4)
-            fp_batch_kernel<4><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+            fp_batch_kernel<4><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
         else if (nb4 == 2)
-            fp_batch_kernel<2><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+            fp_batch_kernel<2><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
         else
-            fp_batch_kernel<1><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, sino, b0, used);
+            fp_batch_kernel<1><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
         b0 += used;
     }
     cudaFreeAsync(buf, st);

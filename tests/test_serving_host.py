@@ -23,3 +23,53 @@ def test_summary_percentiles():
     assert s["completed"] == 100 and s["rejected"] == 1
     assert s["p50_s"] == pytest.approx(0.50) and s["p99_s"] == pytest.approx(0.99)
     assert s["recons_per_s"] == pytest.approx(100 / 1.0)
+
+
+def _host_server(budget, max_batch=4, fp=None, bfp=None):
+    """A ReconServer without a device: only the admission logic is exercised, with the
+    footprints given as functions of the request shape."""
+    pytest.importorskip("torch")
+    from paper_1907_10526_gb300.serve import ReconServer
+    s = object.__new__(ReconServer)
+    s.budget, s.max_batch, s.max_active = budget, max_batch, 8
+    s.footprint = fp or (lambda n, v: n * 10)
+    s.batch_footprint = bfp or (lambda n, v, b: n * 10 * b + 5)
+    return s
+
+
+def _req(rid, n, v, iters=20):
+    from paper_1907_10526_gb300.serve import ReconRequest
+    return ReconRequest(rid, 0.001 * rid, n, v, sino=None, iters=iters)
+
+
+def test_admission_one_request_per_job():
+    from collections import deque
+    s = _host_server(budget=1000)
+    q = deque([_req(0, 50, 180)])
+    assert s._take_job(q, "continuous", used=0) == ("run", [q[0]], 500)
+    assert s._take_job(q, "continuous", used=600) is None          # fits later
+    q = deque([_req(1, 200, 180)])
+    kind, reqs, nbytes = s._take_job(q, "sequential", used=0)
+    assert kind == "reject" and reqs == [q[0]] and nbytes == 2000  # never fits
+
+
+def test_admission_batches_same_shape_in_arrival_order():
+    from collections import deque
+    s = _host_server(budget=10_000, max_batch=3)
+    reqs = [_req(0, 50, 180), _req(1, 60, 180), _req(2, 50, 180), _req(3, 50, 360), _req(4, 50, 180),
+            _req(5, 50, 180), _req(6, 50, 180, iters=10)]
+    kind, job, nbytes = s._take_job(deque(reqs), "batched", used=0)
+    # the head and the next waiting requests of its shape and iteration count, up to max_batch
+    assert kind == "run" and [r.rid for r in job] == [0, 2, 4] and nbytes == 50 * 10 * 3 + 5
+
+
+def test_admission_batch_shrinks_to_the_memory_left():
+    from collections import deque
+    s = _host_server(budget=10_000, max_batch=8)
+    reqs = deque(_req(i, 100, 180) for i in range(8))
+    kind, job, nbytes = s._take_job(reqs, "batched", used=10_000 - 3 * 1000 - 5)
+    assert kind == "run" and len(job) == 3 and nbytes == 3005
+    assert s._take_job(reqs, "batched", used=10_000 - 500) is None       # not even one now
+    big = _host_server(budget=900, max_batch=8)
+    kind, job, _ = big._take_job(deque([_req(0, 100, 180)]), "batched", used=0)
+    assert kind == "reject" and [r.rid for r in job] == [0]

@@ -98,8 +98,8 @@ int build_tile_view_table(cnsf_geometry *geo)
 // values are one addition away): the cell coordinate sigma (minus J) and, for the arc
 // detector, the sine-series factor G.  Flat or parallel detector: sigma is the ratio of
 // two affine functions of the pixel offset (perspective division, Eq. 4).  Arc detector:
-// the angle from the tile centre's ray, atan of (y' Dt - yt D_n)/(D_n Dt + y' yt) (a
-// numerator without constant term), in cells.
+// the angle from the ray through the tile's reference point, atan of
+// (y' Dt - yt D_n)/(D_n Dt + y' yt) (a numerator without constant term), in cells.
 struct BpPixel {
     float Dn, yp, sig, G;
 };
@@ -133,10 +133,10 @@ __device__ __forceinline__ float bp_quad_hwc(const TileViewS<float> &T, float Dn
     return fmaf(a.kz * zs * rD * rD, fmaf(a.h2, rD, 1.02f), a.ke);
 }
 
-// The two entries of cell pair (2m, 2m + 1) for one pixel in packed FP32x2 arithmetic,
-// without the factor 2/B of the normalisation h^2/(2B) (the caller folds it into the
-// sinogram weights, once for both pixels of a pair) and without h^2/4 (applied to the sum):
-// the window difference divided by tau'.  d holds the two cells' offsets from the pixel's
+// The two entries of one cell pair (cells 2m + o, 2m + o + 1 of the tables of parity o)
+// for one pixel in packed FP32x2 arithmetic, without the factor 2/B of the normalisation
+// h^2/(2B) (the caller folds it into the sinogram weights, once for both pixels of a pair)
+// and without h^2/4 (applied to the sum): the window difference divided by tau'.  d holds the two cells' offsets from the pixel's
 // projection, in cells; qiC = q/C.  Arc detector: |s'| = R sin(dg d), R the pixel's
 // distance from the source; with dg d below ~0.05 rad, R dg d (1 - (dg d)^2/6) is that sine
 // to ~1e-9 relative (the next term of the series).

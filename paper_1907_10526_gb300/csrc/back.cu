@@ -2,9 +2,10 @@
 //
 // Pixel-driven gather, no atomics.  A block owns a 16 x 16 pixel tile; for each view the
 // pixel centre is projected onto the detector (perspective division, Eq. 4) and the cells
-// its footprint reaches are gathered.  The projection of the tile centre is computed once
-// per view in FP64 (tile_view_double) and split into an integer cell index plus a small
-// remainder, so that FP32 carries the sub-cell position of every pixel to ~1e-6 cells;
+// its footprint reaches are gathered.  The projection of the tile's reference point (the
+// centre of the tile's part inside the image) is computed once per view in FP64
+// (tile_view_double) and split into an integer cell index plus a small remainder, so that
+// FP32 carries the sub-cell position of every pixel to ~1e-6 cells;
 // the per-pixel work is then a handful of FP32 FMAs and one reciprocal.  The cell window
 // is bounded per pixel from the footprint widths of the ray through the pixel centre
 // (BpWindow), so few cells outside the support are visited.  In FP32 a thread owns a 2 x 2

@@ -41,7 +41,7 @@ struct BpArgs {
     int cell_odd;       // and 8 ceil(n_det/2)
 };
 
-// The FP32 per-(tile, view) coefficients from the FP64 projection of the tile centre.
+// The FP32 per-(tile, view) coefficients from the FP64 projection of the tile's reference point.
 __device__ __forceinline__ void tile_view_f32(const GeomConsts &g, double c, double s, double it, double rt,
                                               TileViewS<float> &T, int &J)
 {

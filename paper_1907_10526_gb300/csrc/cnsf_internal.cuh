@@ -155,7 +155,7 @@ __host__ __device__ inline BoxConsts<T> make_box_consts(double B, double C, doub
 }
 
 // Per (pixel tile, view) coefficients of the back projector.  For the pixel at offset
-// (di, dr) from the tile origin:
+// (di, dr) from the tile's reference point:
 //   D_n   = Dt + aD di + bD dr            (depth of the pixel centre along u from the source)
 //   y'    = yt + ay di + by dr            (coordinate along w)
 //   sigma = J + phi + (rho + a1 di + b1 dr) / D_n
@@ -168,11 +168,12 @@ struct TileView {
     int J;
 };
 
-// (it, rt) is the reference point of the tile in pixel-index units (its centre, so that the
-// per-pixel offsets stay small).  (hc, hs) = h (cos, sin) is the per-pixel step of the depth.
+// (it, rt) is the reference point of the tile in pixel-index units (the centre of the
+// tile's part inside the image, so that the per-pixel offsets stay small and the point lies
+// in front of the source).  (hc, hs) = h (cos, sin) is the per-pixel step of the depth.
 // Parallel beam: the projection is affine, sigma = (y' - s_0)/ds; the depth is held at
 // D_n = 1 (hc = hs = 0) so that the same per-pixel arithmetic applies.
-// Arc detector: sigma = (D_ps atan2(y', D_n) - s_0)/ds.  Relative to the tile centre,
+// Arc detector: sigma = (D_ps atan2(y', D_n) - s_0)/ds.  Relative to the reference point,
 //   sigma = J + phi + (D_ps/ds) atan((a1 di + b1 dr) / (D_n Dt + y' yt)),
 // where a1 di + b1 dr = y' Dt - yt D_n exactly (no constant term, so no cancellation), and
 // rho = 0.

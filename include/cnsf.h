@@ -93,8 +93,8 @@ typedef struct {
 
 /* Build a geometry and its device tables on the current device (Sec. II.A and
  * Eq. 17: per-view rotations, per-cell effective-blur slopes, per-ray walk
- * tables).  Synchronous.  Rejects (CNSF_ERR_INVALID): non-positive sizes or
- * lengths and, for the fan beams, d_ps <= d_po and images that reach within two
+ * tables).  Synchronous.  Rejects (CNSF_ERR_INVALID): non-positive sizes,
+ * non-positive or non-finite lengths, offsets or view angles and, for the fan beams, d_ps <= d_po and images that reach within two
  * pixels of the source circle (the footprint model needs every pixel in front of the
  * source), and arcs that reach 80 degrees from -u; CNSF_ERR_UNSUPPORTED for an unknown
  * detector kind or n_views * n_det or n_x * n_y of 2^31 or more.

@@ -50,6 +50,12 @@ extern "C" {
 int cnsf_geometry_create(const cnsf_geometry_desc *desc, cnsf_geometry **out)
 {
     try {
+        // lengths must be finite as well as positive (the geometry builder checks the rest)
+        if (desc && (!std::isfinite(desc->pixel_mm) || !std::isfinite(desc->det_spacing_mm) ||
+                     !std::isfinite(desc->det_width_mm) ||
+                     (desc->detector != CNSF_DETECTOR_PARALLEL &&
+                      (!std::isfinite(desc->d_po_mm) || !std::isfinite(desc->d_ps_mm)))))
+            return CNSF_ERR_INVALID;
         return build_geometry(desc, out);
     } catch (const std::bad_alloc &) {
         return CNSF_ERR_NOMEM;

@@ -1,6 +1,7 @@
 """The C ABI library builds for sm_103a, loads without a GPU and exports every function
 that include/cnsf.h declares; invalid geometries are refused before any CUDA call."""
 import ctypes
+import math
 import os
 import re
 
@@ -52,6 +53,24 @@ def test_invalid_geometries_refused_without_gpu():
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_UNSUPPORTED
     assert lib.cnsf_forward_project(None, None, None, 1, 0, None) == CNSF_ERR_INVALID
     assert lib.cnsf_status_string(0) == b"ok"
+    # the source must stay 2 pixels outside the circle through the image corners
+    r = math.hypot(4.0, 4.0)
+    edge = GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 1, 0, r + 2.0, 60, 0)
+    assert lib.cnsf_geometry_create(ctypes.byref(edge), ctypes.byref(h)) == CNSF_ERR_INVALID
+    # non-finite sizes and angles
+    nan = float("nan")
+    for d in (GeometryDesc(8, 8, nan, 0, 0, 4, None, 8, 1, 1, 0, 30, 60, 0),
+              GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, float("inf"), 0, 30, 60, 0),
+              GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, float("inf"), 1, 0, 30, 60, 0),
+              GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 30, float("inf"), 0)):
+        assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
+    ang = (ctypes.c_double * 4)(0.0, 0.5, nan, 1.5)
+    d = GeometryDesc(8, 8, 1.0, 0, 0, 4, ang, 8, 1, 1, 0, 30, 60, 0)
+    assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
+    # queries refuse missing arguments before touching a device
+    n = ctypes.c_size_t()
+    assert lib.cnsf_projection_scratch_bytes(None, 0, 1, 0, ctypes.byref(n)) == CNSF_ERR_INVALID
+    assert lib.cnsf_plan_create(None, 0, None, None, 1, 0, None) == CNSF_ERR_INVALID
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -137,6 +137,14 @@ def _prep(x: torch.Tensor, inner: tuple, what: str):
 
 
 def _run(fn, name, geom: Geometry, x: torch.Tensor, in_shape, out_shape, out, stream):
+    if stream is not None:
+        # the torch-side copies and allocations go on the same stream as the kernels
+        with torch.cuda.stream(stream):
+            return _run_on_stream(fn, name, geom, x, in_shape, out_shape, out, stream)
+    return _run_on_stream(fn, name, geom, x, in_shape, out_shape, out, stream)
+
+
+def _run_on_stream(fn, name, geom: Geometry, x: torch.Tensor, in_shape, out_shape, out, stream):
     lead, batch = _prep(x, in_shape, name)
     host_in = x.device.type != "cuda"
     dev = geom.device
@@ -167,8 +175,9 @@ def forward_project(geom: Geometry, image: torch.Tensor, out: Optional[torch.Ten
                     stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
     """y = A c.  image [..., ny, nx] float32/float64 -> sinogram [..., n_views, n_det].
 
-    A CUDA tensor runs asynchronously on ``stream`` (default: current stream).  A CPU
-    tensor is copied to the geometry's device, projected there and copied back.
+    A CUDA tensor runs asynchronously on ``stream`` (default: current stream; the
+    binding's own copies and allocations go on it too).  A CPU tensor is copied to the
+    geometry's device, projected there and copied back.
     """
     return _run(lib.cnsf_forward_project, "cnsf_forward_project", geom, image, geom.image_shape,
                 geom.sino_shape, out, stream)

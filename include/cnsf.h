@@ -89,7 +89,34 @@ typedef struct {
     double d_po_mm;            /* source to rotation centre (D_po); fan beams only    */
     double d_ps_mm;            /* source to detector (D_ps > D_po); fan beams only    */
     int32_t detector;          /* cnsf_detector: FLAT, ARC or PARALLEL               */
+    int32_t options;           /* cnsf_option bits (0: the library chooses)          */
 } cnsf_geometry_desc;
+
+/* Choices of evaluation that leave the operator unchanged (the paper has no counterpart;
+ * they select among implementations of the same entries of Eq. 18).
+ *   CNSF_OPT_NO_SYMMETRY: never use the quarter-turn symmetry below.  By default, when the
+ *     image is square (n_x = n_y) and centred on the rotation axis (center_x = center_y = 0),
+ *     and the views are closed under a quarter turn (n_views divisible by 4 and, for given
+ *     angles, angles_rad[k + n_views/4] = angles_rad[k] + pi/2 to 1e-12 rad), the view
+ *     v + k n_views/4 sees the image of view v turned by k quarter turns, a quarter turn maps
+ *     the pixel lattice onto itself, and so every entry a(v + k n_views/4, j, n) equals
+ *     a(v, j, n turned back by k quarter turns).  The FP32 single-image projections then
+ *     evaluate each distinct entry once and apply it to the four (view, pixel) pairs it
+ *     belongs to.  Results agree with the general kernels to FP32 rounding.
+ *   CNSF_OPT_EXACT_DIFFERENCES / CNSF_OPT_PLAIN_DIFFERENCES: how the FP32 kernels form the
+ *     window difference of Eq. (18), B H(s'+tau'/2) - B H(s'-tau'/2) (H the antiderivative of
+ *     the footprint trapezoid).  PLAIN subtracts the two antiderivative values (relative error
+ *     ~ 6e-8 B / tau' per entry); EXACT adds the trapezoid's pieces over the window, which
+ *     are non-negative, with the cut points taken relative to s' (error ~ 1e-7 whatever
+ *     tau'), at about twice the cost.  With neither bit the geometry takes EXACT when the
+ *     smallest effective blur tau' of any entry falls below B/32 (PLAIN would lose more than
+ *     five bits there) and PLAIN otherwise; cnsf_geometry_paths reports the choice.  FP64
+ *     always uses the plain form (its error ~1e-16 B/tau'). */
+typedef enum {
+    CNSF_OPT_NO_SYMMETRY = 1,
+    CNSF_OPT_EXACT_DIFFERENCES = 2,
+    CNSF_OPT_PLAIN_DIFFERENCES = 4
+} cnsf_option;
 
 /* Build a geometry and its device tables on the current device (Sec. II.A and
  * Eq. 17: per-view rotations, per-cell effective-blur slopes, per-ray walk
@@ -104,6 +131,12 @@ CNSF_API int cnsf_geometry_create(const cnsf_geometry_desc *desc, cnsf_geometry 
 /* Release a geometry (NULL is allowed).  The caller must first make sure that no
  * work launched with it is still pending. */
 CNSF_API void cnsf_geometry_destroy(cnsf_geometry *geom);
+
+/* The evaluation paths a geometry's FP32 single-image projections take (the paper has no
+ * counterpart): *symmetric = 1 when entries are reused across the quarter-turn symmetry,
+ * *exact_differences = 1 when the window differences are formed piece by piece (see
+ * cnsf_option).  Either pointer may be NULL. */
+CNSF_API int cnsf_geometry_paths(const cnsf_geometry *geom, int32_t *symmetric, int32_t *exact_differences);
 
 /* Sizes of a geometry: any output pointer may be NULL. */
 CNSF_API int cnsf_geometry_shape(const cnsf_geometry *geom, int32_t *n_x, int32_t *n_y, int32_t *n_views,

@@ -15,7 +15,8 @@ from typing import Optional
 
 import torch
 
-from ._lib import CNSF_DETECTOR, CNSF_F32, CNSF_F64, AsdPocsParams, CnsfError, GeometryDesc, check, lib  # noqa: F401
+from ._lib import (CNSF_DETECTOR, CNSF_F32, CNSF_F64, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_NO_SYMMETRY,  # noqa: F401
+                   CNSF_OPT_PLAIN_DIFFERENCES, AsdPocsParams, CnsfError, GeometryDesc, check, lib)
 
 __all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
            "count_nonzeros", "forward_project_noalloc", "asd_pocs", "Plan",
@@ -44,9 +45,16 @@ class Geometry:
     n_det, pixel, det_spacing, det_width, d_po, d_ps, center_x, center_y, det_offset,
     angles, and optionally detector = "flat" | "arc" | "parallel") or from the same names as
     keyword arguments.  The tables live on ``device`` (default: the current CUDA device).
+
+    ``symmetry`` (default True) lets the FP32 single-image projections reuse each entry over
+    the quarter turns of the acquisition when it has that symmetry (square image centred on
+    the rotation axis, views closed under a quarter turn); ``differences`` ("auto", "plain"
+    or "exact") selects how the FP32 kernels form the window difference of Eq. (18) (see
+    ``cnsf_option`` in include/cnsf.h).  Neither changes the operator; ``paths`` reports the
+    choice the library made.
     """
 
-    def __init__(self, desc=None, device=None, **kw):
+    def __init__(self, desc=None, device=None, symmetry: bool = True, differences: str = "auto", **kw):
         if desc is None:
             from types import SimpleNamespace
             base = dict(pixel=1.0, det_spacing=1.0, det_width=1.0, d_po=500.0, d_ps=1000.0,
@@ -54,6 +62,7 @@ class Geometry:
             base.update(kw)
             desc = SimpleNamespace(**base)
         self.desc = desc
+        self._opts = {"symmetry": symmetry, "differences": differences}
         self.nx, self.ny = int(desc.nx), int(desc.ny)
         self.n_views, self.n_det = int(desc.n_views), int(desc.n_det)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
@@ -66,7 +75,9 @@ class Geometry:
                          self.n_views,
                          ctypes.cast(self._angles, ctypes.POINTER(ctypes.c_double)) if self._angles else None,
                          self.n_det, float(desc.det_spacing), float(desc.det_width), float(desc.det_offset),
-                         float(desc.d_po), float(desc.d_ps), CNSF_DETECTOR[getattr(desc, "detector", "flat")])
+                         float(desc.d_po), float(desc.d_ps), CNSF_DETECTOR[getattr(desc, "detector", "flat")],
+                         (0 if symmetry else CNSF_OPT_NO_SYMMETRY) |
+                         {"auto": 0, "plain": CNSF_OPT_PLAIN_DIFFERENCES, "exact": CNSF_OPT_EXACT_DIFFERENCES}[differences])
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(self._h)), "cnsf_geometry_create")
@@ -74,6 +85,15 @@ class Geometry:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def paths(self) -> dict:
+        """The evaluation paths of the FP32 single-image projections: ``symmetric`` (entries
+        reused over the quarter turns) and ``exact_differences`` (window differences formed
+        piece by piece)."""
+        sym, ex = ctypes.c_int32(), ctypes.c_int32()
+        check(lib.cnsf_geometry_paths(self.handle, ctypes.byref(sym), ctypes.byref(ex)), "cnsf_geometry_paths")
+        return {"symmetric": bool(sym.value), "exact_differences": bool(ex.value)}
 
     def view_angles(self):
         """The view angles (rad): the given ones, else 2 pi k / n_views."""
@@ -93,7 +113,8 @@ class Geometry:
             base["n_det"] = self.n_det
             base["detector"] = getattr(self.desc, "detector", "flat")
             views = [list(range(s, self.n_views, n)) for s in range(n)]
-            geoms = [Geometry(SimpleNamespace(n_views=len(v), angles=[ang[t] for t in v], **base), device=self.device)
+            geoms = [Geometry(SimpleNamespace(n_views=len(v), angles=[ang[t] for t in v], **base), device=self.device,
+                              **self._opts)
                      for v in views]
             cache[n] = (geoms, [t for v in views for t in v])
         return cache[n]

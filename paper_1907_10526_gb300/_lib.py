@@ -20,7 +20,7 @@ class GeometryDesc(ctypes.Structure):
         ("n_views", ctypes.c_int32), ("angles_rad", ctypes.POINTER(ctypes.c_double)),
         ("n_det", ctypes.c_int32), ("det_spacing_mm", ctypes.c_double), ("det_width_mm", ctypes.c_double),
         ("det_offset_mm", ctypes.c_double), ("d_po_mm", ctypes.c_double), ("d_ps_mm", ctypes.c_double),
-        ("detector", ctypes.c_int32),
+        ("detector", ctypes.c_int32), ("options", ctypes.c_int32),
     ]
 
 
@@ -37,12 +37,14 @@ class AsdPocsParams(ctypes.Structure):
 CNSF_OK, CNSF_ERR_INVALID, CNSF_ERR_CUDA, CNSF_ERR_NOMEM, CNSF_ERR_UNSUPPORTED, CNSF_ERR_INTERNAL = range(6)
 CNSF_F32, CNSF_F64 = 0, 1
 CNSF_DETECTOR = {"flat": 0, "arc": 1, "parallel": 2}
+CNSF_OPT_NO_SYMMETRY, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_PLAIN_DIFFERENCES = 1, 2, 4
 
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "cnsf_geometry_create": (ctypes.c_int, [ctypes.POINTER(GeometryDesc), ctypes.POINTER(_P)]),
     "cnsf_geometry_destroy": (None, [_P]),
     "cnsf_geometry_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int32)] * 4),
+    "cnsf_geometry_paths": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int32)] * 2),
     "cnsf_forward_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_back_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_forward_project_ref": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),

@@ -136,14 +136,14 @@ __device__ __forceinline__ float bp_quad_hwc(const TileViewS<float> &T, float Dn
 
 // The two entries of one cell pair (cells 2m + o, 2m + o + 1 of the tables of parity o)
 // for one pixel in packed FP32x2 arithmetic, without the factor 2/B of the normalisation
-// h^2/(2B) (the caller folds it into the sinogram weights, once for both pixels of a pair)
-// and without h^2/4 (applied to the sum): the window difference divided by tau'.  d holds the two cells' offsets from the pixel's
-// projection, in cells; qiC = q/C.  Arc detector: |s'| = R sin(dg d), R the pixel's
+// h^2/(2B) (the sinogram pairs carry it) and without h^2/4 (applied to the sum): the
+// window difference divided by tau'.  d holds the two cells' offsets from the pixel's
+// projection, in cells.  Arc detector: |s'| = R sin(dg d), R the pixel's
 // distance from the source; with dg d below ~0.05 rad, R dg d (1 - (dg d)^2/6) is that sine
 // to ~1e-9 relative (the next term of the series).
 template <bool ARC>
 __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const float (&A)[8], const float (&C)[8],
-                                              float2 qiC, float nk6)
+                                              float nk6)
 {
     const float2 ne1 = make_float2(-1.f, -1.f);
     float2 xs;
@@ -155,8 +155,8 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
     const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
     const float2 e = __ffma2_rn(make_float2(P.Dn, P.Dn), make_float2(C[2], C[3]),
                                 __fmul2_rn(make_float2(P.yp, P.yp), make_float2(C[4], C[5])));
-    const float2 w = window_diff2p(x, e, ne1, make_float2(A[0], A[1]), qiC, make_float2(A[4], A[5]),
-                                   make_float2(A[6], A[7]));
+    const float2 w = window_diff2p(x, e, ne1, make_float2(A[0], A[1]), make_float2(A[2], A[3]),
+                                   make_float2(A[4], A[5]), make_float2(A[6], A[7]));
     return __fmul2_rn(w, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
 }
 
@@ -191,12 +191,11 @@ __device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel 
     float2 acca = make_float2(0.f, 0.f), accb = make_float2(0.f, 0.f);
     for (int m = m0; m <= m1; ++m) {
         float A[8], C[8];
-        ldg256(boxrow + 8 * m, A);    // p | 2/B | 1/C | -C/2, pairs
+        ldg256(boxrow + 8 * m, A);    // q | p/C | 1/C | -C/2, pairs
         ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
-        const float2 yb = __fmul2_rn(__ldg(y2row + m), make_float2(A[2], A[3]));         // y 2/B
-        const float2 qiC = __ffma2_rn(make_float2(A[0], A[1]), make_float2(A[4], A[5]), make_float2(1.f, 1.f));
-        acca = __ffma2_rn(yb, bp_pair_f32<ARC>(Pa, da, A, C, qiC, a.nk6), acca);
-        accb = __ffma2_rn(yb, bp_pair_f32<ARC>(Pb, db, A, C, qiC, a.nk6), accb);
+        const float2 yb = __ldg(y2row + m);                                                  // y 2/B
+        acca = __ffma2_rn(yb, bp_pair_f32<ARC>(Pa, da, A, C, a.nk6), acca);
+        accb = __ffma2_rn(yb, bp_pair_f32<ARC>(Pb, db, A, C, a.nk6), accb);
         da = __fadd2_rn(da, m2);
         db = __fadd2_rn(db, m2);
     }
@@ -321,6 +320,202 @@ __global__ void bp_sum_parts_kernel(const float *__restrict__ partial, float *__
     }
 }
 
+// ------------------------------------------------------------------ four rotations
+// With the quarter-turn symmetry of fp_rot4_f32_kernel, a(v + kV/4, j, n) = a(v, j, R^-k n)
+// (R the quarter turn of the pixel lattice, (i, r) -> (N-1-r, i)), so
+//     (A^T y)[n] = sum_k T_k(R^-k n),   T_k(p) = sum_{v < V/4} sum_j y[v + kV/4][j] a(v, j, p).
+// Every pixel p gathers T_0 .. T_3 over the first quarter of the views: each entry a(v, j, p)
+// is evaluated once and weighs the four sinogram values y[v + kV/4][j], which a per-call table
+// holds together (one 32-byte entry per cell pair and view).  The orbit sum then adds
+// T_k(R^-k n) over k for every pixel n.
+
+// Y4[o][v][m] holds, for k = 0..3, the pair (w y[v + kV/4][2m + o], w' y[v + kV/4][2m + o + 1])
+// with w = 2/B of (v, cell) (the same for the four views: a quarter turn swaps the two widths
+// of Eq. 16), 0 past n_det; v < V/4.
+__global__ void sino_pairs_rot4_kernel(const float *__restrict__ y, const BoxF *__restrict__ box,
+                                       float4 *__restrict__ y4, int nv, int nd)
+{
+    const int ndh = (nd + 1) >> 1, nv4 = nv >> 2;
+    const long long n = 2LL * nv4 * ndh;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(t / ((long long)nv4 * ndh));
+        const long long rem = t - (long long)o * nv4 * ndh;
+        const int v = (int)(rem / ndh), m = (int)(rem - (long long)v * ndh);
+        const int j = 2 * m + o;
+        const BoxF *br = box + (long long)v * nd;
+        float out[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float *yr = y + (long long)(v + k * nv4) * nd;
+            out[2 * k] = j < nd ? yr[j] / (br[j].q - br[j].hC) : 0.f;
+            out[2 * k + 1] = j + 1 < nd ? yr[j + 1] / (br[j + 1].q - br[j + 1].hC) : 0.f;
+        }
+        y4[2 * t] = make_float4(out[0], out[1], out[2], out[3]);
+        y4[2 * t + 1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+}
+
+// bp_view2_f32 for the four rotations: the same window and cell pairs; each pair's entries
+// for pixels a and b are applied to the four weighted sinogram pairs of the step and added
+// to ta[k], tb[k] (lanes: the two cells of the pair).
+template <bool ARC>
+__device__ __forceinline__ void bp_view2_rot4(const BpPixel &Pa, const BpPixel &Pb, float hwc, int J, const BpArgs &a,
+                                              int nd, const float *__restrict__ y4row,
+                                              const float *__restrict__ y4orow, const float *__restrict__ boxrow,
+                                              const float *__restrict__ cell2, float2 (&ta)[4], float2 (&tb)[4])
+{
+    const float lo = fminf(Pa.sig, Pb.sig) - hwc, hi = fmaxf(Pa.sig, Pb.sig) + hwc;
+    const int g0 = J + max((int)ceilf(lo), -J), g1 = J + min((int)floorf(hi), nd - 1 - J);
+    const int odd = g0 & 1;
+    const int m0 = g0 >> 1, m1 = (g1 - odd) >> 1;   // m0 > m1 when the window misses the detector
+    if (odd) {   // pairs (2m + 1, 2m + 2)
+        boxrow += a.box_odd;
+        cell2 += a.cell_odd;
+        y4row = y4orow;
+    }
+    const float off = (float)(2 * m0 + odd - J);
+    float2 da = make_float2(Pa.sig - off, Pa.sig - off - 1.f), db = make_float2(Pb.sig - off, Pb.sig - off - 1.f);
+    const float2 m2 = make_float2(-2.f, -2.f);
+    for (int m = m0; m <= m1; ++m) {
+        float A[8], C[8], Y[8];
+        ldg256(boxrow + 8 * m, A);    // q | p/C | 1/C | -C/2, pairs
+        ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
+        ldg256(y4row + 8 * m, Y);     // y 2/B of the four rotations, pairs
+        const float2 wa = bp_pair_f32<ARC>(Pa, da, A, C, a.nk6), wb = bp_pair_f32<ARC>(Pb, db, A, C, a.nk6);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 yk = make_float2(Y[2 * k], Y[2 * k + 1]);
+            ta[k] = __ffma2_rn(yk, wa, ta[k]);
+            tb[k] = __ffma2_rn(yk, wb, tb[k]);
+        }
+        da = __fadd2_rn(da, m2);
+        db = __fadd2_rn(db, m2);
+    }
+}
+
+// bp_f32_kernel over the first quarter of the views with four accumulators per pixel: the
+// partial images T_k (view part s: partial[(4 s + k)][N][N]).  The quad's pixel pairs are
+// gathered along the axis that moves the projection least, the two pairings in two
+// branches (uniform over the block) so that every accumulator keeps its register.
+template <bool ARC>
+__global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomConsts g, const float *__restrict__ box2,
+                                                                     const float *__restrict__ cell2,
+                                                                     const float *__restrict__ y4, BpArgs a,
+                                                                     const int *__restrict__ order, int ntx, int nsplit,
+                                                                     float *__restrict__ partial,
+                                                                     const double *__restrict__ view_cs,
+                                                                     const float4 *__restrict__ tvtab,
+                                                                     const int *__restrict__ tjtab)
+{
+    __shared__ TileViewS<float> tv[BP_CHUNK];
+    __shared__ int tj[BP_CHUNK];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = 2 * (lane & 7), ty = 8 * warp + 2 * (lane >> 3);
+    const int tile = order[blockIdx.x];   // tiles with the most work first
+    const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
+    const int nv4 = g.nv >> 2;
+    const int vbeg = (int)((long long)nv4 * blockIdx.y / nsplit), vend = (int)((long long)nv4 * (blockIdx.y + 1) / nsplit);
+    const int i = it + tx, r = rt + ty;
+    const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
+    const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
+    const int ndh = (g.nd + 1) >> 1;
+    const double refx = tile_ref(it, g.nx), refy = tile_ref(rt, g.ny);
+    const float di = (float)(tx - refx), dr = (float)(ty - refy);
+    float2 t[4][4];   // [quad pixel][rotation]
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[q][k] = make_float2(0.f, 0.f);
+    for (int v0 = vbeg; v0 < vend; v0 += BP_CHUNK) {
+        const int nvc = min(BP_CHUNK, vend - v0);
+        __syncthreads();
+        for (int k = tid; k < nvc; k += BP_QUAD_THREADS) {
+            if (tvtab) {   // precomputed with the geometry
+                const long long tt = (long long)tile * g.nv + v0 + k;
+                const float4 u0 = __ldg(tvtab + 2 * tt), u1 = __ldg(tvtab + 2 * tt + 1);
+                TileViewS<float> T;
+                T.Dt = u0.x; T.yt = u0.y; T.a1 = u0.z; T.b1 = u0.w; T.rho = u1.x; T.phi = u1.y; T.hc = u1.z; T.hs = u1.w;
+                tv[k] = T;
+                tj[k] = __ldg(tjtab + tt);
+            } else {
+                tile_view_f32(g, view_cs[2 * (v0 + k)], view_cs[2 * (v0 + k) + 1], it + refx, rt + refy, tv[k],
+                              tj[k]);
+            }
+        }
+        __syncthreads();
+        if (!in0) continue;
+        for (int vv = 0; vv < nvc; ++vv) {
+            const int v = v0 + vv;
+            const TileViewS<float> T = tv[vv];
+            const int J = tj[vv];
+            const bool col = fabsf(T.b1) <= fabsf(T.a1);   // pairs along a column
+            const float *brow = box2 + 8 * (long long)v * ndh;
+            const float *yrow = y4 + 8 * (long long)v * ndh, *yorow = y4 + 8 * (long long)(nv4 + v) * ndh;
+            const float Dn0 = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
+            const float yp0 = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
+            const float nu0 = ARC ? fmaf(T.a1, di, T.b1 * dr) : fmaf(T.a1, di, fmaf(T.b1, dr, T.rho));
+            const float sDn = col ? -T.hs : -T.hc, syp = col ? T.hc : -T.hs, snu = col ? T.b1 : T.a1;   // pair step
+            const float oDn = col ? -T.hc : -T.hs, oyp = col ? -T.hs : T.hc, onu = col ? T.a1 : T.b1;   // other step
+            const BpPixel P0 = bp_pixel_f32<ARC>(T, Dn0, yp0, nu0, a);
+            BpPixel P1 = bp_pixel_f32<ARC>(T, Dn0 + sDn, yp0 + syp, nu0 + snu, a);
+            BpPixel P2 = bp_pixel_f32<ARC>(T, Dn0 + oDn, yp0 + oyp, nu0 + onu, a);
+            BpPixel P3 = bp_pixel_f32<ARC>(T, Dn0 + oDn + sDn, yp0 + oyp + syp, nu0 + onu + snu, a);
+            const bool inP1 = col ? in2 : in1, inP2 = col ? in1 : in2;
+            if (!inP1) P1.sig = P0.sig;
+            if (!inP2) P2.sig = P0.sig;
+            if (!in3) P3.sig = P0.sig;
+            const float hwc = bp_quad_hwc(T, Dn0, yp0, a);
+            if (col) {   // P1 is quad pixel 2, P2 quad pixel 1
+                bp_view2_rot4<ARC>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[2]);
+                bp_view2_rot4<ARC>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[1], t[3]);
+            } else {
+                bp_view2_rot4<ARC>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[1]);
+                bp_view2_rot4<ARC>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[2], t[3]);
+            }
+        }
+    }
+    if (in0) {
+        const long long nn = (long long)g.nx * g.ny;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int iq = i + (q & 1), rq = r + (q >> 1);
+            if (iq >= g.nx || rq >= g.ny) continue;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                partial[(4LL * blockIdx.y + k) * nn + (long long)rq * g.nx + iq] = (t[q][k].x + t[q][k].y) * a.h2q;
+        }
+    }
+}
+
+// img[n] = sum_k T_k(R^-k n), T_k the sum of partial[4 s + k] over the view parts s (in part
+// order), through four 32 x 32 shared-memory tiles: R^-1 (i, r) = (r, N-1-i),
+// R^-2 (i, r) = (N-1-i, N-1-r), R^-3 (i, r) = (N-1-r, i).
+__global__ void orbit_sum_kernel(const float *__restrict__ partial, float *__restrict__ img, int n, int nsplit)
+{
+    __shared__ float s[4][32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    const long long nn = (long long)n * n;
+    auto at = [&](int k, int row, int col) {
+        if (row < 0 || row >= n || col < 0 || col >= n) return 0.f;
+        const long long idx = (long long)row * n + col;
+        float v = partial[(long long)k * nn + idx];
+        for (int sp = 1; sp < nsplit; ++sp) v += partial[(4LL * sp + k) * nn + idx];
+        return v;
+    };
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        s[0][a][tx] = at(0, r0 + a, i0 + tx);                       // T_0 at (i, r)
+        s[1][a][tx] = at(1, n - i0 - 32 + a, r0 + tx);              // T_1 at (r, N-1-i)
+        s[2][a][tx] = at(2, n - r0 - 32 + a, n - i0 - 32 + tx);     // T_2 at (N-1-i, N-1-r)
+        s[3][a][tx] = at(3, i0 + a, n - r0 - 32 + tx);              // T_3 at (N-1-r, i)
+    }
+    __syncthreads();
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        if (i0 + tx < n && r0 + a < n)
+            img[(long long)(r0 + a) * n + i0 + tx] =
+                ((s[0][a][tx] + s[1][31 - tx][a]) + s[2][31 - a][31 - tx]) + s[3][tx][31 - a];
+    }
+}
+
 // FP64: same tiling and window; every per-pair constant is recomputed in FP64 from the view
 // and cell angles.
 __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double *__restrict__ view_cs,
@@ -385,7 +580,7 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
                                          : fabs(Dn * (g.ds * cg / g.dps) * (sig - jl));
                 // tau'/2 = depth along the cell's ray * dtan_j / 2
                 const double e = g.par ? 0.5 * g.tau : (cg * Dn + sg * yp) * 0.5 * dt;
-                const double w = window_diff(x, e, bc.p, bc.q * bc.iC, bc.iC, 0.5 * C);
+                const double w = window_diff(x, e, bc.q, bc.p * bc.iC, bc.iC, 0.5 * C);
                 part += yrow[j] * bc.nrm * (w / e);
             }
             acc += part;
@@ -394,9 +589,11 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
     if (inside) img[(b * g.ny + r) * g.nx + i] = acc;
 }
 
-// The sinogram as cell pairs of parity o: y2[b][v][m] = (y[b][v][2m + o], y[b][v][2m + o + 1]),
-// 0 for cells past n_det.
-__global__ void sino_pairs_kernel(const float *__restrict__ y, float2 *__restrict__ y2, long long nrows, int nd, int o)
+// The sinogram as weighted cell pairs of parity o: y2[b][v][m] = (w y[b][v][2m + o],
+// w' y[b][v][2m + o + 1]) with w = 2/B of that (view, cell) (the normalisation h^2/(2B) of
+// Eq. 18 without h^2/4), 0 for cells past n_det.
+__global__ void sino_pairs_kernel(const float *__restrict__ y, const BoxF *__restrict__ box, float2 *__restrict__ y2,
+                                  long long nrows, int nv, int nd, int o)
 {
     const int ndh = (nd + 1) >> 1;
     const long long n = nrows * ndh;
@@ -404,7 +601,11 @@ __global__ void sino_pairs_kernel(const float *__restrict__ y, float2 *__restric
         const long long row = t / ndh;
         const int j = 2 * (int)(t - row * ndh) + o;
         const float *yr = y + row * nd;
-        y2[t] = make_float2(j < nd ? yr[j] : 0.f, j + 1 < nd ? yr[j + 1] : 0.f);
+        const BoxF *br = box + (row % nv) * nd;
+        float2 v = make_float2(0.f, 0.f);
+        if (j < nd) v.x = yr[j] / (br[j].q - br[j].hC);
+        if (j + 1 < nd) v.y = yr[j + 1] / (br[j + 1].q - br[j + 1].hC);
+        y2[t] = v;
     }
 }
 
@@ -422,14 +623,63 @@ static int bp_view_parts(const cnsf_geometry *geo, int batch)
     return nsplit;
 }
 
+// View parts of the four-rotation gather (over the first quarter of the views).
+static int bp_view_parts_rot4(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geo->device);
+    const long long blocks = (long long)((g.nx + BP_T - 1) / BP_T) * ((g.ny + BP_T - 1) / BP_T);
+    int nsplit = 1;
+    while (nsplit < 32 && blocks * nsplit < 32LL * std::max(sms, 1) && (g.nv / 4) / (2 * nsplit) >= 8) nsplit *= 2;
+    return nsplit;
+}
+
+static size_t back_rot4_alloc_bytes(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    const size_t y4 = 2 * (size_t)(g.nv / 4) * ((g.nd + 1) / 2) * 8 * sizeof(float);
+    return y4 + (size_t)bp_view_parts_rot4(geo) * 4 * g.nx * g.ny * sizeof(float);
+}
+
+// FP32 back projection of one image by the four-rotation gather (geo->sym).
+static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *img, cudaStream_t st)
+{
+    const GeomConsts &g = geo->gc;
+    const int nv4 = g.nv / 4, ndh = (g.nd + 1) / 2, n = g.nx;
+    const int nsplit = bp_view_parts_rot4(geo);
+    const size_t ny4 = 2 * (size_t)nv4 * ndh * 8;
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, back_rot4_alloc_bytes(geo), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    float *y4 = reinterpret_cast<float *>(buf), *partial = y4 + ny4;
+    const long long npair = 2LL * nv4 * ndh;
+    sino_pairs_rot4_kernel<<<(unsigned)std::min<long long>((npair + 255) / 256, 8192), 256, 0, st>>>(
+        sino, geo->d_box, reinterpret_cast<float4 *>(y4), g.nv, g.nd);
+    const double dg = g.arc ? g.ds / g.dps : 0.0;
+    BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
+             (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0), 8LL * g.nv * ndh, 8 * ndh};
+    const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
+    auto kern = g.arc ? bp_rot4_f32_kernel<true> : bp_rot4_f32_kernel<false>;
+    kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_box2, geo->d_cell2, y4, a, geo->d_bp_order,
+                                                                 ntx, nsplit, partial, geo->d_view_cs, geo->d_tv,
+                                                                 geo->d_tj);
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    orbit_sum_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(partial, img, n, nsplit);
+    cudaFreeAsync(buf, st);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
 size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 {
     if (batch <= 0 || dtype != CNSF_F32) return 0;
     if (batch >= 2) return back_batch_alloc_bytes(geo);
+    if (geo->sym) return back_rot4_alloc_bytes(geo);
     const GeomConsts &g = geo->gc;
     const int nsplit = bp_view_parts(geo, batch);
     const size_t npair = (size_t)batch * g.nv * ((g.nd + 1) / 2);
-    // odd-aligned sinogram pairs, and the even-aligned copy whether or not the call's pointer needs it
+    // the weighted sinogram pairs in both alignments
     return (nsplit > 1 ? (size_t)nsplit * batch * g.nx * g.ny * sizeof(float) : 0) + 2 * npair * sizeof(float2);
 }
 
@@ -437,6 +687,7 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
 {
     if (batch == 0) return CNSF_OK;
     if (dtype == CNSF_F32 && batch >= 2) return launch_back_batch(geo, (const float *)sino, (float *)img, batch, st);
+    if (dtype == CNSF_F32 && geo->sym) return launch_back_rot4(geo, (const float *)sino, (float *)img, st);
     const GeomConsts &g = geo->gc;
     dim3 blk(BP_T, BP_T), grd((g.nx + BP_T - 1) / BP_T, (g.ny + BP_T - 1) / BP_T, batch);
     if (dtype == CNSF_F32) {
@@ -452,23 +703,19 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
             cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nimg * sizeof(float), st);
             if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
         }
-        // the sinogram as cell pairs: odd-aligned pairs from a copy; even-aligned pairs
-        // directly when n_det is even and the pointer 8-byte aligned, otherwise from a copy
-        const bool direct = (g.nd % 2 == 0) && (((uintptr_t)sino & 7u) == 0);
+        // the sinogram as weighted cell pairs in both alignments (copies: each value carries
+        // the 2/B of its view and cell)
         const long long nrows = (long long)batch * g.nv, npair = nrows * ((g.nd + 1) / 2);
         float2 *copy = nullptr;
-        cudaError_t e = cudaMallocAsync((void **)&copy, (size_t)(direct ? 1 : 2) * npair * sizeof(float2), st);
+        cudaError_t e = cudaMallocAsync((void **)&copy, (size_t)2 * npair * sizeof(float2), st);
         if (e != cudaSuccess) {
             if (partial) cudaFreeAsync(partial, st);
             return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
         }
         const unsigned pblocks = (unsigned)std::min<long long>((npair + 255) / 256, 8192);
-        sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, copy, nrows, g.nd, 1);
-        const float2 *y2 = reinterpret_cast<const float2 *>(sino);
-        if (!direct) {
-            sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, copy + npair, nrows, g.nd, 0);
-            y2 = copy + npair;
-        }
+        sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, geo->d_box, copy, nrows, g.nv, g.nd, 1);
+        sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, geo->d_box, copy + npair, nrows, g.nv, g.nd, 0);
+        const float2 *y2 = copy + npair;
         auto kern = g.arc ? bp_f32_kernel<true> : bp_f32_kernel<false>;
         kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_QUAD_THREADS), 0, st>>>(
             g, geo->d_view_cs, geo->d_box2, geo->d_cell2, y2, copy, (float *)img, a, geo->d_bp_order,

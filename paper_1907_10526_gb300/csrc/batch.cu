@@ -99,7 +99,7 @@ struct Acc {
 // wider than pixels).
 template <int KC, int NB4>
 __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__restrict__ base, int pitch4, float B,
-                                              float p, float qiC, float iC, float hC, Acc<NB4> &acc)
+                                              float q, float piC, float iC, float hC, Acc<NB4> &acc)
 {
     long long A = R.A0 + 0xFFFFFFFFLL;   // ceil-ready: high word = ceil(f - hw)
     float er = R.e0;
@@ -114,7 +114,7 @@ __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__res
         for (int m = 0; m < kc; ++m) {
             const float um = u0 + (float)m;
             const float e = fmaf(R.kap, um, er);
-            const float d = window_diff(fabsf(B * um), e, p, qiC, iC, hC);
+            const float d = window_diff(fabsf(B * um), e, q, piC, iC, hC);
             part.fma_from(d * rcp_approx(e), rp + m * NB4);
         }
         A += R.G;
@@ -132,7 +132,7 @@ __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__res
 template <int NB4>
 __device__ __forceinline__ void fp_batch_walk_lines(RayF R, int l0, int l1, const float4 *__restrict__ P,
                                                     const float4 *__restrict__ Tt, int pitchP, int pitchT, int pad,
-                                                    float B, float p, float qiC, float iC, float hC, Acc<NB4> &acc)
+                                                    float B, float q, float piC, float iC, float hC, Acc<NB4> &acc)
 {
     if (l1 <= l0) return;
     const int k = l0 - R.r0;
@@ -145,21 +145,21 @@ __device__ __forceinline__ void fp_batch_walk_lines(RayF R, int l0, int l1, cons
     const float4 *base = (tr ? Tt : P) + ((long long)R.r0 * pitch + pad) * NB4;
     const int p4 = pitch * NB4;
     switch (R.kc) {
-        case 1: fp_batch_walk<1, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        case 2: fp_batch_walk<2, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        case 3: fp_batch_walk<3, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        case 4: fp_batch_walk<4, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        case 5: fp_batch_walk<5, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        case 6: fp_batch_walk<6, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        case 7: fp_batch_walk<7, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        case 8: fp_batch_walk<8, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
-        default: fp_batch_walk<0, NB4>(R, base, p4, B, p, qiC, iC, hC, acc); break;
+        case 1: fp_batch_walk<1, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 2: fp_batch_walk<2, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 3: fp_batch_walk<3, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 4: fp_batch_walk<4, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 5: fp_batch_walk<5, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 6: fp_batch_walk<6, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 7: fp_batch_walk<7, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 8: fp_batch_walk<8, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        default: fp_batch_walk<0, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
     }
 }
 
-// Trapezoid constants of one ray (Eq. 16 widths): p, q/C, 1/C, C/2 and B = 2(p + C/2).
+// Trapezoid constants of one ray (Eq. 16 widths): q, p/C, 1/C, C/2 and B = 2(q - C/2).
 struct RayBox {
-    float p, qiC, iC, hC, B;
+    float q, piC, iC, hC, B;
 };
 
 // Two adjacent rays of one view (cells j, j + 1) walking the same line family, over the
@@ -191,8 +191,8 @@ __device__ __forceinline__ void fp_batch_walk_joint(const RayF &Ra, const RayF &
             for (int k = 0; k < NB4; ++k) v[k] = __ldg(base + (long long)c * NB4 + k);
             const float ua = ua0 + (float)(c - ia), ub = ub0 + (float)(c - ib);
             const float ea = fmaf(Ra.kap, ua, era), eb = fmaf(Rb.kap, ub, erb);
-            const float da = window_diff(fabsf(Xa.B * ua), ea, Xa.p, Xa.qiC, Xa.iC, Xa.hC);
-            const float db = window_diff(fabsf(Xb.B * ub), eb, Xb.p, Xb.qiC, Xb.iC, Xb.hC);
+            const float da = window_diff(fabsf(Xa.B * ua), ea, Xa.q, Xa.piC, Xa.iC, Xa.hC);
+            const float db = window_diff(fabsf(Xb.B * ub), eb, Xb.q, Xb.piC, Xb.iC, Xb.hC);
             parta.fma_with(da * rcp_approx(ea), v);
             partb.fma_with(db * rcp_approx(eb), v);
         }
@@ -234,9 +234,9 @@ __global__ void __launch_bounds__(64) fp_batch_kernel(const int *__restrict__ or
     for (int s = 0; s < 2; ++s) {
         R[s] = rays[s == 0 || !has1 ? q : q + 1];
         const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + (s == 0 || !has1 ? q : q + 1)));
-        X[s].p = bx.x; X[s].qiC = bx.y; X[s].iC = bx.z; X[s].hC = bx.w;
-        X[s].B = 2.f * (bx.x + bx.w);
-        if (R[s].nrows > 0) tighten_window(R[s], X[s].p, X[s].hC, X[s].B);
+        X[s].q = bx.x; X[s].piC = bx.y; X[s].iC = bx.z; X[s].hC = bx.w;
+        X[s].B = 2.f * (bx.x - bx.w);
+        if (R[s].nrows > 0) tighten_window(R[s], X[s].q, X[s].B);
         acc[s].zero();
     }
     const int la0 = R[0].r0, la1 = R[0].r0 + max(R[0].nrows, 0);
@@ -246,13 +246,13 @@ __global__ void __launch_bounds__(64) fp_batch_kernel(const int *__restrict__ or
                        (R[0].flags & 1) == (R[1].flags & 1) && j0 < j1;
     if (joint) {
         // each ray alone before and after the common lines, then both together
-        fp_batch_walk_lines<NB4>(R[0], la0, j0, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].p, X[0].qiC, X[0].iC,
+        fp_batch_walk_lines<NB4>(R[0], la0, j0, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].q, X[0].piC, X[0].iC,
                                  X[0].hC, acc[0]);
-        fp_batch_walk_lines<NB4>(R[0], j1, la1, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].p, X[0].qiC, X[0].iC,
+        fp_batch_walk_lines<NB4>(R[0], j1, la1, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].q, X[0].piC, X[0].iC,
                                  X[0].hC, acc[0]);
-        fp_batch_walk_lines<NB4>(R[1], lb0, j0, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].p, X[1].qiC, X[1].iC,
+        fp_batch_walk_lines<NB4>(R[1], lb0, j0, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].q, X[1].piC, X[1].iC,
                                  X[1].hC, acc[1]);
-        fp_batch_walk_lines<NB4>(R[1], j1, lb1, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].p, X[1].qiC, X[1].iC,
+        fp_batch_walk_lines<NB4>(R[1], j1, lb1, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].q, X[1].piC, X[1].iC,
                                  X[1].hC, acc[1]);
         const bool tr = (R[0].flags & 1) != 0;
         const int pitch = tr ? pitchT : pitchP;
@@ -263,12 +263,12 @@ __global__ void __launch_bounds__(64) fp_batch_kernel(const int *__restrict__ or
         for (int s = 0; s < 2; ++s)
             if ((s == 0 || has1) && R[s].nrows > 0)
                 fp_batch_walk_lines<NB4>(R[s], R[s].r0, R[s].r0 + R[s].nrows, P, Tt, pitchP, pitchT, pad, X[s].B,
-                                         X[s].p, X[s].qiC, X[s].iC, X[s].hC, acc[s]);
+                                         X[s].q, X[s].piC, X[s].iC, X[s].hC, acc[s]);
     }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         if (s == 1 && !has1) break;
-        const float nrm = R[s].nrows > 0 ? h2q / (X[s].p + X[s].hC) : 0.f;
+        const float nrm = R[s].nrows > 0 ? h2q / (X[s].q - X[s].hC) : 0.f;
         const float *a = reinterpret_cast<const float *>(acc[s].v);
 #pragma unroll
         for (int k = 0; k < 4 * NB4; ++k)
@@ -373,8 +373,8 @@ __global__ void __launch_bounds__(BPB_THREADS) bp_batch_kernel(GeomConsts g, con
                 const float e0 = fmaf(Dn0, C.y, yp0 * C.z), e1 = fmaf(Dn1, C.y, yp1 * C.z);
                 const float w0 = window_diff(x0, e0, A.x, A.y, A.z, A.w);
                 const float w1 = window_diff(x1, e1, A.x, A.y, A.z, A.w);
-                part0.fma_with(w0 * rcp_approx((A.x + A.w) * e0), yv);
-                part1.fma_with(w1 * rcp_approx((A.x + A.w) * e1), yv);
+                part0.fma_with(w0 * rcp_approx((A.x - A.w) * e0), yv);   // (B/2) tau'/2
+                part1.fma_with(w1 * rcp_approx((A.x - A.w) * e1), yv);
                 d0 -= 1.f;
                 d1 -= 1.f;
             }

@@ -72,6 +72,14 @@ void cnsf_geometry_destroy(cnsf_geometry *geom)
     }
 }
 
+int cnsf_geometry_paths(const cnsf_geometry *geom, int32_t *symmetric, int32_t *exact_differences)
+{
+    if (!geom) return CNSF_ERR_INVALID;
+    if (symmetric) *symmetric = geom->sym;
+    if (exact_differences) *exact_differences = geom->exact;
+    return CNSF_OK;
+}
+
 int cnsf_geometry_shape(const cnsf_geometry *geom, int32_t *n_x, int32_t *n_y, int32_t *n_views, int32_t *n_det)
 {
     if (!geom) return CNSF_ERR_INVALID;

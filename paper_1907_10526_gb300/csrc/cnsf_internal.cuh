@@ -234,10 +234,10 @@ static_assert(sizeof(RayF) == 48, "RayF layout");
 // |u| < ((B + C)/2 + e_max)/(B - |kap|): shrink the window to that (when narrower), moving
 // its fixed-point start by the same amount, and walk fewer candidates per line.
 #ifdef __CUDACC__
-__device__ __forceinline__ void tighten_window(RayF &R, float p, float hC, float B)
+__device__ __forceinline__ void tighten_window(RayF &R, float q, float B)
 {
     const float emax = fmaxf(R.e0, fmaf((float)(R.nrows - 1), R.de, R.e0));
-    const float hw = (p + 2.f * hC + emax) / (B - fabsf(R.kap)) + 1e-3f;
+    const float hw = (q + emax) / (B - fabsf(R.kap)) + 1e-3f;
     if (hw < R.hw) {
         const long long D = __float2ll_rz((R.hw - hw) * 4294967296.0f);   // >= 0, in 32.32 units
         R.A0 += D;
@@ -248,10 +248,11 @@ __device__ __forceinline__ void tighten_window(RayF &R, float p, float hC, float
 #endif
 
 // Per-(view, cell) trapezoid constants of the FP32 kernels: box_B * box_C (Eq. 16 widths)
-// as p = (B - C)/2, q/C, 1/C (clamped for C = 0) and C/2.  B = 2(p + C/2); the
-// normalisation of Eq. (18) with the pixel area is h^2/(2B).
+// as its outer half-width q = (B + C)/2, p/C with p = (B - C)/2 the plateau half-width,
+// 1/C (clamped for C = 0) and C/2.  B = 2(q - C/2); the normalisation of Eq. (18) with the
+// pixel area is h^2/(2B).
 struct alignas(16) BoxF {
-    float p, qiC, iC, hC;
+    float q, piC, iC, hC;
 };
 
 // Per-cell constants of the FP32 back projector: s' = D_n g1 (sigma - j) and
@@ -264,11 +265,11 @@ struct alignas(16) CellF {
 // 2m + o + 1 side by side, so the two cells' values come as FP32 pairs for the packed
 // (FFMA2) arithmetic, and a window can start its pairs at any cell.  A cell past n_det
 // repeats the last cell's constants (its sinogram value is 0).  Each entry is 32 bytes,
-// read with one 256-bit load: per (parity, view, pair) the
-// trapezoid constants (p, 2/B, 1/C, -C/2 of both cells; q/C = p/C + 1 is formed in the
-// kernel), per (parity, pair) the view-independent
-// cell slopes (ds/L_j, cos(g_j) dtan_j/2, sin(g_j) dtan_j/2 of both cells), a table of a
-// few KB that stays in L1 across views.
+// read with one 256-bit load: per (parity, view, pair) the trapezoid constants (q, p/C,
+// 1/C, -C/2 of both cells), per (parity, pair) the view-independent cell slopes (ds/L_j,
+// cos(g_j) dtan_j/2, sin(g_j) dtan_j/2 of both cells), a table of a few KB that stays in
+// L1 across views.  The normalisation 2/B of each (view, cell) is applied to the sinogram
+// value when the call builds its cell pairs.
 
 // Back-projector cell window (cells) of a pixel at depth D_n, coordinate y' along w:
 //   hwc = kz * h(|y' c - D_n s| + |y' s + D_n c|) / D_n^2 * (1.02 + 2 h / D_n) + ke
@@ -287,16 +288,19 @@ struct cnsf_geometry {
     int device;
     int pad;                  // zero columns on each side of the padded image copies
     int kc_max;               // largest candidate count per walked line
+    int sym;                  // 1: FP32 single-image projections reuse entries over the quarter turn
+    int exact;                // 1: FP32 kernels form window differences piece by piece
     cnsf::BpWindow bw;        // back projector cell window
     // device tables
     double *d_view_cs;        // [nv][2] cos, sin (FP64)
     double *d_cell_d;         // [nd][4] sin(g_j), cos(g_j), dtan_j, s_j (FP64; parallel: 0, 1, 0, s_j)
     cnsf::BoxF *d_box;        // [nv][nd]
     cnsf::CellF *d_cellf;     // [nd]
-    float *d_box2;            // [2][nv][ceil(n_det/2)][8]: p, 2/B, 1/C, -C/2 of cells 2m + o, 2m + o + 1
+    float *d_box2;            // [2][nv][ceil(n_det/2)][8]: q, p/C, 1/C, -C/2 of cells 2m + o, 2m + o + 1
     float *d_cell2;           // [2][ceil(n_det/2)][8]: ds/L, c1, c2 of cells 2m + o, 2m + o + 1, 0, 0
     // launch orders, heaviest blocks first (so that the tail of the grid is short work)
     int *d_fp_order;          // [ceil(nv*nd/128)] forward blocks of 128 rays
+    int *d_fp_order4;         // [ceil(nv/4*nd/128)] the same over the rays of views < nv/4 (sym only)
     int *d_bp_order;          // [ceil(nx/16)*ceil(ny/16)] back-projection tiles
     float4 *d_tv;             // [tiles][nv][2] FP32 back-projection tile coefficients (when <= 1 GiB), or null
     int *d_tj;                // [tiles][nv] their integer cell offsets

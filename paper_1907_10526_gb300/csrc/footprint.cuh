@@ -5,15 +5,17 @@
 // M_[B, C, 2e](s') = box_B * box_C * box_2e (Sec. III.A).  It is evaluated as the window
 // average of the trapezoid T = box_B * box_C:
 //
-//   M(x) = (G(x + e) - G(x - e)) / (2e),   G(y) = 1/2 + sgn(y) H(|y|),  H' = T,
-//   B H(z) = min(z, p) + C/2 - (C/2) v(z)^2,   v(z) = sat((q - z)/C),
+//   M(x) = (G(x + e) - G(x - e)) / (2e),   G(y) = sgn(y) H(|y|),  H' = T,  H(0) = 0,
+//   B H(z) = min(z, q) - (C/2) r(z)^2,   r(z) = sat((z - p)/C),
 //
-// with p = (B - C)/2, q = (B + C)/2.  The C/(2C) ramps carry their own factor C, so
-// no step divides a difference by a small width: the 1/(zeta1 zeta2 tau') of the
-// literal divided-difference form of Eq. (18) never appears, and C = 0 (axis-aligned
-// rays, M_0 = delta) needs no branch (v is then 0 or 1).  The one remaining difference
-// G(x + e) - G(x - e) ~ 2e T(x) loses about log2(B / 2e) bits (a few at the blur widths
-// of fan-beam CT).  window_diff returns B * 2e * M(x) for x = |s'|.
+// with p = (B - C)/2, q = (B + C)/2 (the plateau and outer half-widths).  B H is the
+// identity on the plateau, bends over the ramp and is B/2 beyond q.  The ramp term carries
+// its own factor C, so no step divides a difference by a small width: the
+// 1/(zeta1 zeta2 tau') of the literal divided-difference form of Eq. (18) never appears,
+// and C = 0 (axis-aligned rays, M_0 = delta) needs no branch (r is then 0 or 1).  The one
+// remaining difference G(x + e) - G(x - e) ~ 2e T(x) loses about log2(B / 2e) bits (a few
+// at the blur widths of fan-beam CT; window_diff_exact below has no such loss).
+// window_diff returns B * 2e * M(x) for x = |s'| from the constants q, p/C, 1/C and C/2.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,18 +26,16 @@ __device__ __forceinline__ float sat01(float x) { return __saturatef(x); }
 __device__ __forceinline__ double sat01(double x) { return fmin(fmax(x, 0.0), 1.0); }
 
 template <typename T>
-__device__ __forceinline__ T window_diff(T x, T e, T p, T qiC, T iC, T hC)
+__device__ __forceinline__ T window_diff(T x, T e, T q, T piC, T iC, T hC)
 {
     T z1 = x + e;                 // >= 0
     T z0 = x - e;                 // either sign
     T a0 = fabs(z0);
-    T m1 = fmin(z1, p);
-    T m0 = fmin(a0, p);
-    T v1 = sat01(fma(-z1, iC, qiC));
-    T v0 = sat01(fma(-a0, iC, qiC));
-    T h1 = fma(-hC * v1, v1, m1);          // B H(z1) - C/2
-    T h0 = fma(-hC * v0, v0, m0) + hC;     // B H(|z0|)
-    return (h1 + hC) - copysign(h0, z0);
+    T r1 = sat01(fma(z1, iC, -piC));
+    T r0 = sat01(fma(a0, iC, -piC));
+    T h1 = fma(-hC * r1, r1, fmin(z1, q));   // B H(z1)
+    T h0 = fma(-hC * r0, r0, fmin(a0, q));   // B H(|z0|)
+    return h1 - copysign(h0, z0);
 }
 
 // 1/x by the hardware approximation (max error ~1 ulp); x is a blur half-width or a
@@ -68,42 +68,36 @@ __device__ __forceinline__ void ldg256(const float *p, float (&r)[8])
 
 // Two entries at once with the packed FP32 instructions of sm_100+ (FADD2/FMUL2/FFMA2):
 // the same arithmetic as window_diff, lane by lane, for candidates that share the
-// trapezoid constants (p, q/C, 1/C, C/2 given as pairs).  min, saturate and sign
-// handling have no packed form and stay scalar.
-__device__ __forceinline__ float2 window_diff2(float2 x, float2 e, float2 ne1, float p, float qiC, float iC,
-                                               float2 hC2, float2 nhC2)
+// trapezoid constants (q, p/C, 1/C given as scalars, -C/2 as a pair).  min, saturate and
+// sign handling have no packed form and stay scalar.
+__device__ __forceinline__ float2 window_diff2(float2 x, float2 e, float2 ne1, float q, float piC, float iC,
+                                               float2 nhC2)
 {
     const float2 z1 = __fadd2_rn(x, e);
     const float2 z0 = __ffma2_rn(e, ne1, x);          // x - e
     const float a0x = fabsf(z0.x), a0y = fabsf(z0.y);
-    const float2 m1 = make_float2(fminf(z1.x, p), fminf(z1.y, p));
-    const float2 m0 = make_float2(fminf(a0x, p), fminf(a0y, p));
-    const float2 v1 = make_float2(sat01(fmaf(-z1.x, iC, qiC)), sat01(fmaf(-z1.y, iC, qiC)));
-    const float2 v0 = make_float2(sat01(fmaf(-a0x, iC, qiC)), sat01(fmaf(-a0y, iC, qiC)));
-    const float2 t1 = __ffma2_rn(__fmul2_rn(nhC2, v1), v1, m1);   // B H(z1) - C/2
-    const float2 t0 = __ffma2_rn(__fmul2_rn(nhC2, v0), v0, m0);
-    const float2 h0 = __fadd2_rn(t0, hC2);                      // B H(|z0|)
+    const float2 r1 = make_float2(sat01(fmaf(z1.x, iC, -piC)), sat01(fmaf(z1.y, iC, -piC)));
+    const float2 r0 = make_float2(sat01(fmaf(a0x, iC, -piC)), sat01(fmaf(a0y, iC, -piC)));
+    const float2 h1 = __ffma2_rn(__fmul2_rn(nhC2, r1), r1, make_float2(fminf(z1.x, q), fminf(z1.y, q)));
+    const float2 h0 = __ffma2_rn(__fmul2_rn(nhC2, r0), r0, make_float2(fminf(a0x, q), fminf(a0y, q)));
     const float2 cs = make_float2(copysignf(h0.x, z0.x), copysignf(h0.y, z0.y));
-    return __ffma2_rn(cs, ne1, __fadd2_rn(t1, hC2));             // (t1 + C/2) - sgn(z0) h0
+    return __ffma2_rn(cs, ne1, h1);                   // B H(z1) - sgn(z0) B H(|z0|)
 }
 
-// Two entries with different trapezoid constants (cells j and j + 1), packed: p, qiC, iC
+// Two entries with different trapezoid constants (cells j and j + 1), packed: q, p/C, 1/C
 // and nhC = -C/2 are pairs.  Same arithmetic as window_diff, lane by lane.
-__device__ __forceinline__ float2 window_diff2p(float2 x, float2 e, float2 ne1, float2 p, float2 qiC, float2 iC,
+__device__ __forceinline__ float2 window_diff2p(float2 x, float2 e, float2 ne1, float2 q, float2 piC, float2 iC,
                                                 float2 nhC)
 {
     const float2 z1 = __fadd2_rn(x, e);
     const float2 z0 = __ffma2_rn(e, ne1, x);          // x - e
     const float a0x = fabsf(z0.x), a0y = fabsf(z0.y);
-    const float2 m1 = make_float2(fminf(z1.x, p.x), fminf(z1.y, p.y));
-    const float2 m0 = make_float2(fminf(a0x, p.x), fminf(a0y, p.y));
-    const float2 v1 = make_float2(sat01(fmaf(-z1.x, iC.x, qiC.x)), sat01(fmaf(-z1.y, iC.y, qiC.y)));
-    const float2 v0 = make_float2(sat01(fmaf(-a0x, iC.x, qiC.x)), sat01(fmaf(-a0y, iC.y, qiC.y)));
-    const float2 t1 = __ffma2_rn(__fmul2_rn(nhC, v1), v1, m1);   // B H(z1) - C/2
-    const float2 t0 = __ffma2_rn(__fmul2_rn(nhC, v0), v0, m0);
-    const float2 h0 = __ffma2_rn(nhC, ne1, t0);                 // B H(|z0|)
+    const float2 r1 = make_float2(sat01(fmaf(z1.x, iC.x, -piC.x)), sat01(fmaf(z1.y, iC.y, -piC.y)));
+    const float2 r0 = make_float2(sat01(fmaf(a0x, iC.x, -piC.x)), sat01(fmaf(a0y, iC.y, -piC.y)));
+    const float2 h1 = __ffma2_rn(__fmul2_rn(nhC, r1), r1, make_float2(fminf(z1.x, q.x), fminf(z1.y, q.y)));
+    const float2 h0 = __ffma2_rn(__fmul2_rn(nhC, r0), r0, make_float2(fminf(a0x, q.x), fminf(a0y, q.y)));
     const float2 cs = make_float2(copysignf(h0.x, z0.x), copysignf(h0.y, z0.y));
-    return __ffma2_rn(cs, ne1, __ffma2_rn(nhC, ne1, t1));       // (t1 + C/2) - sgn(z0) h0
+    return __ffma2_rn(cs, ne1, h1);
 }
 
 }  // namespace cnsf

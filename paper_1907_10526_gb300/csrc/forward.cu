@@ -59,7 +59,7 @@ __global__ void pad_transpose_kernel(const T *__restrict__ img, T *__restrict__ 
 // (ia - f) of the first candidate.
 template <int KC, bool COUNT>
 __device__ __forceinline__ float line_sum(const float *__restrict__ rp, float u, float er, float kap,
-                                          float B, float p, float qiC, float iC, float hC)
+                                          float B, float q, float piC, float iC, float hC)
 {
     float s = 0.f;
 #pragma unroll
@@ -70,9 +70,9 @@ __device__ __forceinline__ float line_sum(const float *__restrict__ rp, float u,
         float c = __ldg(rp + m);
         if (COUNT) {
             // strictly inside the support |s'| < (B + C + tau')/2 of M_[B,C,tau']
-            s += (x < p + 2.f * hC + e) ? c : 0.f;
+            s += (x < q + e) ? c : 0.f;
         } else {
-            float d = window_diff(x, e, p, qiC, iC, hC);
+            float d = window_diff(x, e, q, piC, iC, hC);
             s = fmaf(c, d * rcp_approx(e), s);
         }
     }
@@ -85,7 +85,7 @@ __device__ __forceinline__ float line_sum(const float *__restrict__ rp, float u,
 template <int KC>
 __device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, const float *__restrict__ rp1,
                                                 float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1,
-                                                float p, float qiC, float iC, float2 hC2, float2 nhC2)
+                                                float q, float piC, float iC, float2 nhC2)
 {
     float2 s = make_float2(0.f, 0.f);
     // B u and tau'/2 grow by B and kap per candidate
@@ -93,7 +93,7 @@ __device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, c
 #pragma unroll
     for (int m = 0; m < KC; ++m) {
         const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));
-        const float2 d = window_diff2(x, e, ne1, p, qiC, iC, hC2, nhC2);
+        const float2 d = window_diff2(x, e, ne1, q, piC, iC, nhC2);
         const float2 w = __fmul2_rn(d, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
         const float2 c = make_float2(__ldg(rp0 + m), __ldg(rp1 + m));
         s = __ffma2_rn(c, w, s);
@@ -116,14 +116,14 @@ __device__ __forceinline__ void fx_window(long long Bc, int &ilo, float &rho)
 
 template <int KC>
 __device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ base, int pitch, float B,
-                                       float p, float qiC, float iC, float hC)
+                                       float q, float piC, float iC, float hC)
 {
     long long A = R.A0 + 0xFFFFFFFFLL;   // ceil-ready walk state (fx_window)
     const long long G = R.G;
     float2 er2 = make_float2(R.e0, R.e0 + R.de);
     const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);
     const float2 B2 = make_float2(B, B), ne1 = make_float2(-1.0f, -1.0f);
-    const float2 hC2 = make_float2(hC, hC), nhC2 = make_float2(-hC, -hC);
+    const float2 nhC2 = make_float2(-hC, -hC);
     const float hw = R.hw;
     float2 acc = make_float2(0.f, 0.f), part = make_float2(0.f, 0.f);
     int rr = 0;
@@ -133,8 +133,8 @@ __device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ 
         fx_window(A, ilo0, rho0);
         fx_window(A + G, ilo1, rho1);
         const float2 u = make_float2(rho0 - hw, rho1 - hw);
-        part = __fadd2_rn(part, line_pair_sum<KC>(base + ilo0, base + pitch + ilo1, u, er2, kap2, B2, ne1, p,
-                                                  qiC, iC, hC2, nhC2));
+        part = __fadd2_rn(part, line_pair_sum<KC>(base + ilo0, base + pitch + ilo1, u, er2, kap2, B2, ne1, q,
+                                                  piC, iC, nhC2));
         A += 2 * G;
         er2 = __fadd2_rn(er2, de2);
         base += 2 * pitch;
@@ -149,14 +149,14 @@ __device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ 
         int ilo;
         float rho;
         fx_window(A, ilo, rho);
-        tot += line_sum<KC, false>(base + ilo, rho - hw, er2.x, R.kap, B, p, qiC, iC, hC);
+        tot += line_sum<KC, false>(base + ilo, rho - hw, er2.x, R.kap, B, q, piC, iC, hC);
     }
     return tot;
 }
 
 template <int KC, bool COUNT>
 __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ base, int pitch, float B,
-                                      float p, float qiC, float iC, float hC)
+                                      float q, float piC, float iC, float hC)
 {
     long long A = R.A0;
     float er = R.e0;
@@ -168,7 +168,7 @@ __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ b
         int ilo = (int)(A >> 32) + (((unsigned)A) != 0u ? 1 : 0);
         unsigned nl = 0u - (unsigned)A;
         float rho = __uint_as_float(0x3f800000u | (nl >> 9)) - 1.0f;
-        part += line_sum<KC, COUNT>(base + ilo, rho - hw, er, kap, B, p, qiC, iC, hC);
+        part += line_sum<KC, COUNT>(base + ilo, rho - hw, er, kap, B, q, piC, iC, hC);
         A += G;
         er += de;
         base += pitch;
@@ -205,30 +205,30 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
     float acc = 0.f;
     if (R.nrows > 0) {
         const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
-        const float p = bx.x, qiC = bx.y, iC = bx.z, hC = bx.w;
-        const float B = 2.f * (p + hC);
-        tighten_window(R, p, hC, B);
+        const float qw = bx.x, piC = bx.y, iC = bx.z, hC = bx.w;
+        const float B = 2.f * (qw - hC);
+        tighten_window(R, qw, B);
         const bool tr = (R.flags & 1) != 0;
         const int pitch = tr ? pitchT : pitchP;
         const float *base = (tr ? imgT + b * strideT : imgP + b * strideP) + pad + (long long)R.r0 * pitch;
         const int kcase = COUNT ? R.kc : 100 + R.kc;
         switch (kcase) {
-            case 1: acc = walk<1, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 2: acc = walk<2, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 3: acc = walk<3, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 4: acc = walk<4, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 5: acc = walk<5, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 6: acc = walk<6, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 7: acc = walk<7, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 8: acc = walk<8, COUNT>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 101: acc = walk2<1>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 102: acc = walk2<2>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 103: acc = walk2<3>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 104: acc = walk2<4>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 105: acc = walk2<5>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 106: acc = walk2<6>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 107: acc = walk2<7>(R, base, pitch, B, p, qiC, iC, hC); break;
-            case 108: acc = walk2<8>(R, base, pitch, B, p, qiC, iC, hC); break;
+            case 1: acc = walk<1, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 2: acc = walk<2, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 3: acc = walk<3, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 4: acc = walk<4, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 5: acc = walk<5, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 6: acc = walk<6, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 7: acc = walk<7, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 8: acc = walk<8, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 101: acc = walk2<1>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 102: acc = walk2<2>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 103: acc = walk2<3>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 104: acc = walk2<4>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 105: acc = walk2<5>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 106: acc = walk2<6>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 107: acc = walk2<7>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 108: acc = walk2<8>(R, base, pitch, B, qw, piC, iC, hC); break;
             default: {
                 // wide windows (cells much wider than pixels): generic loop
                 long long A = R.A0;
@@ -242,9 +242,9 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
                         float x = fabsf(B * u);
                         float c = __ldg(base + ilo + m);
                         if (COUNT)
-                            acc += (x < p + 2.f * hC + e) ? c : 0.f;
+                            acc += (x < qw + e) ? c : 0.f;
                         else
-                            acc += c * window_diff(x, e, p, qiC, iC, hC) * rcp_approx(e);
+                            acc += c * window_diff(x, e, qw, piC, iC, hC) * rcp_approx(e);
                     }
                     A += R.G;
                     er += R.de;
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
                 }
             }
         }
-        if (!COUNT) acc *= h2q / (p + hC);   // h^2/(2B), B = 2(p + C/2)
+        if (!COUNT) acc *= h2q / (qw - hC);   // h^2/(2B), B = 2(q - C/2)
     }
     if (nsplit > 1)
         partial[((long long)blockIdx.z * gridDim.y + b) * nr + q] = acc;
@@ -268,6 +268,188 @@ __global__ void fp_sum_parts_kernel(const float *__restrict__ partial, float *__
         for (int k = 1; k < nsplit; ++k) s += partial[k * n + t];
         sino[t] = s;
     }
+}
+
+// ------------------------------------------------------------------ FP32 walk, four rotations
+// A square image centred on the rotation axis, with views closed under a quarter turn
+// (theta_{v + V/4} = theta_v + pi/2): the acquisition of view v + kV/4 is that of view v
+// turned by k quarter turns (source, detector and cells alike, Sec. II.A), and a quarter
+// turn maps the pixel lattice onto itself, pixel (i, r) to R(i, r) = (N-1-r, i), with the
+// square pixel basis unchanged (the widths of Eq. 16 swap roles).  So every entry of Eq. (18)
+// satisfies a(v + kV/4, j, n) = a(v, j, R^-k n), and
+//     y[v + kV/4][j] = sum_m a(v, j, m) c[R^k m].
+// One thread per ray of the first quarter of the views evaluates each entry once and applies
+// it to the four values c4[m] = (c[m], c[Rm], c[R^2 m], c[R^3 m]) of an interleaved copy of
+// the image, producing the four sinogram values at once.
+
+// c4 in both zero-padded layouts (rows: P4[r][pad + i]; transposed: T4[i][pad + r]), through
+// four 32 x 32 shared-memory tiles of the image (the rotated reads stay coalesced).
+__global__ void pad_rot4_kernel(const float *__restrict__ img, float4 *__restrict__ P4, float4 *__restrict__ T4, int n,
+                                int pad, int pitch)
+{
+    __shared__ float s[4][32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    auto at = [&](int row, int col) { return (row >= 0 && row < n && col >= 0 && col < n) ? img[(long long)row * n + col] : 0.f; };
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        s[0][a][tx] = at(r0 + a, i0 + tx);                      // c[m]       = img[r][i]
+        s[1][a][tx] = at(i0 + a, n - r0 - 32 + tx);             // c[R m]     = img[i][n-1-r]
+        s[2][a][tx] = at(n - r0 - 32 + a, n - i0 - 32 + tx);    // c[R^2 m]   = img[n-1-r][n-1-i]
+        s[3][a][tx] = at(n - i0 - 32 + a, r0 + tx);             // c[R^3 m]   = img[n-1-i][r]
+    }
+    __syncthreads();
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        // rows layout: pixel (i0 + tx, r0 + a)
+        if (i0 + tx < n && r0 + a < n)
+            P4[(long long)(r0 + a) * pitch + pad + i0 + tx] =
+                make_float4(s[0][a][tx], s[1][tx][31 - a], s[2][31 - a][31 - tx], s[3][31 - tx][a]);
+        // transposed layout: pixel (i0 + a, r0 + tx)
+        if (i0 + a < n && r0 + tx < n)
+            T4[(long long)(i0 + a) * pitch + pad + r0 + tx] =
+                make_float4(s[0][tx][a], s[1][a][31 - tx], s[2][31 - tx][31 - a], s[3][31 - a][tx]);
+    }
+    // the zero margins of the rows (and transposed rows) of this tile
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int tid = threadIdx.y * 32 + tx, nt = 32 * blockDim.y;
+    if (blockIdx.x == 0 || blockIdx.x == gridDim.x - 1)
+        for (int t = tid; t < 32 * pad; t += nt) {
+            const int a = t / pad, c = t - a * pad;
+            if (r0 + a >= n) continue;
+            if (blockIdx.x == 0) P4[(long long)(r0 + a) * pitch + c] = z;
+            if (blockIdx.x == gridDim.x - 1) P4[(long long)(r0 + a) * pitch + pad + n + c] = z;
+        }
+    if (blockIdx.y == 0 || blockIdx.y == gridDim.y - 1)
+        for (int t = tid; t < 32 * pad; t += nt) {
+            const int a = t / pad, c = t - a * pad;
+            if (i0 + a >= n) continue;
+            if (blockIdx.y == 0) T4[(long long)(i0 + a) * pitch + c] = z;
+            if (blockIdx.y == gridDim.y - 1) T4[(long long)(i0 + a) * pitch + pad + n + c] = z;
+        }
+}
+
+// The candidates of two consecutive lines, packed as in line_pair_sum, each entry applied to
+// the four rotated values of its pixel; s[k] accumulates rotation k (lanes: the two lines).
+// KC = 0: kc candidates (wide cells).
+template <int KC>
+__device__ __forceinline__ void line_pair_sum_rot4(const float4 *__restrict__ rp0, const float4 *__restrict__ rp1,
+                                                   int kc, float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1,
+                                                   float q, float piC, float iC, float2 nhC2, float2 (&s)[4])
+{
+    float2 xs = __fmul2_rn(B2, u), e = __ffma2_rn(kap2, u, er2);
+#pragma unroll
+    for (int m = 0; m < (KC > 0 ? KC : kc); ++m) {
+        const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));
+        const float2 d = window_diff2(x, e, ne1, q, piC, iC, nhC2);
+        const float2 w = __fmul2_rn(d, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
+        const float4 c0 = __ldg(rp0 + m), c1 = __ldg(rp1 + m);
+        s[0] = __ffma2_rn(make_float2(c0.x, c1.x), w, s[0]);
+        s[1] = __ffma2_rn(make_float2(c0.y, c1.y), w, s[1]);
+        s[2] = __ffma2_rn(make_float2(c0.z, c1.z), w, s[2]);
+        s[3] = __ffma2_rn(make_float2(c0.w, c1.w), w, s[3]);
+        xs = __fadd2_rn(xs, B2);
+        e = __fadd2_rn(e, kap2);
+    }
+}
+
+// walk2 for the four rotations: two lines per packed step, blocked sums of 16 lines.
+template <int KC>
+__device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restrict__ base, int pitch, float B,
+                                           float q, float piC, float iC, float hC, float (&out)[4])
+{
+    long long A = R.A0 + 0xFFFFFFFFLL;   // ceil-ready walk state (fx_window)
+    const long long G = R.G;
+    const int kc = KC > 0 ? KC : R.kc;
+    float2 er2 = make_float2(R.e0, R.e0 + R.de);
+    const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);
+    const float2 B2 = make_float2(B, B), ne1 = make_float2(-1.0f, -1.0f), nhC2 = make_float2(-hC, -hC);
+    const float hw = R.hw;
+    float2 acc[4], part[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = part[k] = make_float2(0.f, 0.f);
+    int rr = 0;
+    for (; rr + 1 < R.nrows; rr += 2) {
+        int ilo0, ilo1;
+        float rho0, rho1;
+        fx_window(A, ilo0, rho0);
+        fx_window(A + G, ilo1, rho1);
+        line_pair_sum_rot4<KC>(base + ilo0, base + pitch + ilo1, kc, make_float2(rho0 - hw, rho1 - hw), er2, kap2,
+                               B2, ne1, q, piC, iC, nhC2, part);
+        A += 2 * G;
+        er2 = __fadd2_rn(er2, de2);
+        base += 2 * pitch;
+        if ((rr & 15) == 14) {   // blocked summation: partial sums of 16 lines
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc[k] = __fadd2_rn(acc[k], part[k]);
+                part[k] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        acc[k] = __fadd2_rn(acc[k], part[k]);
+        out[k] = acc[k].x + acc[k].y;
+    }
+    if (rr < R.nrows) {   // odd line count: the last line alone
+        int ilo;
+        float rho;
+        fx_window(A, ilo, rho);
+        float um = rho - hw;
+        for (int m = 0; m < kc; ++m, um += 1.0f) {
+            const float e = fmaf(R.kap, um, er2.x);
+            const float w = window_diff(fabsf(B * um), e, q, piC, iC, hC) * rcp_approx(e);
+            const float4 c = __ldg(base + ilo + m);
+            out[0] = fmaf(c.x, w, out[0]);
+            out[1] = fmaf(c.y, w, out[1]);
+            out[2] = fmaf(c.z, w, out[2]);
+            out[3] = fmaf(c.w, w, out[3]);
+        }
+    }
+}
+
+// One thread per ray (v, j) of views v < V/4 (and line part): the four sinogram values
+// y[v + kV/4][j], k = 0..3, written to rows v + kV/4 (nr4 = V/4 n_det rays apart).
+__global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
+                                                          const BoxF *__restrict__ box, float h2q,
+                                                          const float4 *__restrict__ imgP, const float4 *__restrict__ imgT,
+                                                          int pitch, int pad, int nr, int nr4,
+                                                          float *__restrict__ sino, int nsplit,
+                                                          float *__restrict__ partial)
+{
+    const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
+    if (q >= nr4) return;
+    RayF R = rays[q];
+    if (nsplit > 1) {
+        const int l0 = (int)((long long)R.nrows * blockIdx.z / nsplit), l1 = (int)((long long)R.nrows * (blockIdx.z + 1) / nsplit);
+        R.A0 += (long long)l0 * R.G;
+        R.e0 += (float)l0 * R.de;
+        R.r0 += l0;
+        R.nrows = l1 - l0;
+    }
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+    if (R.nrows > 0) {
+        const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
+        const float qw = bx.x, piC = bx.y, iC = bx.z, hC = bx.w;
+        const float B = 2.f * (qw - hC);
+        tighten_window(R, qw, B);
+        const float4 *base = ((R.flags & 1) ? imgT : imgP) + pad + (long long)R.r0 * pitch;
+        switch (R.kc) {
+            case 1: walk2_rot4<1>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 2: walk2_rot4<2>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 3: walk2_rot4<3>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 4: walk2_rot4<4>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 5: walk2_rot4<5>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 6: walk2_rot4<6>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 7: walk2_rot4<7>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 8: walk2_rot4<8>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            default: walk2_rot4<0>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+        }
+        const float nrm = h2q / (qw - hC);   // h^2/(2B)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out[k] *= nrm;
+    }
+    float *dst = nsplit > 1 ? partial + (long long)blockIdx.z * nr : sino;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[q + (long long)k * nr4] = out[k];
 }
 
 // ------------------------------------------------------------------ FP64 walk
@@ -289,7 +471,7 @@ __global__ void __launch_bounds__(128) fp_f64_kernel(GeomConsts g, const double 
         int k = q / g.nd, j = q - k * g.nd;
         RayParams<double> R = make_ray_params<double>(g, view_cs[2 * k], view_cs[2 * k + 1], j);
         BoxConsts<double> bc = make_box_consts<double>(R.B, R.C, g.h);
-        const double hC = 0.5 * R.C, qiC = bc.q * bc.iC;
+        const double hC = 0.5 * R.C, piC = bc.p * bc.iC;
         const bool tr = (F.flags & 1) != 0;
         const int pitch = tr ? pitchT : pitchP;
         const double *base = (tr ? imgT + b * strideT : imgP + b * strideP) + pad + (long long)F.r0 * pitch;
@@ -303,7 +485,7 @@ __global__ void __launch_bounds__(128) fp_f64_kernel(GeomConsts g, const double 
             for (int m = 0; m < F.kc; ++m) {
                 double u = (double)(ilo + m) - f;
                 double e = fma(R.kap, u, er);
-                double d = window_diff(fabs(R.B * u), e, bc.p, qiC, bc.iC, hC);
+                double d = window_diff(fabs(R.B * u), e, bc.q, piC, bc.iC, hC);
                 part += base[ilo + m] * (d / e);
             }
             A += F.G;
@@ -352,10 +534,55 @@ static int fp_line_parts(const cnsf_geometry *geo)
     return nsplit;
 }
 
+// The same over the rays of the first quarter of the views (the four-rotation kernel).
+static int fp_line_parts_rot4(const cnsf_geometry *geo)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geo->device);
+    const long long blocks = ((long long)(geo->gc.nv / 4) * geo->gc.nd + 127) / 128;
+    int nsplit = 1;
+    while (nsplit < 8 && blocks * nsplit < 128LL * std::max(sms, 1)) nsplit *= 2;
+    return nsplit;
+}
+
+static size_t forward_rot4_alloc_bytes(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    const int nsplit = fp_line_parts_rot4(geo);
+    const size_t img4 = 2 * (size_t)g.nx * (g.nx + 2 * geo->pad) * sizeof(float4);
+    return img4 + (nsplit > 1 ? (size_t)nsplit * g.nv * g.nd * sizeof(float) : 0);
+}
+
+// FP32 forward projection of one image by the four-rotation kernel (geo->sym).
+static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float *sino, cudaStream_t st)
+{
+    const GeomConsts &g = geo->gc;
+    const int n = g.nx, pad = geo->pad, pitch = n + 2 * pad;
+    const int nr = g.nv * g.nd, nr4 = (g.nv / 4) * g.nd;
+    const int nsplit = fp_line_parts_rot4(geo);
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, forward_rot4_alloc_bytes(geo), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    float4 *P4 = reinterpret_cast<float4 *>(buf), *T4 = P4 + (size_t)n * pitch;
+    float *partial = nsplit > 1 ? reinterpret_cast<float *>(T4 + (size_t)n * pitch) : nullptr;
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    pad_rot4_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(img, P4, T4, n, pad, pitch);
+    fp_rot4_f32_kernel<<<dim3((nr4 + 127) / 128, 1, nsplit), 128, 0, st>>>(
+        geo->d_fp_order4, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P4, T4, pitch, pad, nr, nr4, sino,
+        nsplit, partial);
+    if (nsplit > 1)
+        fp_sum_parts_kernel<<<(unsigned)std::min<long long>((nr + 255) / 256, 4096), 256, 0, st>>>(partial, sino, nr,
+                                                                                                   nsplit);
+    cudaFreeAsync(buf, st);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
 size_t forward_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 {
     if (batch <= 0) return 0;
     if (dtype == CNSF_F32 && batch >= 2) return forward_batch_alloc_bytes(geo);
+    if (dtype == CNSF_F32 && geo->sym) return forward_rot4_alloc_bytes(geo);
     size_t bytes = forward_scratch_bytes(geo, batch, dtype);   // padded copies
     if (dtype == CNSF_F32) {
         const int nsplit = fp_line_parts(geo);
@@ -368,6 +595,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
 {
     if (batch == 0) return CNSF_OK;
     if (dtype == CNSF_F32 && batch >= 2) return launch_forward_batch(geo, (const float *)img, (float *)sino, batch, st);
+    if (dtype == CNSF_F32 && geo->sym) return launch_forward_rot4(geo, (const float *)img, (float *)sino, st);
     const GeomConsts &g = geo->gc;
     const int nr = g.nv * g.nd;
     int pitchP, pitchT;

@@ -52,7 +52,27 @@ static int validate(const cnsf_geometry_desc *d)
     if (d->angles_rad)
         for (int k = 0; k < d->n_views; ++k)
             if (!std::isfinite(d->angles_rad[k])) return CNSF_ERR_INVALID;
+    const int known = CNSF_OPT_NO_SYMMETRY | CNSF_OPT_EXACT_DIFFERENCES | CNSF_OPT_PLAIN_DIFFERENCES;
+    if ((d->options & ~known) != 0) return CNSF_ERR_INVALID;
+    if ((d->options & CNSF_OPT_EXACT_DIFFERENCES) && (d->options & CNSF_OPT_PLAIN_DIFFERENCES)) return CNSF_ERR_INVALID;
     return CNSF_OK;
+}
+
+// The quarter-turn symmetry of an acquisition: a square image centred on the rotation axis
+// and views closed under a quarter turn, view k + V/4 at theta_k + pi/2.  Turning the whole
+// acquisition of view k (source, detector line or arc, cells; Sec. II.A) by a quarter turn
+// gives view k + V/4, and the turn maps the pixel lattice onto itself.
+static bool quarter_turn_symmetric(const cnsf_geometry_desc *d)
+{
+    if (d->options & CNSF_OPT_NO_SYMMETRY) return false;
+    if (d->n_x != d->n_y || d->center_x_mm != 0.0 || d->center_y_mm != 0.0 || d->n_views % 4 != 0) return false;
+    if (!d->angles_rad) return true;   // 2 pi k / V
+    const int q = d->n_views / 4;
+    for (int k = 0; k + q < d->n_views; ++k) {
+        const double r = std::remainder(d->angles_rad[k + q] - d->angles_rad[k] - 0.5 * M_PI, 2.0 * M_PI);
+        if (!(std::fabs(r) <= 1e-12)) return false;
+    }
+    return true;
 }
 
 int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
@@ -115,8 +135,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
             RayParams<double> R = make_ray_params<double>(g, cs[2 * k], cs[2 * k + 1], j);
             BoxConsts<double> bc = make_box_consts<double>(R.B, R.C, g.h);
             BoxF &V = box[q];
-            V.p = (float)bc.p;
-            V.qiC = (float)(bc.q * bc.iC);
+            V.q = (float)bc.q;
+            V.piC = (float)(bc.p * bc.iC);
             V.iC = (float)bc.iC;
             V.hC = (float)(0.5 * R.C);
             double emax = g.par ? 0.5 * g.tau : tmax * 0.5 * R.dtan;
@@ -169,8 +189,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     // sinogram value is 0)
     const int ndh = (nd + 1) / 2;
     // 32 bytes per cell pair (read with one 256-bit load): trapezoid constants
-    // (p, p, 2/B, 2/B, 1/C, 1/C, -C/2, -C/2) per (parity, view, pair) (q/C = p/C + 1 is
-    // formed in the kernel); cell slopes (ds/L, ds/L, c1, c1, c2, c2, 0, 0) per (parity, pair)
+    // (q, q, p/C, p/C, 1/C, 1/C, -C/2, -C/2) per (parity, view, pair); cell slopes
+    // (ds/L, ds/L, c1, c1, c2, c2, 0, 0) per (parity, pair)
     const size_t npairs = (size_t)nv * ndh;
     std::vector<float> box2(2 * 8 * npairs);
     std::vector<float> cell2(2 * 8 * (size_t)ndh, 0.0f);
@@ -180,7 +200,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
                 float *A = &box2[8 * (o * npairs + (size_t)k * ndh + m)];
                 for (int h = 0; h < 2; ++h) {
                     const BoxF &b = box[(size_t)k * nd + std::min(2 * m + o + h, nd - 1)];
-                    A[h] = b.p; A[2 + h] = (float)(1.0 / ((double)b.p + (double)b.hC)); A[4 + h] = b.iC; A[6 + h] = -b.hC;
+                    A[h] = b.q; A[2 + h] = b.piC; A[4 + h] = b.iC; A[6 + h] = -b.hC;
                 }
             }
     for (int o = 0; o < 2; ++o)
@@ -208,16 +228,22 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     // Launch orders.  Forward: blocks of 128 consecutive rays by descending walk length
     // (lines x candidates).  Back: 16 x 16 tiles by descending mean magnification of their
     // centre over the views, 1/sqrt(D_po^2 - rho^2) for a tile at radius rho.
-    std::vector<int> fp_order((nr + 127) / 128), bp_order;
+    const bool sym = quarter_turn_symmetric(d);
+    const size_t nr4 = sym ? (size_t)(nv / 4) * nd : 0;
+    std::vector<int> fp_order((nr + 127) / 128), fp_order4((nr4 + 127) / 128), bp_order;
     {
-        std::vector<std::pair<double, int>> w(fp_order.size());
-        for (size_t bi = 0; bi < fp_order.size(); ++bi) {
-            double s = 0.0;
-            for (size_t q = bi * 128; q < std::min(nr, bi * 128 + 128); ++q) s += (double)rays[q].nrows * rays[q].kc;
-            w[bi] = {-s, (int)bi};
-        }
-        std::stable_sort(w.begin(), w.end());
-        for (size_t bi = 0; bi < w.size(); ++bi) fp_order[bi] = w[bi].second;
+        auto order_blocks = [&](size_t nrays, std::vector<int> &order) {
+            std::vector<std::pair<double, int>> w(order.size());
+            for (size_t bi = 0; bi < order.size(); ++bi) {
+                double s = 0.0;
+                for (size_t q = bi * 128; q < std::min(nrays, bi * 128 + 128); ++q) s += (double)rays[q].nrows * rays[q].kc;
+                w[bi] = {-s, (int)bi};
+            }
+            std::stable_sort(w.begin(), w.end());
+            for (size_t bi = 0; bi < w.size(); ++bi) order[bi] = w[bi].second;
+        };
+        order_blocks(nr, fp_order);
+        order_blocks(nr4, fp_order4);
         const int tx = (g.nx + 15) / 16, ty = (g.ny + 15) / 16;
         std::vector<std::pair<double, int>> t((size_t)tx * ty);
         for (int b = 0; b < ty; ++b)
@@ -238,6 +264,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     geo->gc = g;
     geo->pad = pad;
     geo->kc_max = kc_max;
+    geo->sym = sym ? 1 : 0;
+    geo->exact = (d->options & CNSF_OPT_EXACT_DIFFERENCES) ? 1 : 0;
     // Back-projector window: cells within kz*zs/D_n^2*(1.02 + 2h/D_n) + ke of the pixel's
     // projection.  W bounds |s_n - s_j| over the window (widest at the nearest pixel depth).
     if (g.par) {
@@ -276,8 +304,10 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         {(void **)&geo->d_ray, rays.data(), rays.size() * sizeof(RayF)},
         {(void **)&geo->d_fp_order, fp_order.data(), fp_order.size() * sizeof(int)},
         {(void **)&geo->d_bp_order, bp_order.data(), bp_order.size() * sizeof(int)},
+        {(void **)&geo->d_fp_order4, fp_order4.data(), fp_order4.size() * sizeof(int)},
     };
     for (const Up &u : ups) {
+        if (u.bytes == 0) continue;
         cudaError_t e = cudaMalloc(u.dst, u.bytes);
         if (e != cudaSuccess) {
             destroy_geometry(geo);
@@ -296,7 +326,8 @@ void destroy_geometry(cnsf_geometry *geo)
 {
     if (!geo) return;
     void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray,
-                    geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2, geo->d_tv, geo->d_tj};
+                    geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2, geo->d_tv, geo->d_tj,
+                    geo->d_fp_order4};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete geo;

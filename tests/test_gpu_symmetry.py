@@ -1,0 +1,116 @@
+"""Entries reused over the quarter turns of the acquisition (GPU).
+
+A square image centred on the rotation axis, with views closed under a quarter turn
+(view k + V/4 at theta_k + pi/2), has every entry of Eq. (18) repeated four times:
+a(v + kV/4, j, n) = a(v, j, n turned back by k quarter turns).  The FP32 single-image
+projections then evaluate each entry once.  These tests hold that path, on every output,
+to the FP64 oracle (1e-5 relative L2, the FP32 bar) and to the general kernels of the same
+geometry (1e-6: the two differ only by FP32 rounding), check the adjoint identity between
+its two directions, and check that the library takes it exactly when the geometry has the
+symmetry.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import FanGeometry, config_geometry
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SYMMETRIC = {
+    # several 16 x 16 back-projection tiles and 32 x 32 copy tiles, with ragged edges
+    "flat_72": FanGeometry(nx=72, ny=72, n_views=88, n_det=150),
+    # odd side (the centre pixel is its own quarter turn), detector offset, close source
+    "flat_odd_offset": FanGeometry(nx=37, ny=37, n_views=40, n_det=96, d_po=200.0, d_ps=450.0, det_offset=0.3,
+                                   det_spacing=0.9, det_width=0.8),
+    "arc": FanGeometry(nx=48, ny=48, n_views=64, n_det=110, d_po=300.0, d_ps=600.0, detector="arc"),
+    "parallel": FanGeometry(nx=40, ny=40, n_views=36, n_det=70, detector="parallel"),
+    # an explicit angle list that starts off zero and is closed under the quarter turn
+    "angles_offset": FanGeometry(nx=32, ny=32, n_views=24, n_det=64,
+                                 angles=tuple(0.1 + 2.0 * math.pi * k / 24 for k in range(24))),
+    # cells 6x the pixel size: more than 8 candidates per line (the generic walk)
+    "wide_cells": FanGeometry(nx=40, ny=40, n_views=16, n_det=24, det_spacing=6.0, det_width=6.0, d_po=100.0,
+                              d_ps=200.0),
+}
+
+NOT_SYMMETRIC = {
+    "views_not_multiple_of_4": config_geometry(1),                                 # 90 views
+    "off_centre": FanGeometry(nx=32, ny=32, n_views=24, n_det=64, center_x=0.5),
+    "not_square": FanGeometry(nx=32, ny=30, n_views=24, n_det=64),
+    "angles_not_closed": FanGeometry(nx=32, ny=32, n_views=24, n_det=64,
+                                     angles=tuple(2.0 * math.pi * k / 24 + 1e-3 * (k == 7) for k in range(24))),
+}
+
+
+@pytest.fixture(scope="module")
+def cnsf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1907_10526_gb300 as m
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _fwd(cnsf, geom, x):
+    return cnsf.forward_project(geom, torch.tensor(x, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+
+
+def _bwd(cnsf, geom, y):
+    return cnsf.back_project(geom, torch.tensor(y, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+
+
+@pytest.mark.parametrize("name", sorted(SYMMETRIC))
+def test_symmetric_path_matches_oracle_and_general(cnsf, name):
+    g = SYMMETRIC[name]
+    geom = cnsf.Geometry(g)
+    gen = cnsf.Geometry(g, symmetry=False)
+    assert geom.paths["symmetric"] and not gen.paths["symmetric"]
+    rng = np.random.default_rng(50 + len(name))
+    img = rng.uniform(0.0, 1.0, (g.ny, g.nx))
+    sino = rng.uniform(0.0, 1.0, (g.n_views, g.n_det))
+    y, yg, yo = _fwd(cnsf, geom, img), _fwd(cnsf, gen, img), oracle.forward(g, img)
+    assert rel(y, yo) < 1e-5
+    assert rel(y, yg) < 1e-6
+    c, cg, co = _bwd(cnsf, geom, sino), _bwd(cnsf, gen, sino), oracle.back(g, sino)
+    assert rel(c, co) < 1e-5
+    assert rel(c, cg) < 1e-6
+    # adjoint identity <A x, s> = <x, A^T s> between the two symmetric kernels
+    lhs, rhs = float(np.vdot(y, sino)), float(np.vdot(img, c))
+    assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(y) * np.linalg.norm(sino)
+
+
+@pytest.mark.parametrize("name", sorted(NOT_SYMMETRIC))
+def test_general_path_when_not_symmetric(cnsf, name):
+    g = NOT_SYMMETRIC[name]
+    geom = cnsf.Geometry(g)
+    assert not geom.paths["symmetric"]
+    rng = np.random.default_rng(7)
+    img = rng.uniform(0.0, 1.0, (g.ny, g.nx))
+    assert rel(_fwd(cnsf, geom, img), oracle.forward(g, img)) < 1e-5
+
+
+def test_headline_workload_takes_symmetric_path(cnsf):
+    geom = cnsf.Geometry(config_geometry(2))
+    assert geom.paths == {"symmetric": True, "exact_differences": False}
+
+
+def test_symmetric_repeats_bitwise(cnsf):
+    """No atomics and fixed reduction orders: repeated calls give the same bits."""
+    g = SYMMETRIC["flat_72"]
+    geom = cnsf.Geometry(g)
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.uniform(0, 1, (g.ny, g.nx)), dtype=torch.float32, device="cuda")
+    y1 = cnsf.forward_project(geom, x)
+    y2 = cnsf.forward_project(geom, x)
+    assert torch.equal(y1, y2)
+    c1 = cnsf.back_project(geom, y1)
+    c2 = cnsf.back_project(geom, y1)
+    assert torch.equal(c1, c2)

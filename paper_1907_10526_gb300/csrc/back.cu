@@ -141,7 +141,7 @@ __device__ __forceinline__ float bp_quad_hwc(const TileViewS<float> &T, float Dn
 // projection, in cells.  Arc detector: |s'| = R sin(dg d), R the pixel's
 // distance from the source; with dg d below ~0.05 rad, R dg d (1 - (dg d)^2/6) is that sine
 // to ~1e-9 relative (the next term of the series).
-template <bool ARC>
+template <bool ARC, bool EXACT>
 __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const float (&A)[8], const float (&C)[8],
                                               float nk6)
 {
@@ -155,7 +155,7 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
     const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));                                 // |s'|
     const float2 e = __ffma2_rn(make_float2(P.Dn, P.Dn), make_float2(C[2], C[3]),
                                 __fmul2_rn(make_float2(P.yp, P.yp), make_float2(C[4], C[5])));
-    const float2 w = window_diff2p(x, e, ne1, make_float2(A[0], A[1]), make_float2(A[2], A[3]),
+    const float2 w = wdiff2p<EXACT>(x, e, ne1, make_float2(A[0], A[1]), make_float2(A[2], A[3]),
                                    make_float2(A[4], A[5]), make_float2(A[6], A[7]));
     return __fmul2_rn(w, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
 }
@@ -170,7 +170,7 @@ __device__ __forceinline__ float2 bp_pair_f32(const BpPixel &P, float2 d, const 
 // past g1 of an odd-length window, lies outside that pixel's support (the window bounds the
 // support with margin), so its entry for that pixel is exactly 0; a cell past n_det has
 // sinogram value 0.  Returns the two pixels' sums.
-template <bool ARC>
+template <bool ARC, bool EXACT>
 __device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel &Pb, float hwc, int J, const BpArgs &a,
                                                int nd, const float2 *__restrict__ y2row,
                                                const float2 *__restrict__ y2orow, const float *__restrict__ boxrow,
@@ -194,8 +194,8 @@ __device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel 
         ldg256(boxrow + 8 * m, A);    // q | p/C | 1/C | -C/2, pairs
         ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
         const float2 yb = __ldg(y2row + m);                                                  // y 2/B
-        acca = __ffma2_rn(yb, bp_pair_f32<ARC>(Pa, da, A, C, a.nk6), acca);
-        accb = __ffma2_rn(yb, bp_pair_f32<ARC>(Pb, db, A, C, a.nk6), accb);
+        acca = __ffma2_rn(yb, bp_pair_f32<ARC, EXACT>(Pa, da, A, C, a.nk6), acca);
+        accb = __ffma2_rn(yb, bp_pair_f32<ARC, EXACT>(Pb, db, A, C, a.nk6), accb);
         da = __fadd2_rn(da, m2);
         db = __fadd2_rn(db, m2);
     }
@@ -208,7 +208,7 @@ __device__ __forceinline__ float2 bp_view2_f32(const BpPixel &Pa, const BpPixel 
 // along the image axis whose unit step moves the projection least (columns when
 // |d sigma/d row| <= |d sigma/d column|), so the two pixels of a pair reach nearly the same
 // cells and their union window adds little.
-template <bool ARC>
+template <bool ARC, bool EXACT>
 __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts g, const double *__restrict__ view_cs,
                                                                  const float *__restrict__ box2,
                                                                  const float *__restrict__ cell2,
@@ -280,8 +280,8 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
                 if (!in3) P3.sig = P0.sig;
                 const float hwc = bp_quad_hwc(T, Dn0, yp0, a);
                 const float2 *yorow = yo + (long long)v * ndh;
-                const float2 s1 = bp_view2_f32<ARC>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2);
-                const float2 s2 = bp_view2_f32<ARC>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2);
+                const float2 s1 = bp_view2_f32<ARC, EXACT>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2);
+                const float2 s2 = bp_view2_f32<ARC, EXACT>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2);
                 part[0] += s1.x;
                 part[1] += col ? s2.x : s1.y;
                 part[2] += col ? s1.y : s2.x;
@@ -358,7 +358,7 @@ __global__ void sino_pairs_rot4_kernel(const float *__restrict__ y, const BoxF *
 // bp_view2_f32 for the four rotations: the same window and cell pairs; each pair's entries
 // for pixels a and b are applied to the four weighted sinogram pairs of the step and added
 // to ta[k], tb[k] (lanes: the two cells of the pair).
-template <bool ARC>
+template <bool ARC, bool EXACT>
 __device__ __forceinline__ void bp_view2_rot4(const BpPixel &Pa, const BpPixel &Pb, float hwc, int J, const BpArgs &a,
                                               int nd, const float *__restrict__ y4row,
                                               const float *__restrict__ y4orow, const float *__restrict__ boxrow,
@@ -381,7 +381,7 @@ __device__ __forceinline__ void bp_view2_rot4(const BpPixel &Pa, const BpPixel &
         ldg256(boxrow + 8 * m, A);    // q | p/C | 1/C | -C/2, pairs
         ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
         ldg256(y4row + 8 * m, Y);     // y 2/B of the four rotations, pairs
-        const float2 wa = bp_pair_f32<ARC>(Pa, da, A, C, a.nk6), wb = bp_pair_f32<ARC>(Pb, db, A, C, a.nk6);
+        const float2 wa = bp_pair_f32<ARC, EXACT>(Pa, da, A, C, a.nk6), wb = bp_pair_f32<ARC, EXACT>(Pb, db, A, C, a.nk6);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float2 yk = make_float2(Y[2 * k], Y[2 * k + 1]);
@@ -397,7 +397,7 @@ __device__ __forceinline__ void bp_view2_rot4(const BpPixel &Pa, const BpPixel &
 // partial images T_k (view part s: partial[(4 s + k)][N][N]).  The quad's pixel pairs are
 // gathered along the axis that moves the projection least, the two pairings in two
 // branches (uniform over the block) so that every accumulator keeps its register.
-template <bool ARC>
+template <bool ARC, bool EXACT>
 __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomConsts g, const float *__restrict__ box2,
                                                                      const float *__restrict__ cell2,
                                                                      const float *__restrict__ y4, BpArgs a,
@@ -466,11 +466,11 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
             if (!in3) P3.sig = P0.sig;
             const float hwc = bp_quad_hwc(T, Dn0, yp0, a);
             if (col) {   // P1 is quad pixel 2, P2 quad pixel 1
-                bp_view2_rot4<ARC>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[2]);
-                bp_view2_rot4<ARC>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[1], t[3]);
+                bp_view2_rot4<ARC, EXACT>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[2]);
+                bp_view2_rot4<ARC, EXACT>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[1], t[3]);
             } else {
-                bp_view2_rot4<ARC>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[1]);
-                bp_view2_rot4<ARC>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[2], t[3]);
+                bp_view2_rot4<ARC, EXACT>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[1]);
+                bp_view2_rot4<ARC, EXACT>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[2], t[3]);
             }
         }
     }
@@ -660,7 +660,8 @@ static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *
     BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
              (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0), 8LL * g.nv * ndh, 8 * ndh};
     const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
-    auto kern = g.arc ? bp_rot4_f32_kernel<true> : bp_rot4_f32_kernel<false>;
+    auto kern = g.arc ? (geo->exact ? bp_rot4_f32_kernel<true, true> : bp_rot4_f32_kernel<true, false>)
+                      : (geo->exact ? bp_rot4_f32_kernel<false, true> : bp_rot4_f32_kernel<false, false>);
     kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_box2, geo->d_cell2, y4, a, geo->d_bp_order,
                                                                  ntx, nsplit, partial, geo->d_view_cs, geo->d_tv,
                                                                  geo->d_tj);
@@ -716,7 +717,8 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, geo->d_box, copy, nrows, g.nv, g.nd, 1);
         sino_pairs_kernel<<<pblocks, 256, 0, st>>>((const float *)sino, geo->d_box, copy + npair, nrows, g.nv, g.nd, 0);
         const float2 *y2 = copy + npair;
-        auto kern = g.arc ? bp_f32_kernel<true> : bp_f32_kernel<false>;
+        auto kern = g.arc ? (geo->exact ? bp_f32_kernel<true, true> : bp_f32_kernel<true, false>)
+                          : (geo->exact ? bp_f32_kernel<false, true> : bp_f32_kernel<false, false>);
         kern<<<dim3(grd.x * grd.y, nsplit, grd.z), dim3(BP_QUAD_THREADS), 0, st>>>(
             g, geo->d_view_cs, geo->d_box2, geo->d_cell2, y2, copy, (float *)img, a, geo->d_bp_order,
             (int)grd.x, nsplit, partial, geo->d_tv, geo->d_tj);

@@ -97,7 +97,7 @@ struct Acc {
 // ------------------------------------------------------------------ forward
 // KC candidates per line; KC = 0: R.kc of them (windows wider than 8 pixels, cells much
 // wider than pixels).
-template <int KC, int NB4>
+template <int KC, int NB4, bool EXACT>
 __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__restrict__ base, int pitch4, float B,
                                               float q, float piC, float iC, float hC, Acc<NB4> &acc)
 {
@@ -114,7 +114,7 @@ __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__res
         for (int m = 0; m < kc; ++m) {
             const float um = u0 + (float)m;
             const float e = fmaf(R.kap, um, er);
-            const float d = window_diff(fabsf(B * um), e, q, piC, iC, hC);
+            const float d = wdiff<EXACT>(fabsf(B * um), e, q, piC, iC, hC);
             part.fma_from(d * rcp_approx(e), rp + m * NB4);
         }
         A += R.G;
@@ -129,7 +129,7 @@ __device__ __forceinline__ void fp_batch_walk(const RayF &R, const float4 *__res
 }
 
 // One ray's walk over its lines [l0, l1), a part of [R.r0, R.r0 + R.nrows), added to acc.
-template <int NB4>
+template <int NB4, bool EXACT>
 __device__ __forceinline__ void fp_batch_walk_lines(RayF R, int l0, int l1, const float4 *__restrict__ P,
                                                     const float4 *__restrict__ Tt, int pitchP, int pitchT, int pad,
                                                     float B, float q, float piC, float iC, float hC, Acc<NB4> &acc)
@@ -145,15 +145,15 @@ __device__ __forceinline__ void fp_batch_walk_lines(RayF R, int l0, int l1, cons
     const float4 *base = (tr ? Tt : P) + ((long long)R.r0 * pitch + pad) * NB4;
     const int p4 = pitch * NB4;
     switch (R.kc) {
-        case 1: fp_batch_walk<1, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        case 2: fp_batch_walk<2, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        case 3: fp_batch_walk<3, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        case 4: fp_batch_walk<4, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        case 5: fp_batch_walk<5, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        case 6: fp_batch_walk<6, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        case 7: fp_batch_walk<7, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        case 8: fp_batch_walk<8, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
-        default: fp_batch_walk<0, NB4>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 1: fp_batch_walk<1, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 2: fp_batch_walk<2, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 3: fp_batch_walk<3, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 4: fp_batch_walk<4, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 5: fp_batch_walk<5, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 6: fp_batch_walk<6, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 7: fp_batch_walk<7, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        case 8: fp_batch_walk<8, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
+        default: fp_batch_walk<0, NB4, EXACT>(R, base, p4, B, q, piC, iC, hC, acc); break;
     }
 }
 
@@ -169,7 +169,7 @@ struct RayBox {
 // entry for that ray is exactly 0 (image pixels lie in front of the source, so tau'/2 > 0
 // there; padding pixels are 0).  The union lies between the two windows, inside the padded
 // line.
-template <int NB4>
+template <int NB4, bool EXACT>
 __device__ __forceinline__ void fp_batch_walk_joint(const RayF &Ra, const RayF &Rb, const RayBox &Xa,
                                                     const RayBox &Xb, int j0, int j1, const float4 *__restrict__ base,
                                                     int p4, Acc<NB4> &acca, Acc<NB4> &accb)
@@ -191,8 +191,8 @@ __device__ __forceinline__ void fp_batch_walk_joint(const RayF &Ra, const RayF &
             for (int k = 0; k < NB4; ++k) v[k] = __ldg(base + (long long)c * NB4 + k);
             const float ua = ua0 + (float)(c - ia), ub = ub0 + (float)(c - ib);
             const float ea = fmaf(Ra.kap, ua, era), eb = fmaf(Rb.kap, ub, erb);
-            const float da = window_diff(fabsf(Xa.B * ua), ea, Xa.q, Xa.piC, Xa.iC, Xa.hC);
-            const float db = window_diff(fabsf(Xb.B * ub), eb, Xb.q, Xb.piC, Xb.iC, Xb.hC);
+            const float da = wdiff<EXACT>(fabsf(Xa.B * ua), ea, Xa.q, Xa.piC, Xa.iC, Xa.hC);
+            const float db = wdiff<EXACT>(fabsf(Xb.B * ub), eb, Xb.q, Xb.piC, Xb.iC, Xb.hC);
             parta.fma_with(da * rcp_approx(ea), v);
             partb.fma_with(db * rcp_approx(eb), v);
         }
@@ -216,7 +216,7 @@ __device__ __forceinline__ void fp_batch_walk_joint(const RayF &Ra, const RayF &
 // over their common lines when they are adjacent cells of one view with the same walk axis,
 // each alone over the rest of its lines; otherwise each alone.  The pairing does not depend
 // on the batch, so neither does any image's result.
-template <int NB4>
+template <int NB4, bool EXACT>
 __global__ void __launch_bounds__(64) fp_batch_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
                                                       const BoxF *__restrict__ box,
                                                       float h2q, const float4 *__restrict__ P,
@@ -246,23 +246,23 @@ __global__ void __launch_bounds__(64) fp_batch_kernel(const int *__restrict__ or
                        (R[0].flags & 1) == (R[1].flags & 1) && j0 < j1;
     if (joint) {
         // each ray alone before and after the common lines, then both together
-        fp_batch_walk_lines<NB4>(R[0], la0, j0, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].q, X[0].piC, X[0].iC,
+        fp_batch_walk_lines<NB4, EXACT>(R[0], la0, j0, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].q, X[0].piC, X[0].iC,
                                  X[0].hC, acc[0]);
-        fp_batch_walk_lines<NB4>(R[0], j1, la1, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].q, X[0].piC, X[0].iC,
+        fp_batch_walk_lines<NB4, EXACT>(R[0], j1, la1, P, Tt, pitchP, pitchT, pad, X[0].B, X[0].q, X[0].piC, X[0].iC,
                                  X[0].hC, acc[0]);
-        fp_batch_walk_lines<NB4>(R[1], lb0, j0, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].q, X[1].piC, X[1].iC,
+        fp_batch_walk_lines<NB4, EXACT>(R[1], lb0, j0, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].q, X[1].piC, X[1].iC,
                                  X[1].hC, acc[1]);
-        fp_batch_walk_lines<NB4>(R[1], j1, lb1, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].q, X[1].piC, X[1].iC,
+        fp_batch_walk_lines<NB4, EXACT>(R[1], j1, lb1, P, Tt, pitchP, pitchT, pad, X[1].B, X[1].q, X[1].piC, X[1].iC,
                                  X[1].hC, acc[1]);
         const bool tr = (R[0].flags & 1) != 0;
         const int pitch = tr ? pitchT : pitchP;
         const float4 *base = (tr ? Tt : P) + ((long long)j0 * pitch + pad) * NB4;
-        fp_batch_walk_joint<NB4>(R[0], R[1], X[0], X[1], j0, j1, base, pitch * NB4, acc[0], acc[1]);
+        fp_batch_walk_joint<NB4, EXACT>(R[0], R[1], X[0], X[1], j0, j1, base, pitch * NB4, acc[0], acc[1]);
     } else {
 #pragma unroll
         for (int s = 0; s < 2; ++s)
             if ((s == 0 || has1) && R[s].nrows > 0)
-                fp_batch_walk_lines<NB4>(R[s], R[s].r0, R[s].r0 + R[s].nrows, P, Tt, pitchP, pitchT, pad, X[s].B,
+                fp_batch_walk_lines<NB4, EXACT>(R[s], R[s].r0, R[s].r0 + R[s].nrows, P, Tt, pitchP, pitchT, pad, X[s].B,
                                          X[s].q, X[s].piC, X[s].iC, X[s].hC, acc[s]);
     }
 #pragma unroll
@@ -294,7 +294,7 @@ struct alignas(16) TileViewB {
 // sigma are affine in the offset).  Per-view sums are added to the accumulators in shared
 // memory every 16 views (blocked summation), in the same order for every chunk size, so an
 // image's result does not depend on the batch it is projected in.
-template <int NB4>
+template <int NB4, bool EXACT>
 __global__ void __launch_bounds__(BPB_THREADS) bp_batch_kernel(GeomConsts g, const double *__restrict__ view_cs,
                                                                const float4 *__restrict__ box,
                                                                const float4 *__restrict__ cell,
@@ -371,8 +371,8 @@ __global__ void __launch_bounds__(BPB_THREADS) bp_batch_kernel(GeomConsts g, con
                 const float x0 = g.arc ? fabsf(G0 * d0 * fmaf(d0 * d0, nk6, 1.f)) : fabsf(Dn0 * C.x * d0);
                 const float x1 = g.arc ? fabsf(G1 * d1 * fmaf(d1 * d1, nk6, 1.f)) : fabsf(Dn1 * C.x * d1);
                 const float e0 = fmaf(Dn0, C.y, yp0 * C.z), e1 = fmaf(Dn1, C.y, yp1 * C.z);
-                const float w0 = window_diff(x0, e0, A.x, A.y, A.z, A.w);
-                const float w1 = window_diff(x1, e1, A.x, A.y, A.z, A.w);
+                const float w0 = wdiff<EXACT>(x0, e0, A.x, A.y, A.z, A.w);
+                const float w1 = wdiff<EXACT>(x1, e1, A.x, A.y, A.z, A.w);
                 part0.fma_with(w0 * rcp_approx((A.x - A.w) * e0), yv);   // (B/2) tau'/2
                 part1.fma_with(w1 * rcp_approx((A.x - A.w) * e1), yv);
                 d0 -= 1.f;
@@ -444,11 +444,11 @@ int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino
         const float h2q = (float)(0.25 * g.h * g.h);
         const float4 *P4 = reinterpret_cast<const float4 *>(P), *T4 = reinterpret_cast<const float4 *>(Tt);
         if (nb4 == 4)
-            fp_batch_kernel<4><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
+            (geo->exact ? fp_batch_kernel<4, true> : fp_batch_kernel<4, false>)<<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
         else if (nb4 == 2)
-            fp_batch_kernel<2><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
+            (geo->exact ? fp_batch_kernel<2, true> : fp_batch_kernel<2, false>)<<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
         else
-            fp_batch_kernel<1><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
+            (geo->exact ? fp_batch_kernel<1, true> : fp_batch_kernel<1, false>)<<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, h2q, P4, T4, pitchP, pitchT, pad, nr, g.nd, sino, b0, used);
         b0 += used;
     }
     cudaFreeAsync(buf, st);
@@ -475,11 +475,11 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
             sino, buf, nvd, b0, used, NB);
         const float4 *Y = reinterpret_cast<const float4 *>(buf);
         if (nb4 == 4)
-            bp_batch_kernel<4><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
+            (geo->exact ? bp_batch_kernel<4, true> : bp_batch_kernel<4, false>)<<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
         else if (nb4 == 2)
-            bp_batch_kernel<2><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
+            (geo->exact ? bp_batch_kernel<2, true> : bp_batch_kernel<2, false>)<<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
         else
-            bp_batch_kernel<1><<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
+            (geo->exact ? bp_batch_kernel<1, true> : bp_batch_kernel<1, false>)<<<grd, blk, 0, st>>>(g, geo->d_view_cs, box, cell, Y, img, kz, ke, h2, h2q, b0, used, geo->d_bp_order, ntx, kscale, dg, nk6);
         b0 += used;
     }
     cudaFreeAsync(buf, st);

@@ -100,4 +100,78 @@ __device__ __forceinline__ float2 window_diff2p(float2 x, float2 e, float2 ne1, 
     return __ffma2_rn(cs, ne1, h1);
 }
 
+// ---------------------------------------------------------------- exact window difference
+// The same B * 2e * M(x) (x >= 0) without the cancellation: with G the odd extension of
+// B H, G(z) = clamp(z, -q, q) - (C/2) (r+(z)^2 - r-(z)^2), r+(z) = sat((z - p)/C),
+// r-(z) = sat((-z - p)/C), the difference over the window [z0, z1] = [x - e, x + e] is
+//   G(z1) - G(z0) = L - (C/2) (dr (r+(z1) + r+(z0)) + r-(z0)^2)
+// (r-(z1) = 0 for x >= 0), where L = |[z0, z1] n [-q, q]| = max(0, min(2e, 2q, (q - x) + e))
+// and dr = r+(z1) - r+(z0) = max(0, min(2e/C, 1, 1 - (q - x)/C + e/C, (q - x)/C + e/C)), the
+// clipped lengths written with the cut points relative to x.  Every term is formed from
+// q - x, e and constants, none as the difference of two values of size B, so the result
+// keeps ~1e-7 of 2e however thin the blur (the plain form loses log2(B / 2e) bits); the one
+// subtraction left cancels only where the window leaves the footprint's ramp, and there the
+// value itself is small.  About twice the instructions of window_diff.
+template <typename T>
+__device__ __forceinline__ T window_diff_exact(T x, T e, T q, T piC, T iC, T hC)
+{
+    const T one = T(1), zero = T(0);
+    const T u = q - x;                                       // distance to the outer edge
+    const T L = fmax(zero, fmin(fmin(e + e, q + q), u + e));
+    const T ep = e * iC, v = u * iC;                         // e/C, (q - x)/C
+    const T ope = one + ep;
+    const T t1 = ope - v;                                    // (x + e - p)/C
+    const T b = v + ep;                                      // (q - x + e)/C = 1 - (x - e - p)/C
+    const T dr = fmax(zero, fmin(fmin(ep + ep, one), fmin(t1, b)));
+    const T sr = sat01(t1) + sat01((one - ep) - v);          // r+(z1) + r+(z0)
+    const T rm = sat01(ope - fma(x, iC, piC + one));         // r-(z0) = sat((e - x - p)/C)
+    return fma(-hC, fma(dr, sr, rm * rm), L);
+}
+
+// Packed forms of window_diff_exact (shared constants; pair constants), lane by lane the
+// same arithmetic.
+__device__ __forceinline__ float2 window_diff2p_exact(float2 x, float2 e, float2 ne1, float2 q, float2 piC, float2 iC,
+                                                      float2 nhC)
+{
+    const float2 one = make_float2(1.f, 1.f);
+    const float2 u = __ffma2_rn(x, ne1, q);
+    const float2 eu = __fadd2_rn(u, e), e2 = __fadd2_rn(e, e), q2 = __fadd2_rn(q, q);
+    const float2 L = make_float2(fmaxf(0.f, fminf(fminf(e2.x, q2.x), eu.x)), fmaxf(0.f, fminf(fminf(e2.y, q2.y), eu.y)));
+    const float2 ep = __fmul2_rn(e, iC), v = __fmul2_rn(u, iC);
+    const float2 ope = __fadd2_rn(one, ep);
+    const float2 t1 = __ffma2_rn(v, ne1, ope);
+    const float2 b = __fadd2_rn(v, ep), ep2 = __fadd2_rn(ep, ep);
+    const float2 dr = make_float2(fmaxf(0.f, fminf(fminf(ep2.x, 1.f), fminf(t1.x, b.x))),
+                                  fmaxf(0.f, fminf(fminf(ep2.y, 1.f), fminf(t1.y, b.y))));
+    const float2 t0 = __ffma2_rn(v, ne1, __ffma2_rn(ep, ne1, one));
+    const float2 sr = __fadd2_rn(make_float2(sat01(t1.x), sat01(t1.y)), make_float2(sat01(t0.x), sat01(t0.y)));
+    const float2 w = __ffma2_rn(x, iC, __fadd2_rn(piC, one));
+    const float2 m = __ffma2_rn(w, ne1, ope);
+    const float2 rm = make_float2(sat01(m.x), sat01(m.y));
+    return __ffma2_rn(nhC, __ffma2_rn(rm, rm, __fmul2_rn(dr, sr)), L);
+}
+
+__device__ __forceinline__ float2 window_diff2_exact(float2 x, float2 e, float2 ne1, float q, float piC, float iC,
+                                                     float2 nhC2)
+{
+    return window_diff2p_exact(x, e, ne1, make_float2(q, q), make_float2(piC, piC), make_float2(iC, iC), nhC2);
+}
+
+// The form a kernel instantiation uses: EXACT selects the cancellation-free differences.
+template <bool EXACT, typename T>
+__device__ __forceinline__ T wdiff(T x, T e, T q, T piC, T iC, T hC)
+{
+    return EXACT ? window_diff_exact(x, e, q, piC, iC, hC) : window_diff(x, e, q, piC, iC, hC);
+}
+template <bool EXACT>
+__device__ __forceinline__ float2 wdiff2(float2 x, float2 e, float2 ne1, float q, float piC, float iC, float2 nhC2)
+{
+    return EXACT ? window_diff2_exact(x, e, ne1, q, piC, iC, nhC2) : window_diff2(x, e, ne1, q, piC, iC, nhC2);
+}
+template <bool EXACT>
+__device__ __forceinline__ float2 wdiff2p(float2 x, float2 e, float2 ne1, float2 q, float2 piC, float2 iC, float2 nhC)
+{
+    return EXACT ? window_diff2p_exact(x, e, ne1, q, piC, iC, nhC) : window_diff2p(x, e, ne1, q, piC, iC, nhC);
+}
+
 }  // namespace cnsf

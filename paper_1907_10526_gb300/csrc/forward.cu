@@ -57,7 +57,7 @@ __global__ void pad_transpose_kernel(const T *__restrict__ img, T *__restrict__ 
 // ------------------------------------------------------------------ FP32 walk
 // One line of the walk with KC candidates, fully unrolled.  u is the signed a-offset
 // (ia - f) of the first candidate.
-template <int KC, bool COUNT>
+template <int KC, bool COUNT, bool EXACT>
 __device__ __forceinline__ float line_sum(const float *__restrict__ rp, float u, float er, float kap,
                                           float B, float q, float piC, float iC, float hC)
 {
@@ -72,7 +72,7 @@ __device__ __forceinline__ float line_sum(const float *__restrict__ rp, float u,
             // strictly inside the support |s'| < (B + C + tau')/2 of M_[B,C,tau']
             s += (x < q + e) ? c : 0.f;
         } else {
-            float d = window_diff(x, e, q, piC, iC, hC);
+            float d = wdiff<EXACT>(x, e, q, piC, iC, hC);
             s = fmaf(c, d * rcp_approx(e), s);
         }
     }
@@ -82,7 +82,7 @@ __device__ __forceinline__ float line_sum(const float *__restrict__ rp, float u,
 // Two consecutive lines of the walk at once with packed FP32 arithmetic: lane .x of every
 // float2 belongs to line rb, lane .y to line rb + 1, and the KC candidates of both lines
 // are evaluated pair by pair (no padding candidates).
-template <int KC>
+template <int KC, bool EXACT>
 __device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, const float *__restrict__ rp1,
                                                 float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1,
                                                 float q, float piC, float iC, float2 nhC2)
@@ -93,7 +93,7 @@ __device__ __forceinline__ float2 line_pair_sum(const float *__restrict__ rp0, c
 #pragma unroll
     for (int m = 0; m < KC; ++m) {
         const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));
-        const float2 d = window_diff2(x, e, ne1, q, piC, iC, nhC2);
+        const float2 d = wdiff2<EXACT>(x, e, ne1, q, piC, iC, nhC2);
         const float2 w = __fmul2_rn(d, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
         const float2 c = make_float2(__ldg(rp0 + m), __ldg(rp1 + m));
         s = __ffma2_rn(c, w, s);
@@ -114,7 +114,7 @@ __device__ __forceinline__ void fx_window(long long Bc, int &ilo, float &rho)
     rho = fmaf(__uint2float_rn((unsigned)Bc), -1.0f / 4294967296.0f, 1.0f);
 }
 
-template <int KC>
+template <int KC, bool EXACT>
 __device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ base, int pitch, float B,
                                        float q, float piC, float iC, float hC)
 {
@@ -133,7 +133,7 @@ __device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ 
         fx_window(A, ilo0, rho0);
         fx_window(A + G, ilo1, rho1);
         const float2 u = make_float2(rho0 - hw, rho1 - hw);
-        part = __fadd2_rn(part, line_pair_sum<KC>(base + ilo0, base + pitch + ilo1, u, er2, kap2, B2, ne1, q,
+        part = __fadd2_rn(part, line_pair_sum<KC, EXACT>(base + ilo0, base + pitch + ilo1, u, er2, kap2, B2, ne1, q,
                                                   piC, iC, nhC2));
         A += 2 * G;
         er2 = __fadd2_rn(er2, de2);
@@ -149,12 +149,12 @@ __device__ __forceinline__ float walk2(const RayF &R, const float *__restrict__ 
         int ilo;
         float rho;
         fx_window(A, ilo, rho);
-        tot += line_sum<KC, false>(base + ilo, rho - hw, er2.x, R.kap, B, q, piC, iC, hC);
+        tot += line_sum<KC, false, EXACT>(base + ilo, rho - hw, er2.x, R.kap, B, q, piC, iC, hC);
     }
     return tot;
 }
 
-template <int KC, bool COUNT>
+template <int KC, bool COUNT, bool EXACT>
 __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ base, int pitch, float B,
                                       float q, float piC, float iC, float hC)
 {
@@ -168,7 +168,7 @@ __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ b
         int ilo = (int)(A >> 32) + (((unsigned)A) != 0u ? 1 : 0);
         unsigned nl = 0u - (unsigned)A;
         float rho = __uint_as_float(0x3f800000u | (nl >> 9)) - 1.0f;
-        part += line_sum<KC, COUNT>(base + ilo, rho - hw, er, kap, B, q, piC, iC, hC);
+        part += line_sum<KC, COUNT, EXACT>(base + ilo, rho - hw, er, kap, B, q, piC, iC, hC);
         A += G;
         er += de;
         base += pitch;
@@ -180,7 +180,7 @@ __device__ __forceinline__ float walk(const RayF &R, const float *__restrict__ b
     return acc + part;
 }
 
-template <bool COUNT>
+template <bool COUNT, bool EXACT>
 __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
                                                      const BoxF *__restrict__ box, float h2q,
                                                      const float *__restrict__ imgP, const float *__restrict__ imgT,
@@ -213,22 +213,22 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
         const float *base = (tr ? imgT + b * strideT : imgP + b * strideP) + pad + (long long)R.r0 * pitch;
         const int kcase = COUNT ? R.kc : 100 + R.kc;
         switch (kcase) {
-            case 1: acc = walk<1, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 2: acc = walk<2, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 3: acc = walk<3, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 4: acc = walk<4, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 5: acc = walk<5, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 6: acc = walk<6, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 7: acc = walk<7, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 8: acc = walk<8, COUNT>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 101: acc = walk2<1>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 102: acc = walk2<2>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 103: acc = walk2<3>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 104: acc = walk2<4>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 105: acc = walk2<5>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 106: acc = walk2<6>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 107: acc = walk2<7>(R, base, pitch, B, qw, piC, iC, hC); break;
-            case 108: acc = walk2<8>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 1: acc = walk<1, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 2: acc = walk<2, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 3: acc = walk<3, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 4: acc = walk<4, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 5: acc = walk<5, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 6: acc = walk<6, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 7: acc = walk<7, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 8: acc = walk<8, COUNT, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 101: acc = walk2<1, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 102: acc = walk2<2, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 103: acc = walk2<3, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 104: acc = walk2<4, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 105: acc = walk2<5, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 106: acc = walk2<6, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 107: acc = walk2<7, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
+            case 108: acc = walk2<8, EXACT>(R, base, pitch, B, qw, piC, iC, hC); break;
             default: {
                 // wide windows (cells much wider than pixels): generic loop
                 long long A = R.A0;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
                         if (COUNT)
                             acc += (x < qw + e) ? c : 0.f;
                         else
-                            acc += c * window_diff(x, e, qw, piC, iC, hC) * rcp_approx(e);
+                            acc += c * wdiff<EXACT>(x, e, qw, piC, iC, hC) * rcp_approx(e);
                     }
                     A += R.G;
                     er += R.de;
@@ -329,7 +329,7 @@ __global__ void pad_rot4_kernel(const float *__restrict__ img, float4 *__restric
 // The candidates of two consecutive lines, packed as in line_pair_sum, each entry applied to
 // the four rotated values of its pixel; s[k] accumulates rotation k (lanes: the two lines).
 // KC = 0: kc candidates (wide cells).
-template <int KC>
+template <int KC, bool EXACT>
 __device__ __forceinline__ void line_pair_sum_rot4(const float4 *__restrict__ rp0, const float4 *__restrict__ rp1,
                                                    int kc, float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1,
                                                    float q, float piC, float iC, float2 nhC2, float2 (&s)[4])
@@ -338,7 +338,7 @@ __device__ __forceinline__ void line_pair_sum_rot4(const float4 *__restrict__ rp
 #pragma unroll
     for (int m = 0; m < (KC > 0 ? KC : kc); ++m) {
         const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));
-        const float2 d = window_diff2(x, e, ne1, q, piC, iC, nhC2);
+        const float2 d = wdiff2<EXACT>(x, e, ne1, q, piC, iC, nhC2);
         const float2 w = __fmul2_rn(d, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
         const float4 c0 = __ldg(rp0 + m), c1 = __ldg(rp1 + m);
         s[0] = __ffma2_rn(make_float2(c0.x, c1.x), w, s[0]);
@@ -351,7 +351,7 @@ __device__ __forceinline__ void line_pair_sum_rot4(const float4 *__restrict__ rp
 }
 
 // walk2 for the four rotations: two lines per packed step, blocked sums of 16 lines.
-template <int KC>
+template <int KC, bool EXACT>
 __device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restrict__ base, int pitch, float B,
                                            float q, float piC, float iC, float hC, float (&out)[4])
 {
@@ -371,7 +371,7 @@ __device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restri
         float rho0, rho1;
         fx_window(A, ilo0, rho0);
         fx_window(A + G, ilo1, rho1);
-        line_pair_sum_rot4<KC>(base + ilo0, base + pitch + ilo1, kc, make_float2(rho0 - hw, rho1 - hw), er2, kap2,
+        line_pair_sum_rot4<KC, EXACT>(base + ilo0, base + pitch + ilo1, kc, make_float2(rho0 - hw, rho1 - hw), er2, kap2,
                                B2, ne1, q, piC, iC, nhC2, part);
         A += 2 * G;
         er2 = __fadd2_rn(er2, de2);
@@ -396,7 +396,7 @@ __device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restri
         float um = rho - hw;
         for (int m = 0; m < kc; ++m, um += 1.0f) {
             const float e = fmaf(R.kap, um, er2.x);
-            const float w = window_diff(fabsf(B * um), e, q, piC, iC, hC) * rcp_approx(e);
+            const float w = wdiff<EXACT>(fabsf(B * um), e, q, piC, iC, hC) * rcp_approx(e);
             const float4 c = __ldg(base + ilo + m);
             out[0] = fmaf(c.x, w, out[0]);
             out[1] = fmaf(c.y, w, out[1]);
@@ -408,6 +408,7 @@ __device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restri
 
 // One thread per ray (v, j) of views v < V/4 (and line part): the four sinogram values
 // y[v + kV/4][j], k = 0..3, written to rows v + kV/4 (nr4 = V/4 n_det rays apart).
+template <bool EXACT>
 __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
                                                           const BoxF *__restrict__ box, float h2q,
                                                           const float4 *__restrict__ imgP, const float4 *__restrict__ imgT,
@@ -433,15 +434,15 @@ __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict_
         tighten_window(R, qw, B);
         const float4 *base = ((R.flags & 1) ? imgT : imgP) + pad + (long long)R.r0 * pitch;
         switch (R.kc) {
-            case 1: walk2_rot4<1>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            case 2: walk2_rot4<2>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            case 3: walk2_rot4<3>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            case 4: walk2_rot4<4>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            case 5: walk2_rot4<5>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            case 6: walk2_rot4<6>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            case 7: walk2_rot4<7>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            case 8: walk2_rot4<8>(R, base, pitch, B, qw, piC, iC, hC, out); break;
-            default: walk2_rot4<0>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 1: walk2_rot4<1, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 2: walk2_rot4<2, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 3: walk2_rot4<3, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 4: walk2_rot4<4, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 5: walk2_rot4<5, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 6: walk2_rot4<6, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 7: walk2_rot4<7, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            case 8: walk2_rot4<8, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
+            default: walk2_rot4<0, EXACT>(R, base, pitch, B, qw, piC, iC, hC, out); break;
         }
         const float nrm = h2q / (qw - hC);   // h^2/(2B)
 #pragma unroll
@@ -567,7 +568,7 @@ static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float
     float *partial = nsplit > 1 ? reinterpret_cast<float *>(T4 + (size_t)n * pitch) : nullptr;
     const unsigned nt = (unsigned)((n + 31) / 32);
     pad_rot4_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(img, P4, T4, n, pad, pitch);
-    fp_rot4_f32_kernel<<<dim3((nr4 + 127) / 128, 1, nsplit), 128, 0, st>>>(
+    (geo->exact ? fp_rot4_f32_kernel<true> : fp_rot4_f32_kernel<false>)<<<dim3((nr4 + 127) / 128, 1, nsplit), 128, 0, st>>>(
         geo->d_fp_order4, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P4, T4, pitch, pad, nr, nr4, sino,
         nsplit, partial);
     if (nsplit > 1)
@@ -612,7 +613,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
             cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nout * sizeof(float), st);
             if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
         }
-        fp_f32_kernel<false><<<dim3(grd.x, grd.y, nsplit), blk, 0, st>>>(
+        (geo->exact ? fp_f32_kernel<false, true> : fp_f32_kernel<false, false>)<<<dim3(grd.x, grd.y, nsplit), blk, 0, st>>>(
             geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + (size_t)batch * strideP,
             pitchP, pitchT, strideP, strideT, geo->pad, nr, (float *)sino, nsplit, partial);
         if (nsplit > 1) {
@@ -660,7 +661,7 @@ int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void 
         float *P = (float *)scratch, *Tt = P + (size_t)batch * strideP;
         pad_rows_kernel<float><<<grdr, blk, 0, st>>>((const float *)img, P, g.nx, g.ny, pad, pitchP, 0);
         pad_transpose_kernel<float><<<grdt, blkt, 0, st>>>((const float *)img, Tt, g.nx, g.ny, pad, pitchT, 0);
-        fp_f32_kernel<false><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P, Tt, pitchP, pitchT,
+        (geo->exact ? fp_f32_kernel<false, true> : fp_f32_kernel<false, false>)<<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P, Tt, pitchP, pitchT,
                                                   strideP, strideT, pad, nr, (float *)sino, 1, nullptr);
     } else {
         double *P = (double *)scratch, *Tt = P + (size_t)batch * strideP;
@@ -687,7 +688,7 @@ int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t st)
     cudaError_t e = cudaMallocAsync((void **)&out, (size_t)nr * sizeof(float), st);
     if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
     dim3 blk(128), grd((nr + 127) / 128, 1);
-    fp_f32_kernel<true><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + strideP, pitchP,
+    fp_f32_kernel<true, false><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + strideP, pitchP,
                                              pitchT, strideP, strideT, geo->pad, nr, out, 1, nullptr);
     std::vector<float> host(nr);
     e = cudaMemcpyAsync(host.data(), out, (size_t)nr * sizeof(float), cudaMemcpyDeviceToHost, st);

@@ -265,7 +265,18 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     geo->pad = pad;
     geo->kc_max = kc_max;
     geo->sym = sym ? 1 : 0;
-    geo->exact = (d->options & CNSF_OPT_EXACT_DIFFERENCES) ? 1 : 0;
+    // Window differences: the plain form loses about log2(B / tau') bits (B <= h); take the
+    // exact form when the thinnest effective blur of any entry -- the cell seen at the depth of
+    // the image point nearest the source (Eq. 17), tau itself for parallel rays -- falls below
+    // h/32, unless the caller chose.
+    {
+        double dtan_min = 1e300;
+        for (int j = 0; j < nd; ++j) dtan_min = std::min(dtan_min, celld[4 * j + 2]);
+        const double tau_min = g.par ? g.tau : std::max(g.dpo - g.rimg, 0.0) * dtan_min;
+        geo->exact = (d->options & CNSF_OPT_EXACT_DIFFERENCES) ? 1
+                     : (d->options & CNSF_OPT_PLAIN_DIFFERENCES) ? 0
+                                                                 : (tau_min < g.h / 32.0 ? 1 : 0);
+    }
     // Back-projector window: cells within kz*zs/D_n^2*(1.02 + 2h/D_n) + ke of the pixel's
     // projection.  W bounds |s_n - s_j| over the window (widest at the nearest pixel depth).
     if (g.par) {

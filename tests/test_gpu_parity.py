@@ -322,13 +322,14 @@ def test_largest_workloads_sampled(cnsf, which):
     assert abs(lhs - rhs) / abs(lhs) < 1e-5
 
 
-@pytest.mark.parametrize("tau", [0.05, 0.02])
+@pytest.mark.parametrize("tau", [0.05, 0.02, 0.005, 0.002])
 def test_thin_cells(cnsf, tau):
-    """Thin detector cells (tau -> 0, the limit in which Eq. 18 tends to Eq. 16): the FP32
-    window difference loses about log2(B / tau') bits (tau'/2 = 0.011 / 0.0045 mm at the
-    nearest pixel here), still within the FP32 bar; FP64 stays at 1e-12."""
+    """Thin detector cells (tau -> 0, the limit in which Eq. 18 tends to Eq. 16; tau'/2 down
+    to 0.00046 mm at the nearest pixel here): the geometry takes the exact window
+    differences (tau' < h/32) and FP32 stays within its bar; FP64 stays at 1e-12."""
     g = FanGeometry(nx=64, ny=64, n_views=45, n_det=128, det_width=tau)
     geom = cnsf.Geometry(g)
+    assert geom.paths["exact_differences"]
     img = phantom_for_config(1)
     y_ref = oracle.forward(g, img)
     for dt in (torch.float64, torch.float32):

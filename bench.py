@@ -35,8 +35,12 @@ WORKLOAD = ("512x512 FP32 random-ellipse phantom (20 ellipses, values [0,2], see
             "one forward + one back projection per step, batch 1")
 # FP32 operations of one non-zero entry as the formula is evaluated: s' (2), tau'/2 (1),
 # the window difference of the trapezoid antiderivatives (13), the division by tau' (2) and
-# the accumulation (1).  An FMA counts as one operation.
+# the accumulation (1).  An FMA counts as one operation.  This is the per-entry figure of
+# the roofline (the work of evaluating every entry of A once per projection).
 ALG_OPS_PER_ENTRY = 19
+# The quarter-turn kernels evaluate each distinct entry once for the four entries of A equal
+# to it and accumulate it four times: (19 - 1)/4 + 1 operations per entry of A executed.
+EXEC_OPS_PER_ENTRY_ROT4 = (ALG_OPS_PER_ENTRY - 1) / 4 + 1
 FP32_LANES_PER_SM = 128
 
 
@@ -99,7 +103,37 @@ class ClockSampler:
 KERNEL_SOURCES = {
     "fp_f32_kernel": ("forward.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
     "bp_f32_kernel": ("back.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
+    "fp_rot4_f32_kernel": ("forward.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
+    "bp_rot4_f32_kernel": ("back.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
 }
+
+# kernels one step launches on each path (the line and view parts are split at this size)
+STEP_KERNELS = {
+    True: ["pad_rot4_kernel", "fp_rot4_f32_kernel", "fp_sum_parts_kernel", "sino_pairs_rot4_kernel",
+           "bp_rot4_f32_kernel", "orbit_sum_kernel"],
+    False: ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "fp_sum_parts_kernel", "sino_pairs_kernel",
+            "sino_pairs_kernel", "bp_f32_kernel", "bp_sum_parts_kernel"],
+}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def _code_only(text: str) -> str:
@@ -306,8 +340,11 @@ def run_cnsf(args):
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
     fp_ms, bp_ms = statistics.mean(t_fp), statistics.mean(t_bp)
-    dom, dom_ms = ("fp_f32_kernel", fp_ms) if fp_ms >= bp_ms else ("bp_f32_kernel", bp_ms)
+    sym = geom.paths["symmetric"]
+    names = ("fp_rot4_f32_kernel", "bp_rot4_f32_kernel") if sym else ("fp_f32_kernel", "bp_f32_kernel")
+    dom, dom_ms = (names[0], fp_ms) if fp_ms >= bp_ms else (names[1], bp_ms)
     achieved = ALG_OPS_PER_ENTRY * nnz / (dom_ms * 1e-3)
+    exec_ops = EXEC_OPS_PER_ENTRY_ROT4 if sym else ALG_OPS_PER_ENTRY
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
             "frac": achieved / peak_ops, "traffic": _recorded_traffic(dom), "kernel": dom,
             "ops_per_entry": ALG_OPS_PER_ENTRY, "entries_per_launch": nnz,
@@ -315,7 +352,13 @@ def run_cnsf(args):
                           "(max SM clock of MEASURED_PEAKS.json); an FMA counts as one op",
             "fp_ms": fp_ms, "bp_ms": bp_ms,
             "fp_frac": ALG_OPS_PER_ENTRY * nnz / (fp_ms * 1e-3) / peak_ops,
-            "bp_frac": ALG_OPS_PER_ENTRY * nnz / (bp_ms * 1e-3) / peak_ops}
+            "bp_frac": ALG_OPS_PER_ENTRY * nnz / (bp_ms * 1e-3) / peak_ops,
+            "path": "quarter-turn symmetric (each distinct entry evaluated once for its 4 entries of A)" if sym
+                    else "general",
+            "executed_ops_per_entry": exec_ops,
+            "executed_frac": exec_ops * nnz / (dom_ms * 1e-3) / peak_ops,
+            "executed_fp_frac": exec_ops * nnz / (fp_ms * 1e-3) / peak_ops,
+            "executed_bp_frac": exec_ops * nnz / (bp_ms * 1e-3) / peak_ops}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -330,10 +373,16 @@ def run_cnsf(args):
                        "image -> pinned host; host clock around each step, synchronised"},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": 7 * args.steps,
-        "kernels_per_step": ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "fp_sum_parts_kernel",
-                             "sino_pairs_kernel", "bp_f32_kernel", "bp_sum_parts_kernel"],
+        "gpu_launches": len(STEP_KERNELS[sym]) * args.steps,
+        "kernels_per_step": STEP_KERNELS[sym],
     }
+    # share of the end-to-end step spent outside the device-timed projections (the image
+    # upload, the sinogram and image downloads, host launch work)
+    e2e_ms_step, dev_ms_step = e2e_total / args.steps, total_ms / args.steps
+    line["e2e"]["host_and_copy_share"] = max(0.0, (e2e_ms_step - dev_ms_step) / e2e_ms_step)
+    line["e2e"]["ms_per_step"] = e2e_ms_step
+    if world == 1:
+        line["general_kernels_512x720"] = bench_general(dev, img, nnz, peak_ops)
     if world == 1 and not args.no_extras:   # the extra lines are single-GPU measurements
         line["serving"] = bench_serving(args, dev)
         line["reconstruction_2048"] = bench_solvers(dev)
@@ -345,9 +394,15 @@ def run_cnsf(args):
         line["p50_recon_latency_s"] = line["serving"]["batched"].get("p50_s")
         line["p99_recon_latency_s"] = line["serving"]["batched"].get("p99_s")
     if world == 1 and not args.no_cpu_baseline:
+        import oracle
         r, dt, thr, desc = oracle_sample_rate(720)
+        # one core on a sample of the views (every 12th), scaled by the views it covers
+        oracle.set_num_threads(1)
+        r1, dt1, _, desc1 = oracle_sample_rate(60)
+        oracle.set_num_threads(thr)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc,
-                                "seconds": dt}
+                                "seconds": dt, "cpu_model": cpu_model(), "host_cpus": os.cpu_count(),
+                                "single_core": {"value": r1, "unit": UNIT, "sample": desc1, "seconds": dt1}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -356,6 +411,36 @@ def run_cnsf(args):
 
 
 # ---------------------------------------------------------------------------- extras
+def bench_general(dev, img, nnz, peak_ops, steps: int = 20):
+    """The same workload through the general kernels (the quarter-turn reuse switched off):
+    what every geometry without that symmetry gets.  Device time per direction (CUDA events,
+    L2 flushed between steps) and its fraction of the FP32 peak at 19 operations per entry."""
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import config_geometry
+    g = config_geometry(2)
+    geom = cnsf.Geometry(g, symmetry=False)
+    sino = cnsf.forward_project(geom, img)
+    back = cnsf.back_project(geom, sino)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps + 3)]
+    for k in range(steps + 3):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        cnsf.forward_project(geom, img, out=sino)
+        ev[k][1].record()
+        cnsf.back_project(geom, sino, out=back)
+        ev[k][2].record()
+    torch.cuda.synchronize()
+    fp_ms = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(3, steps + 3))
+    bp_ms = statistics.mean(ev[k][1].elapsed_time(ev[k][2]) for k in range(3, steps + 3))
+    return {"fp_ms": fp_ms, "bp_ms": bp_ms, "paths": geom.paths,
+            "updates_per_s": g.nx * g.ny * g.n_views / ((fp_ms + bp_ms) * 1e-3),
+            "fp_frac": ALG_OPS_PER_ENTRY * nnz / (fp_ms * 1e-3) / peak_ops,
+            "bp_frac": ALG_OPS_PER_ENTRY * nnz / (bp_ms * 1e-3) / peak_ops,
+            "kernels": ["fp_f32_kernel", "bp_f32_kernel"]}
+
+
 def bench_serving(args, dev):
     """Poisson arrivals (200 req/s) of CGLS reconstructions (20 iterations, FP32) with image
     sizes in {256, 512, 768, 1024}^2, views in {180, 360, 720, 1440}, 1.75 n cells, admitted

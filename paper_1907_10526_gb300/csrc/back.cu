@@ -39,6 +39,10 @@ struct BpArgs {
     float nk6;          // arc detector: -dg^2 / 6 (sine series)
     long long box_odd;  // offsets (floats) of the odd-aligned pair tables: 8 nv ceil(n_det/2)
     int cell_odd;       // and 8 ceil(n_det/2)
+    float s0, ds;       // centre of cell 0 and cell pitch (mm)
+    float idps;         // 1/D_ps (0 for parallel rays)
+    float ked;          // arc detector: tau'/2 per unit G (dtan / (2 dg))
+    float nk2;          // arc detector: -dg^2 / 2 (cosine series)
 };
 
 // The FP32 per-(tile, view) coefficients from the FP64 projection of the tile's reference point.
@@ -355,41 +359,145 @@ __global__ void sino_pairs_rot4_kernel(const float *__restrict__ y, const BoxF *
     }
 }
 
-// bp_view2_f32 for the four rotations: the same window and cell pairs; each pair's entries
-// for pixels a and b are applied to the four weighted sinogram pairs of the step and added
-// to ta[k], tb[k] (lanes: the two cells of the pair).
-template <bool ARC, bool EXACT>
-__device__ __forceinline__ void bp_view2_rot4(const BpPixel &Pa, const BpPixel &Pb, float hwc, int J, const BpArgs &a,
-                                              int nd, const float *__restrict__ y4row,
-                                              const float *__restrict__ y4orow, const float *__restrict__ boxrow,
-                                              const float *__restrict__ cell2, float2 (&ta)[4], float2 (&tb)[4])
+// The per-(quad, view) set-up shared by the four-rotation kernels and their span table:
+// pixel 0 from the tile coefficients and its neighbours by the per-pixel steps of D_n, y'
+// and the numerator (down a column (-hs, hc, b1), along a row (-hc, -hs, a1)); P1 is the
+// neighbour along the axis that moves the projection least (col: down the column), P2 the
+// other one, P3 both; a pixel outside the image takes pixel 0's window.
+struct QuadView {
+    BpPixel P0, P1, P2, P3;
+    float hwc;
+    bool col;
+};
+
+template <bool ARC>
+__device__ __forceinline__ QuadView quad_view_setup(const TileViewS<float> &T, float di, float dr, bool in1, bool in2,
+                                                    bool in3, const BpArgs &a)
+{
+    QuadView Q;
+    Q.col = fabsf(T.b1) <= fabsf(T.a1);   // pairs along a column
+    const bool col = Q.col;
+    const float Dn0 = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
+    const float yp0 = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
+    const float nu0 = ARC ? fmaf(T.a1, di, T.b1 * dr) : fmaf(T.a1, di, fmaf(T.b1, dr, T.rho));
+    const float sDn = col ? -T.hs : -T.hc, syp = col ? T.hc : -T.hs, snu = col ? T.b1 : T.a1;   // pair step
+    const float oDn = col ? -T.hc : -T.hs, oyp = col ? -T.hs : T.hc, onu = col ? T.a1 : T.b1;   // other step
+    Q.P0 = bp_pixel_f32<ARC>(T, Dn0, yp0, nu0, a);
+    Q.P1 = bp_pixel_f32<ARC>(T, Dn0 + sDn, yp0 + syp, nu0 + snu, a);
+    Q.P2 = bp_pixel_f32<ARC>(T, Dn0 + oDn, yp0 + oyp, nu0 + onu, a);
+    Q.P3 = bp_pixel_f32<ARC>(T, Dn0 + oDn + sDn, yp0 + oyp + syp, nu0 + onu + snu, a);
+    const bool inP1 = col ? in2 : in1, inP2 = col ? in1 : in2;
+    if (!inP1) Q.P1.sig = Q.P0.sig;
+    if (!inP2) Q.P2.sig = Q.P0.sig;
+    if (!in3) Q.P3.sig = Q.P0.sig;
+    Q.hwc = bp_quad_hwc(T, Dn0, yp0, a);
+    return Q;
+}
+
+// Absolute cells [g0, g1] of the union of two pixels' windows, clipped to the detector
+// (g0 > g1 when the window misses it).
+__device__ __forceinline__ void pair_window(const BpPixel &Pa, const BpPixel &Pb, float hwc, int J, int nd, int &g0,
+                                            int &g1)
 {
     const float lo = fminf(Pa.sig, Pb.sig) - hwc, hi = fmaxf(Pa.sig, Pb.sig) + hwc;
-    const int g0 = J + max((int)ceilf(lo), -J), g1 = J + min((int)floorf(hi), nd - 1 - J);
+    g0 = J + max((int)ceilf(lo), -J);
+    g1 = J + min((int)floorf(hi), nd - 1 - J);
+}
+
+// Per-pixel factors of the quarter-turn gather's merged pair table.  The blur of cell j at a
+// pixel of depth D_n and detector-axis coordinate y' is tau'_j/2 = D_n c1_j + y' c2_j with
+// c2_j = c1_j s_j / D_ps (flat detector, s_j = s_sigma - d ds for the cell d cells below the
+// pixel's projection s_sigma), so tau'_j/2 = c1_j (K - d L), K = D_n + y' s_sigma / D_ps,
+// L = y' ds / D_ps; parallel rays: K = 1, L = 0 (c1 = tau/2).  The flat and parallel gathers
+// carry d' = D_n d (s' = (ds/L_j) d') and L' = L / D_n.  Arc detector: tau'_j/2 =
+// (dtan/2) R cos(dg d), R the pixel's distance from the source, by its two-term series
+// E (1 - (dg d)^2 / 2), E = (dtan/2) R (the next term is below 1e-9 relative for dg d < 0.05).
+struct BpPixel4 {
+    BpPixel P;
+    float K, L;   // flat, parallel: K and L'; arc: E and unused
+};
+
+template <bool ARC>
+__device__ __forceinline__ BpPixel4 bp_pixel4(const BpPixel &P, int J, const BpArgs &a)
+{
+    BpPixel4 Q;
+    Q.P = P;
+    if (ARC) {
+        Q.K = P.G * a.ked;
+        Q.L = 0.f;
+    } else {
+        const float ssig = fmaf((float)J + P.sig, a.ds, a.s0);
+        Q.K = fmaf(P.yp * ssig, a.idps, P.Dn);
+        Q.L = P.yp * a.ds * a.idps * rcp_approx(P.Dn);
+    }
+    return Q;
+}
+
+// The two entries of one cell pair for one pixel from the merged entry A = (q | 1/C | ds/L |
+// c1, pairs) with p/C and -C/2 formed by the caller; d: flat and parallel d' = D_n d, arc d
+// (cells).  Without 2/B and h^2/4, as bp_pair_f32.
+template <bool ARC, bool EXACT>
+__device__ __forceinline__ float2 bp_pair_rot4(const BpPixel4 &Q, float2 d, const float (&A)[8], float2 piC, float2 nhC,
+                                               const BpArgs &a)
+{
+    const float2 ne1 = make_float2(-1.f, -1.f);
+    float2 xs, e;
+    if (ARC) {
+        const float2 d2 = __fmul2_rn(d, d);
+        xs = __fmul2_rn(__fmul2_rn(make_float2(Q.P.G, Q.P.G), d),
+                        __ffma2_rn(d2, make_float2(a.nk6, a.nk6), make_float2(1.f, 1.f)));
+        e = __fmul2_rn(make_float2(Q.K, Q.K), __ffma2_rn(d2, make_float2(a.nk2, a.nk2), make_float2(1.f, 1.f)));
+    } else {
+        xs = __fmul2_rn(make_float2(A[4], A[5]), d);
+        e = __fmul2_rn(make_float2(A[6], A[7]), __ffma2_rn(d, make_float2(-Q.L, -Q.L), make_float2(Q.K, Q.K)));
+    }
+    const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));   // |s'|
+    const float2 w = wdiff2p<EXACT>(x, e, ne1, make_float2(A[0], A[1]), piC, make_float2(A[2], A[3]), nhC);
+    return __fmul2_rn(w, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
+}
+
+// bp_view2_f32 for the four rotations: the same window and cell pairs, the pair's constants
+// in one merged 32-byte entry (ac) and its four rotations' weighted sinogram values in
+// another (y4); each pair's entries for pixels a and b are applied to the four rotations
+// and added to ta[k], tb[k] (lanes: the two cells of the pair).
+template <bool ARC, bool EXACT>
+__device__ __forceinline__ void bp_view2_rot4(const BpPixel4 &Qa, const BpPixel4 &Qb, float hwc, int J,
+                                              const BpArgs &a, int nd, const float *__restrict__ y4row,
+                                              const float *__restrict__ y4orow, const float *__restrict__ acrow,
+                                              long long ac_odd, float2 (&ta)[4], float2 (&tb)[4])
+{
+    int g0, g1;
+    pair_window(Qa.P, Qb.P, hwc, J, nd, g0, g1);
     const int odd = g0 & 1;
     const int m0 = g0 >> 1, m1 = (g1 - odd) >> 1;   // m0 > m1 when the window misses the detector
     if (odd) {   // pairs (2m + 1, 2m + 2)
-        boxrow += a.box_odd;
-        cell2 += a.cell_odd;
+        acrow += ac_odd;
         y4row = y4orow;
     }
     const float off = (float)(2 * m0 + odd - J);
-    float2 da = make_float2(Pa.sig - off, Pa.sig - off - 1.f), db = make_float2(Pb.sig - off, Pb.sig - off - 1.f);
-    const float2 m2 = make_float2(-2.f, -2.f);
+    // cell offsets of the two pixels; flat and parallel carry D_n d
+    const float sa = ARC ? 1.f : Qa.P.Dn, sb = ARC ? 1.f : Qb.P.Dn;
+    float2 da = make_float2(sa * (Qa.P.sig - off), sa * (Qa.P.sig - off - 1.f));
+    float2 db = make_float2(sb * (Qb.P.sig - off), sb * (Qb.P.sig - off - 1.f));
+    const float2 sta = make_float2(-2.f * sa, -2.f * sa), stb = make_float2(-2.f * sb, -2.f * sb);
+    const float2 m1f = make_float2(-1.f, -1.f), mh = make_float2(-0.5f, -0.5f);
     for (int m = m0; m <= m1; ++m) {
-        float A[8], C[8], Y[8];
-        ldg256(boxrow + 8 * m, A);    // q | p/C | 1/C | -C/2, pairs
-        ldg256(cell2 + 8 * m, C);     // ds/L | c1 | c2, pairs
+        float A[8], Y[8];
+        ldg256(acrow + 8 * m, A);     // q | 1/C | ds/L | c1, pairs
         ldg256(y4row + 8 * m, Y);     // y 2/B of the four rotations, pairs
-        const float2 wa = bp_pair_f32<ARC, EXACT>(Pa, da, A, C, a.nk6), wb = bp_pair_f32<ARC, EXACT>(Pb, db, A, C, a.nk6);
+        const float2 iC = make_float2(A[2], A[3]);
+        const float2 piC = __ffma2_rn(make_float2(A[0], A[1]), iC, m1f);                       // q/C - 1
+        const float2 nhC = __fmul2_rn(make_float2(rcp_approx(iC.x), rcp_approx(iC.y)), mh);    // -C/2
+        const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, piC, nhC, a);
+        const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, piC, nhC, a);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float2 yk = make_float2(Y[2 * k], Y[2 * k + 1]);
             ta[k] = __ffma2_rn(yk, wa, ta[k]);
             tb[k] = __ffma2_rn(yk, wb, tb[k]);
         }
-        da = __fadd2_rn(da, m2);
-        db = __fadd2_rn(db, m2);
+        da = __fadd2_rn(da, sta);
+        db = __fadd2_rn(db, stb);
     }
 }
 
@@ -398,8 +506,7 @@ __device__ __forceinline__ void bp_view2_rot4(const BpPixel &Pa, const BpPixel &
 // gathered along the axis that moves the projection least, the two pairings in two
 // branches (uniform over the block) so that every accumulator keeps its register.
 template <bool ARC, bool EXACT>
-__global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomConsts g, const float *__restrict__ box2,
-                                                                     const float *__restrict__ cell2,
+__global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomConsts g, const float *__restrict__ ac,
                                                                      const float *__restrict__ y4, BpArgs a,
                                                                      const int *__restrict__ order, int ntx, int nsplit,
                                                                      float *__restrict__ partial,
@@ -448,29 +555,18 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
             const int v = v0 + vv;
             const TileViewS<float> T = tv[vv];
             const int J = tj[vv];
-            const bool col = fabsf(T.b1) <= fabsf(T.a1);   // pairs along a column
-            const float *brow = box2 + 8 * (long long)v * ndh;
+            const float *arow = ac + 8 * (long long)v * ndh;
             const float *yrow = y4 + 8 * (long long)v * ndh, *yorow = y4 + 8 * (long long)(nv4 + v) * ndh;
-            const float Dn0 = fmaf(-T.hc, di, fmaf(-T.hs, dr, T.Dt));
-            const float yp0 = fmaf(-T.hs, di, fmaf(T.hc, dr, T.yt));
-            const float nu0 = ARC ? fmaf(T.a1, di, T.b1 * dr) : fmaf(T.a1, di, fmaf(T.b1, dr, T.rho));
-            const float sDn = col ? -T.hs : -T.hc, syp = col ? T.hc : -T.hs, snu = col ? T.b1 : T.a1;   // pair step
-            const float oDn = col ? -T.hc : -T.hs, oyp = col ? -T.hs : T.hc, onu = col ? T.a1 : T.b1;   // other step
-            const BpPixel P0 = bp_pixel_f32<ARC>(T, Dn0, yp0, nu0, a);
-            BpPixel P1 = bp_pixel_f32<ARC>(T, Dn0 + sDn, yp0 + syp, nu0 + snu, a);
-            BpPixel P2 = bp_pixel_f32<ARC>(T, Dn0 + oDn, yp0 + oyp, nu0 + onu, a);
-            BpPixel P3 = bp_pixel_f32<ARC>(T, Dn0 + oDn + sDn, yp0 + oyp + syp, nu0 + onu + snu, a);
-            const bool inP1 = col ? in2 : in1, inP2 = col ? in1 : in2;
-            if (!inP1) P1.sig = P0.sig;
-            if (!inP2) P2.sig = P0.sig;
-            if (!in3) P3.sig = P0.sig;
-            const float hwc = bp_quad_hwc(T, Dn0, yp0, a);
-            if (col) {   // P1 is quad pixel 2, P2 quad pixel 1
-                bp_view2_rot4<ARC, EXACT>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[2]);
-                bp_view2_rot4<ARC, EXACT>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[1], t[3]);
+            const long long ac_odd = 8LL * nv4 * ndh;
+            const QuadView Q = quad_view_setup<ARC>(T, di, dr, in1, in2, in3, a);
+            const BpPixel4 P0 = bp_pixel4<ARC>(Q.P0, J, a), P1 = bp_pixel4<ARC>(Q.P1, J, a);
+            const BpPixel4 P2 = bp_pixel4<ARC>(Q.P2, J, a), P3 = bp_pixel4<ARC>(Q.P3, J, a);
+            if (Q.col) {   // P1 is quad pixel 2, P2 quad pixel 1
+                bp_view2_rot4<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[0], t[2]);
+                bp_view2_rot4<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[1], t[3]);
             } else {
-                bp_view2_rot4<ARC, EXACT>(P0, P1, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[0], t[1]);
-                bp_view2_rot4<ARC, EXACT>(P2, P3, hwc, J, a, g.nd, yrow, yorow, brow, cell2, t[2], t[3]);
+                bp_view2_rot4<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[0], t[1]);
+                bp_view2_rot4<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[2], t[3]);
             }
         }
     }
@@ -652,18 +748,20 @@ static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *
     char *buf = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&buf, back_rot4_alloc_bytes(geo), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    const double dg = g.arc ? g.ds / g.dps : 0.0;
+    BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
+             (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0), 8LL * g.nv * ndh, 8 * ndh,
+             (float)g.s0, (float)g.ds, (float)(g.par ? 0.0 : 1.0 / g.dps),
+             (float)(g.arc ? tan(0.5 * g.tau / g.dps) / (g.ds / g.dps) : 0.0), (float)(g.arc ? -0.5 * (g.ds / g.dps) * (g.ds / g.dps) : 0.0)};
+    const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
     float *y4 = reinterpret_cast<float *>(buf), *partial = y4 + ny4;
     const long long npair = 2LL * nv4 * ndh;
     sino_pairs_rot4_kernel<<<(unsigned)std::min<long long>((npair + 255) / 256, 8192), 256, 0, st>>>(
         sino, geo->d_box, reinterpret_cast<float4 *>(y4), g.nv, g.nd);
-    const double dg = g.arc ? g.ds / g.dps : 0.0;
-    BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
-             (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0), 8LL * g.nv * ndh, 8 * ndh};
-    const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
     auto kern = g.arc ? (geo->exact ? bp_rot4_f32_kernel<true, true> : bp_rot4_f32_kernel<true, false>)
                       : (geo->exact ? bp_rot4_f32_kernel<false, true> : bp_rot4_f32_kernel<false, false>);
-    kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_box2, geo->d_cell2, y4, a, geo->d_bp_order,
-                                                                 ntx, nsplit, partial, geo->d_view_cs, geo->d_tv,
+    kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y4, a, geo->d_bp_order, ntx,
+                                                                 nsplit, partial, geo->d_view_cs, geo->d_tv,
                                                                  geo->d_tj);
     const unsigned nt = (unsigned)((n + 31) / 32);
     orbit_sum_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(partial, img, n, nsplit);
@@ -696,7 +794,9 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h),
                  (float)(0.25 * g.h * g.h),
                  (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0),
-                 8LL * g.nv * ((g.nd + 1) / 2), 8 * ((g.nd + 1) / 2)};
+                 8LL * g.nv * ((g.nd + 1) / 2), 8 * ((g.nd + 1) / 2),
+             (float)g.s0, (float)g.ds, (float)(g.par ? 0.0 : 1.0 / g.dps),
+             (float)(g.arc ? tan(0.5 * g.tau / g.dps) / (g.ds / g.dps) : 0.0), (float)(g.arc ? -0.5 * (g.ds / g.dps) * (g.ds / g.dps) : 0.0)};
         const int nsplit = bp_view_parts(geo, batch);
         float *partial = nullptr;
         const long long nimg = (long long)batch * g.nx * g.ny;

@@ -212,6 +212,11 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
                 S[2 + h] = c.c1;
                 S[4 + h] = c.c2;
             }
+    // The quarter-turn back projector's pair table for views v < V/4 (built below when the
+    // symmetry holds): per (parity, view, pair) one 32-byte entry (q, q', 1/C, 1/C', ds/L,
+    // ds/L', c1, c1') of cells 2m + o, 2m + o + 1; p/C = q/C - 1 and -C/2 = -1/(2 (1/C)) are
+    // formed in the kernel, and the blur needs no c2 there (c2 = c1 s_j / D_ps).
+    std::vector<float> ac;
     int pad = ((kc_max + 1 + 3) / 4) * 4;
     // The walk never leaves [-pad, na-1+pad]: windows that meet [0, na-1] are at most kc wide.
     for (size_t q = 0; q < nr; ++q) {
@@ -229,6 +234,20 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     // (lines x candidates).  Back: 16 x 16 tiles by descending mean magnification of their
     // centre over the views, 1/sqrt(D_po^2 - rho^2) for a tile at radius rho.
     const bool sym = quarter_turn_symmetric(d);
+    if (sym) {
+        const size_t np4 = (size_t)(nv / 4) * ndh;
+        ac.assign(2 * 8 * np4, 0.0f);
+        for (int o = 0; o < 2; ++o)
+            for (int k = 0; k < nv / 4; ++k)
+                for (int m = 0; m < ndh; ++m) {
+                    float *A = &ac[8 * (o * np4 + (size_t)k * ndh + m)];
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int j = std::min(2 * m + o + hh, nd - 1);
+                        const BoxF &b = box[(size_t)k * nd + j];
+                        A[hh] = b.q; A[2 + hh] = b.iC; A[4 + hh] = cellf[j].g1; A[6 + hh] = cellf[j].c1;
+                    }
+                }
+    }
     const size_t nr4 = sym ? (size_t)(nv / 4) * nd : 0;
     std::vector<int> fp_order((nr + 127) / 128), fp_order4((nr4 + 127) / 128), bp_order;
     {
@@ -316,6 +335,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         {(void **)&geo->d_fp_order, fp_order.data(), fp_order.size() * sizeof(int)},
         {(void **)&geo->d_bp_order, bp_order.data(), bp_order.size() * sizeof(int)},
         {(void **)&geo->d_fp_order4, fp_order4.data(), fp_order4.size() * sizeof(int)},
+        {(void **)&geo->d_ac, ac.data(), ac.size() * sizeof(float)},
     };
     for (const Up &u : ups) {
         if (u.bytes == 0) continue;
@@ -338,7 +358,7 @@ void destroy_geometry(cnsf_geometry *geo)
     if (!geo) return;
     void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray,
                     geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2, geo->d_tv, geo->d_tj,
-                    geo->d_fp_order4};
+                    geo->d_fp_order4, geo->d_ac};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete geo;

@@ -138,6 +138,11 @@ CNSF_API void cnsf_geometry_destroy(cnsf_geometry *geom);
  * cnsf_option).  Either pointer may be NULL. */
 CNSF_API int cnsf_geometry_paths(const cnsf_geometry *geom, int32_t *symmetric, int32_t *exact_differences);
 
+/* Device bytes the geometry's tables hold from creation to destruction (the paper has no
+ * counterpart; for callers that budget device memory, such as a scheduler caching several
+ * geometries).  *bytes is a host pointer.  CNSF_ERR_INVALID for a NULL argument. */
+CNSF_API int cnsf_geometry_device_bytes(const cnsf_geometry *geom, size_t *bytes);
+
 /* Sizes of a geometry: any output pointer may be NULL. */
 CNSF_API int cnsf_geometry_shape(const cnsf_geometry *geom, int32_t *n_x, int32_t *n_y, int32_t *n_views,
                         int32_t *n_det);
@@ -276,12 +281,15 @@ CNSF_API int cnsf_asd_pocs(const cnsf_geometry *const *subsets, int32_t n_subset
  *     batch * (n_y*(n_x + 2*pad) + n_x*(n_y + 2*pad)) * sizeof(element) <= 16 MiB,
  * pad being the geometry's padding (8 for 1 mm cells and pixels), e.g. batch <= 7 at
  * 512^2 FP32, batch 1 up to ~1400^2 FP32; larger requests return CNSF_ERR_UNSUPPORTED
- * and launch nothing.  The first call on a device looks up the array's device address
- * (which may load the library's device code); make that first call before any stream
- * capture.  Every call on a device shares the one array: calls whose work overlaps on
- * the GPU (different streams without ordering between them) race and may corrupt
- * each other's results.  The array keeps the last call's contents; nothing in it needs
- * clearing because each call rewrites every element it reads. */
+ * and launch nothing.  Every call looks up the array's device address for the current
+ * device (a host-side query; the first one on a device may load the library's device
+ * code, so make the first call before any stream capture).  Every call on a device shares
+ * the one array: calls whose work overlaps on the GPU (different streams without ordering
+ * between them) race and may corrupt each other's results.  The array keeps the last
+ * call's contents; nothing in it needs clearing because each call rewrites every element
+ * it reads.  It runs the general forward kernel with each ray's lines in one part (no
+ * partial sinograms to allocate) and without the quarter-turn reuse, so at large
+ * n_views x n_det it is several times slower than cnsf_forward_project. */
 CNSF_API int cnsf_forward_project_noalloc(const cnsf_geometry *geom, const void *image, void *sino,
                                           int32_t batch, int32_t dtype, void *stream);
 

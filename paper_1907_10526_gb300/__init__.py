@@ -87,6 +87,13 @@ class Geometry:
         return self._h
 
     @property
+    def device_bytes(self) -> int:
+        """Device memory held by this geometry's tables."""
+        n = ctypes.c_size_t()
+        check(lib.cnsf_geometry_device_bytes(self.handle, ctypes.byref(n)), "cnsf_geometry_device_bytes")
+        return int(n.value)
+
+    @property
     def paths(self) -> dict:
         """The evaluation paths of the FP32 single-image projections: ``symmetric`` (entries
         reused over the quarter turns) and ``exact_differences`` (window differences formed

@@ -45,6 +45,7 @@ _SIGNATURES = {
     "cnsf_geometry_destroy": (None, [_P]),
     "cnsf_geometry_shape": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int32)] * 4),
     "cnsf_geometry_paths": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int32)] * 2),
+    "cnsf_geometry_device_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "cnsf_forward_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_back_project": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),
     "cnsf_forward_project_ref": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P]),

@@ -91,6 +91,7 @@ int build_tile_view_table(cnsf_geometry *geo)
         geo->d_tj = nullptr;
         return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     }
+    geo->device_bytes += (size_t)n * (2 * sizeof(float4) + sizeof(int));
     tile_view_table_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256>>>(g, geo->d_view_cs, ntx,
                                                                                           ntx * nty, geo->d_tv,
                                                                                           geo->d_tj);

@@ -80,6 +80,13 @@ int cnsf_geometry_paths(const cnsf_geometry *geom, int32_t *symmetric, int32_t *
     return CNSF_OK;
 }
 
+int cnsf_geometry_device_bytes(const cnsf_geometry *geom, size_t *bytes)
+{
+    if (!geom || !bytes) return CNSF_ERR_INVALID;
+    *bytes = geom->device_bytes;
+    return CNSF_OK;
+}
+
 int cnsf_geometry_shape(const cnsf_geometry *geom, int32_t *n_x, int32_t *n_y, int32_t *n_views, int32_t *n_det)
 {
     if (!geom) return CNSF_ERR_INVALID;

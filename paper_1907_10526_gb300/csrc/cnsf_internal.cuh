@@ -288,6 +288,7 @@ struct cnsf_geometry {
     int device;
     int pad;                  // zero columns on each side of the padded image copies
     int kc_max;               // largest candidate count per walked line
+    size_t device_bytes;      // device memory held by the tables below
     int sym;                  // 1: FP32 single-image projections reuse entries over the quarter turn
     int exact;                // 1: FP32 kernels form window differences piece by piece
     cnsf::BpWindow bw;        // back projector cell window

@@ -346,6 +346,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         }
         e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { destroy_geometry(geo); return record_cuda_error(e); }
+        geo->device_bytes += u.bytes;
     }
     st = build_tile_view_table(geo);
     if (st != CNSF_OK) { destroy_geometry(geo); return st; }

@@ -9,8 +9,6 @@
 // the library and stays reserved until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "cnsf.h"
 #include "cnsf_internal.cuh"
 #include "cnsf_runtime.h"
@@ -19,23 +17,15 @@ namespace cnsf {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[CNSF_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_noalloc_mutex;
-static void *g_noalloc_addr[kMaxDevices];   // device address of the array, per device
-
-// Once per device, with that device current: the array's name in host code is only a
-// host-side stand-in, so its device address is looked up here and passed to the kernels.
-static int noalloc_scratch_address(int dev, void **addr)
+// The array's name in host code is only a host-side stand-in, so its device address is
+// looked up for the current device (a host-side query, repeated on every call so that a
+// device reset that reloads the module cannot leave a stale address behind).
+static int noalloc_scratch_address(void **addr)
 {
-    if (dev < 0 || dev >= kMaxDevices) return CNSF_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return record_cuda_error(e);
-        g_noalloc_addr[dev] = p;
-    }
-    *addr = g_noalloc_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return record_cuda_error(e);
+    *addr = p;
     return CNSF_OK;
 }
 
@@ -58,7 +48,7 @@ extern "C" CNSF_API int cnsf_forward_project_noalloc(const cnsf_geometry *geom, 
         if (forward_scratch_bytes(geom, batch, dtype) > (size_t)CNSF_NOALLOC_SCRATCH_BYTES)
             return CNSF_ERR_UNSUPPORTED;
         void *scratch = nullptr;
-        int s = noalloc_scratch_address(dev, &scratch);
+        int s = noalloc_scratch_address(&scratch);
         if (s != CNSF_OK) return s;
         // The padding kernels write every element of the copies they use, zeros included,
         // so whatever an earlier call left in the array never reaches the result.

@@ -2,10 +2,13 @@
 
 Requests (an n x n image, V views, a sinogram, a CGLS iteration count) arrive over time.
 The scheduler admits work in arrival order whenever a stream slot is free and its device
-footprint fits the HBM budget; every admitted job runs on its own CUDA stream (sinogram
-upload, CGLS iterations through the C library, image download), so the work of requests
-that arrive while others run overlaps on the device.  A finished job frees its slot and
-memory for the next one.
+footprint fits the HBM budget beside the active jobs and the geometries held in the cache
+(each geometry's device tables, cnsf_geometry_device_bytes); when it does not fit, idle
+cached geometries -- none that an active job or the next job uses -- are released, least
+recently used first, and rebuilt if a later request needs them.  Every admitted job runs
+on its own CUDA stream (sinogram upload, CGLS iterations through the C library, image
+download), so the work of requests that arrive while others run overlaps on the device.
+A finished job frees its slot and memory for the next one.
 
 Modes:
 * ``"batched"`` (continuous batching): a job is the oldest waiting request together with
@@ -74,6 +77,12 @@ class ReconServer:
         self.max_active = int(max_active)
         self.max_batch = int(max_batch)
         self.geoms: Dict[Tuple[int, int], Geometry] = {}
+        self.geom_bytes: Dict[Tuple[int, int], int] = {}
+        self.geom_create_s: Dict[Tuple[int, int], float] = {}   # first (cold) build of each shape
+        self.geom_rebuilds = 0
+        self._lru: Dict[Tuple[int, int], int] = {}
+        self._tick = 0
+        self._active_shapes: Dict[Tuple[int, int], int] = {}
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.max_active)]
 
     # ------------------------------------------------------------------ set-up
@@ -81,10 +90,41 @@ class ReconServer:
         key = (n, n_views)
         g = self.geoms.get(key)
         if g is None:
+            t0 = time.perf_counter()
             with torch.cuda.device(self.device):
                 g = Geometry(serving_geometry_desc(n, n_views), device=self.device)
+            if key in self.geom_create_s:
+                self.geom_rebuilds += 1
+            else:
+                self.geom_create_s[key] = time.perf_counter() - t0
             self.geoms[key] = g
+            self.geom_bytes[key] = g.device_bytes
+        self._tick += 1
+        self._lru[key] = self._tick
         return g
+
+    def resident_bytes(self) -> int:
+        """Device bytes of the geometries held in the cache."""
+        return sum(self.geom_bytes.values())
+
+    def _evict(self, key) -> None:
+        g = self.geoms.pop(key, None)
+        self.geom_bytes.pop(key, None)
+        self._lru.pop(key, None)
+        if g is not None:
+            g.close()
+
+    def _fits(self, used: int, nbytes: int, keep) -> bool:
+        """Whether nbytes more fit beside the active jobs (used) and the cached geometries,
+        releasing idle cached geometries (least recently used first, none in keep) as
+        needed."""
+        while used + self.resident_bytes() + nbytes > self.budget:
+            idle = sorted((k for k in self.geom_bytes if k not in keep and not self._active_shapes.get(k)),
+                          key=lambda k: self._lru.get(k, 0))
+            if not idle:
+                return False
+            self._evict(idle[0])
+        return True
 
     def footprint(self, n: int, n_views: int) -> int:
         """Device bytes a request holds while active: sinogram, image, solver workspace
@@ -107,19 +147,27 @@ class ReconServer:
     # ------------------------------------------------------------------ serving
     def _take_job(self, queue: deque, mode: str, used: int):
         """The next job from the head of the queue: (requests, bytes), None to wait for
-        memory, or a rejection."""
+        memory, or a rejection.  Building the head's geometry is part of admission: when
+        its tables do not fit beside the active jobs even after idle geometries are
+        released, it is released again and the head waits."""
         r = queue[0]
+        key = (r.n, r.n_views)
+        one = self.footprint(r.n, r.n_views) if mode != "batched" else self.batch_footprint(r.n, r.n_views, 1)
+        gbytes = self.geom_bytes.get(key, 0)   # the job's own geometry (built above) stays resident
+        if one + gbytes > self.budget:         # never fits, even alone
+            if not self._active_shapes.get(key):
+                self._evict(key)
+            return "reject", [r], one
+        if not self._fits(used, 0, {key}):    # the head's tables alone do not fit yet
+            if not self._active_shapes.get(key):
+                self._evict(key)
+            return None
         if mode != "batched":
-            nbytes = self.footprint(r.n, r.n_views)
-            if nbytes > self.budget:
-                return "reject", [r], nbytes
-            if used + nbytes > self.budget:
+            if not self._fits(used, one, {key}):
                 return None
-            return "run", [r], nbytes
+            return "run", [r], one
         same = [q for q in queue if (q.n, q.n_views, q.iters) == (r.n, r.n_views, r.iters)][:self.max_batch]
-        if self.batch_footprint(r.n, r.n_views, 1) > self.budget:
-            return "reject", [r], 0
-        while same and used + self.batch_footprint(r.n, r.n_views, len(same)) > self.budget:
+        while same and not self._fits(used, self.batch_footprint(r.n, r.n_views, len(same)), {key}):
             same.pop()
         if not same:
             return None
@@ -160,8 +208,13 @@ class ReconServer:
             raise ValueError(f"unknown mode {mode!r}")
         dev = self.device
         reqs = sorted(requests, key=lambda r: (r.arrival_s, r.rid))
+        self._active_shapes = {}
         for r in reqs:
-            self.geometry(r.n, r.n_views)          # geometries are built before the clock starts
+            # geometries are built before the clock starts (their cold build times are in
+            # geom_create_s), as many as the budget holds; one released to make room is
+            # rebuilt inside the timed run when a request needs it
+            self.geometry(r.n, r.n_views)
+            self._fits(0, 0, {(r.n, r.n_views)})
         pending = deque(reqs)
         queue: deque = deque()
         active = {}                                # slot -> (job, done event, buffers, bytes)
@@ -192,6 +245,8 @@ class ReconServer:
                         res.latency_s = done - r.arrival_s
                         res.image = bufs["outs"][k] if keep_images else None
                     used -= nbytes
+                    key = (job[0].n, job[0].n_views)
+                    self._active_shapes[key] -= 1
                     del active[slot]
                     free_slots.append(slot)
                     progressed = True
@@ -208,6 +263,8 @@ class ReconServer:
                     progressed = True
                     continue
                 slot = free_slots.pop()
+                key = (job[0].n, job[0].n_views)
+                self._active_shapes[key] = self._active_shapes.get(key, 0) + 1
                 ev, bufs = self._launch(job, mode, self.streams[slot])
                 admit = time.perf_counter() - t0
                 for r in job:
@@ -215,7 +272,7 @@ class ReconServer:
                 active[slot] = (job, ev, bufs, nbytes)
                 self.batch_sizes.append(len(job))
                 used += nbytes
-                self.max_used = max(self.max_used, used)
+                self.max_used = max(self.max_used, used + self.resident_bytes())
                 self.max_concurrent = max(self.max_concurrent, len(active))
                 progressed = True
                 if mode == "sequential":

@@ -67,7 +67,13 @@ def test_invalid_geometries_refused_without_gpu():
     ang = (ctypes.c_double * 4)(0.0, 0.5, nan, 1.5)
     d = GeometryDesc(8, 8, 1.0, 0, 0, 4, ang, 8, 1, 1, 0, 30, 60, 0)
     assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
+    # unknown option bits, and both window-difference forms at once, are refused
+    for opt in (8, 1 << 20, 2 | 4):
+        d = GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 30, 60, 0, opt)
+        assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
     # queries refuse missing arguments before touching a device
+    assert lib.cnsf_geometry_paths(None, None, None) == CNSF_ERR_INVALID
+    assert lib.cnsf_geometry_device_bytes(None, None) == CNSF_ERR_INVALID
     n = ctypes.c_size_t()
     assert lib.cnsf_projection_scratch_bytes(None, 0, 1, 0, ctypes.byref(n)) == CNSF_ERR_INVALID
     assert lib.cnsf_plan_create(None, 0, None, None, 1, 0, None) == CNSF_ERR_INVALID

@@ -41,20 +41,38 @@ def test_sequential_and_continuous_agree_and_replay(served):
     assert s["completed"] == len(reqs) and s["p99_s"] >= s["p50_s"] > 0
 
 
+def _need(server, r, batched=False):
+    """A request's own bytes: its job's footprint and its geometry's device tables."""
+    fp = server.batch_footprint(r.n, r.n_views, 1) if batched else server.footprint(r.n, r.n_views)
+    return fp + server.geometry(r.n, r.n_views).device_bytes
+
+
 def test_admission_by_footprint(served):
+    """Admission counts the active jobs and the cached geometries' tables: under a budget of
+    1.5x the smallest request's need nothing runs beside it, larger requests are rejected, and
+    the budget is never exceeded (idle geometries are released to make room)."""
     serve, server, reqs = served
-    small = min(reqs, key=lambda r: r.n * r.n_views)
-    one = server.footprint(small.n, small.n_views)
-    tight = serve.ReconServer(hbm_budget_bytes=int(one * 1.5), max_active=4)
+    small = min(reqs, key=lambda r: _need(server, r))
+    tight = serve.ReconServer(hbm_budget_bytes=int(_need(server, small) * 1.5), max_active=4)
     res = tight.run(reqs, mode="continuous")
+    resident = tight.resident_bytes()
     for r, x in zip(reqs, res):
-        if tight.footprint(r.n, r.n_views) > tight.budget:
+        if _need(tight, r) > tight.budget:
             assert x.status.startswith("rejected")
         else:
             assert x.status == "ok"
     assert tight.max_used <= tight.budget
-    assert tight.max_concurrent == 1               # 1.5 footprints: never two at once
+    assert resident <= tight.budget
     assert any(x.status == "ok" for x in res)
+
+
+def test_geometry_tables_counted(served):
+    serve, server, reqs = served
+    keys = sorted({(r.n, r.n_views) for r in reqs})
+    for k in keys:
+        assert server.geometry(*k).device_bytes > 0
+    assert server.resident_bytes() == sum(server.geometry(*k).device_bytes for k in keys)
+    assert set(server.geom_create_s) >= set(keys) and all(t > 0 for t in server.geom_create_s.values())
 
 
 def test_batched_results_independent_of_the_batch(served):
@@ -108,13 +126,14 @@ def test_batched_admission_by_footprint(served):
     budget is never exceeded, and every request is served or rejected by its own size."""
     serve, server, reqs = served
     burst = [serve.ReconRequest(r.rid, 1e-6 * k, r.n, r.n_views, r.sino, r.iters) for k, r in enumerate(reqs)]
-    small = min(burst, key=lambda r: r.n * r.n_views)
-    budget = int(server.batch_footprint(small.n, small.n_views, 2) * 1.2)
+    small = min(burst, key=lambda r: _need(server, r, batched=True))
+    budget = int((server.batch_footprint(small.n, small.n_views, 2) +
+                  server.geometry(small.n, small.n_views).device_bytes) * 1.2)
     tight = serve.ReconServer(hbm_budget_bytes=budget, max_active=4)
     res = tight.run(burst, mode="batched")
     assert tight.max_used <= budget
     for r, x in zip(burst, res):
-        if tight.batch_footprint(r.n, r.n_views, 1) > budget:
+        if _need(tight, r, batched=True) > budget:
             assert x.status.startswith("rejected")
         else:
             assert x.status == "ok"

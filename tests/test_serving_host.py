@@ -34,7 +34,18 @@ def _host_server(budget, max_batch=4, fp=None, bfp=None):
     s.budget, s.max_batch, s.max_active = budget, max_batch, 8
     s.footprint = fp or (lambda n, v: n * 10)
     s.batch_footprint = bfp or (lambda n, v, b: n * 10 * b + 5)
+    s.geoms, s.geom_bytes, s._lru, s._active_shapes, s._tick = {}, {}, {}, {}, 0
     return s
+
+
+def _cache(s, shapes):
+    """Put geometries of the given (shape: bytes) in the fake server's cache, oldest first."""
+    class _G:
+        def close(self):
+            pass
+    for key, nbytes in shapes.items():
+        s._tick += 1
+        s.geoms[key], s.geom_bytes[key], s._lru[key] = _G(), nbytes, s._tick
 
 
 def _req(rid, n, v, iters=20):
@@ -73,3 +84,30 @@ def test_admission_batch_shrinks_to_the_memory_left():
     big = _host_server(budget=900, max_batch=8)
     kind, job, _ = big._take_job(deque([_req(0, 100, 180)]), "batched", used=0)
     assert kind == "reject" and [r.rid for r in job] == [0]
+
+
+def test_admission_counts_cached_geometries_and_evicts_idle_ones():
+    """A job fits beside the active jobs and the cached geometries' tables; idle geometries
+    are released least recently used first, never the job's own or an active job's."""
+    from collections import deque
+    s = _host_server(budget=1000)
+    _cache(s, {(10, 180): 300, (20, 180): 200, (50, 180): 100, (30, 180): 150})
+    s._active_shapes = {(20, 180): 1}
+    q = deque([_req(0, 50, 180)])                                  # footprint 500
+    assert s._take_job(q, "continuous", used=50) == ("run", [q[0]], 500)
+    # 50 + 750 + 500 > 1000: the oldest idle geometry (10, 180) went, and that was enough
+    assert sorted(s.geom_bytes) == [(20, 180), (30, 180), (50, 180)]
+    # with every other geometry busy or needed, the job waits rather than evicting
+    s._active_shapes = {(20, 180): 1, (30, 180): 1}
+    assert s._take_job(q, "continuous", used=300) is None
+    assert sorted(s.geom_bytes) == [(20, 180), (30, 180), (50, 180)]
+    # more room needed: idle geometries go oldest first until the job fits
+    s._active_shapes = {(20, 180): 1}
+    _cache(s, {(40, 180): 100})
+    assert s._take_job(q, "continuous", used=200) == ("run", [q[0]], 500)
+    assert sorted(s.geom_bytes) == [(20, 180), (50, 180)]
+    # a request that cannot fit even beside its own geometry alone is rejected
+    big = _host_server(budget=1000)
+    _cache(big, {(90, 180): 200})
+    kind, job, _ = big._take_job(deque([_req(1, 90, 180)]), "continuous", used=0)
+    assert kind == "reject"

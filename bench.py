@@ -38,9 +38,15 @@ WORKLOAD = ("512x512 FP32 random-ellipse phantom (20 ellipses, values [0,2], see
 # the accumulation (1).  An FMA counts as one operation.  This is the per-entry figure of
 # the roofline (the work of evaluating every entry of A once per projection).
 ALG_OPS_PER_ENTRY = 19
-# The quarter-turn kernels evaluate each distinct entry once for the four entries of A equal
-# to it and accumulate it four times: (19 - 1)/4 + 1 operations per entry of A executed.
-EXEC_OPS_PER_ENTRY_ROT4 = (ALG_OPS_PER_ENTRY - 1) / 4 + 1
+# The symmetric kernels evaluate each distinct entry once for the entries of A equal to it
+# (those of the views 0 .. V/4 - 1 with the quarter turns, 0 .. V/8 with the reflections as
+# well) and accumulate it into each: (19 - 1) (evaluated views / V) + 1 operations per entry
+# of A executed.
+
+
+def exec_ops_per_entry(order: int, n_views: int) -> float:
+    evaluated = {1: n_views, 4: n_views // 4, 8: n_views // 8 + 1}[order]
+    return (ALG_OPS_PER_ENTRY - 1) * evaluated / n_views + 1
 FP32_LANES_PER_SM = 128
 
 
@@ -105,15 +111,22 @@ KERNEL_SOURCES = {
     "bp_f32_kernel": ("back.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
     "fp_rot4_f32_kernel": ("forward.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
     "bp_rot4_f32_kernel": ("back.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
+    "fp_rot8_f32_kernel": ("forward.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
+    "bp_rot8_f32_kernel": ("back.cu", "footprint.cuh", "cnsf_internal.cuh", "geometry.cu"),
 }
 
-# kernels one step launches on each path (the line and view parts are split at this size)
+# kernels one step launches on each path, by symmetry order (the line and view parts are
+# split at this size)
 STEP_KERNELS = {
-    True: ["pad_rot4_kernel", "fp_rot4_f32_kernel", "fp_sum_parts_kernel", "sino_pairs_rot4_kernel",
-           "bp_rot4_f32_kernel", "orbit_sum_kernel"],
-    False: ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "fp_sum_parts_kernel", "sino_pairs_kernel",
-            "sino_pairs_kernel", "bp_f32_kernel", "bp_sum_parts_kernel"],
+    8: ["pad_rot8_kernel", "fp_rot8_f32_kernel", "fp_sum_parts_kernel", "sino_pairs_rot8_kernel",
+        "bp_rot8_f32_kernel", "orbit_sum8_kernel"],
+    4: ["pad_rot4_kernel", "fp_rot4_f32_kernel", "fp_sum_parts_kernel", "sino_pairs_rot4_kernel",
+        "bp_rot4_f32_kernel", "orbit_sum_kernel"],
+    1: ["pad_rows_kernel", "pad_transpose_kernel", "fp_f32_kernel", "fp_sum_parts_kernel", "sino_pairs_kernel",
+        "sino_pairs_kernel", "bp_f32_kernel", "bp_sum_parts_kernel"],
 }
+KERNEL_NAMES = {8: ("fp_rot8_f32_kernel", "bp_rot8_f32_kernel"), 4: ("fp_rot4_f32_kernel", "bp_rot4_f32_kernel"),
+                1: ("fp_f32_kernel", "bp_f32_kernel")}
 
 
 def cpu_model() -> str:
@@ -340,11 +353,11 @@ def run_cnsf(args):
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
     fp_ms, bp_ms = statistics.mean(t_fp), statistics.mean(t_bp)
-    sym = geom.paths["symmetric"]
-    names = ("fp_rot4_f32_kernel", "bp_rot4_f32_kernel") if sym else ("fp_f32_kernel", "bp_f32_kernel")
+    order = geom.paths["symmetry_order"]
+    names = KERNEL_NAMES[order]
     dom, dom_ms = (names[0], fp_ms) if fp_ms >= bp_ms else (names[1], bp_ms)
     achieved = ALG_OPS_PER_ENTRY * nnz / (dom_ms * 1e-3)
-    exec_ops = EXEC_OPS_PER_ENTRY_ROT4 if sym else ALG_OPS_PER_ENTRY
+    exec_ops = exec_ops_per_entry(order, g.n_views)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
             "frac": achieved / peak_ops, "traffic": _recorded_traffic(dom), "kernel": dom,
             "ops_per_entry": ALG_OPS_PER_ENTRY, "entries_per_launch": nnz,
@@ -353,8 +366,10 @@ def run_cnsf(args):
             "fp_ms": fp_ms, "bp_ms": bp_ms,
             "fp_frac": ALG_OPS_PER_ENTRY * nnz / (fp_ms * 1e-3) / peak_ops,
             "bp_frac": ALG_OPS_PER_ENTRY * nnz / (bp_ms * 1e-3) / peak_ops,
-            "path": "quarter-turn symmetric (each distinct entry evaluated once for its 4 entries of A)" if sym
-                    else "general",
+            "path": {8: "quarter turns and reflections (each distinct entry evaluated once for the 8 entries "
+                        "of A equal to it; 4 at views 0 and 90)",
+                     4: "quarter turns (each distinct entry evaluated once for its 4 entries of A)",
+                     1: "general"}[order],
             "executed_ops_per_entry": exec_ops,
             "executed_frac": exec_ops * nnz / (dom_ms * 1e-3) / peak_ops,
             "executed_fp_frac": exec_ops * nnz / (fp_ms * 1e-3) / peak_ops,
@@ -373,8 +388,8 @@ def run_cnsf(args):
                        "image -> pinned host; host clock around each step, synchronised"},
         "roofline": roof,
         "clocks": clocks,
-        "gpu_launches": len(STEP_KERNELS[sym]) * args.steps,
-        "kernels_per_step": STEP_KERNELS[sym],
+        "gpu_launches": len(STEP_KERNELS[order]) * args.steps,
+        "kernels_per_step": STEP_KERNELS[order],
     }
     # share of the end-to-end step spent outside the device-timed projections (the image
     # upload, the sinogram and image downloads, host launch work)

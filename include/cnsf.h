@@ -102,7 +102,13 @@ typedef struct {
  *     the pixel lattice onto itself, and so every entry a(v + k n_views/4, j, n) equals
  *     a(v, j, n turned back by k quarter turns).  The FP32 single-image projections then
  *     evaluate each distinct entry once and apply it to the four (view, pixel) pairs it
- *     belongs to.  Results agree with the general kernels to FP32 rounding.
+ *     belongs to.  When moreover the detector is centred (det_offset = 0) and the views are
+ *     closed under reflection (angles_rad[(n_views - k) mod n_views] = -angles_rad[k] to
+ *     1e-12 rad, true of the default angles), mirroring the acquisition of view v in the x
+ *     axis gives view -v with cell j at n_det - 1 - j and pixel row r at n_y - 1 - r, so each
+ *     distinct entry of the views 0 .. n_views/8 serves eight entries of A (four at the two
+ *     views that are their own mirror images); CNSF_OPT_NO_REFLECTION keeps to the quarter
+ *     turns.  Results agree with the general kernels to FP32 rounding.
  *   CNSF_OPT_EXACT_DIFFERENCES / CNSF_OPT_PLAIN_DIFFERENCES: how the FP32 kernels form the
  *     window difference of Eq. (18), B H(s'+tau'/2) - B H(s'-tau'/2) (H the antiderivative of
  *     the footprint trapezoid).  PLAIN subtracts the two antiderivative values (relative error
@@ -115,7 +121,8 @@ typedef struct {
 typedef enum {
     CNSF_OPT_NO_SYMMETRY = 1,
     CNSF_OPT_EXACT_DIFFERENCES = 2,
-    CNSF_OPT_PLAIN_DIFFERENCES = 4
+    CNSF_OPT_PLAIN_DIFFERENCES = 4,
+    CNSF_OPT_NO_REFLECTION = 8
 } cnsf_option;
 
 /* Build a geometry and its device tables on the current device (Sec. II.A and
@@ -133,7 +140,8 @@ CNSF_API int cnsf_geometry_create(const cnsf_geometry_desc *desc, cnsf_geometry 
 CNSF_API void cnsf_geometry_destroy(cnsf_geometry *geom);
 
 /* The evaluation paths a geometry's FP32 single-image projections take (the paper has no
- * counterpart): *symmetric = 1 when entries are reused across the quarter-turn symmetry,
+ * counterpart): *symmetric = the number of entries of A each evaluated entry serves -- 1
+ * (no symmetry used), 4 (quarter turns) or 8 (quarter turns and reflections);
  * *exact_differences = 1 when the window differences are formed piece by piece (see
  * cnsf_option).  Either pointer may be NULL. */
 CNSF_API int cnsf_geometry_paths(const cnsf_geometry *geom, int32_t *symmetric, int32_t *exact_differences);

@@ -15,8 +15,9 @@ from typing import Optional
 
 import torch
 
-from ._lib import (CNSF_DETECTOR, CNSF_F32, CNSF_F64, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_NO_SYMMETRY,  # noqa: F401
-                   CNSF_OPT_PLAIN_DIFFERENCES, AsdPocsParams, CnsfError, GeometryDesc, check, lib)
+from ._lib import (CNSF_DETECTOR, CNSF_F32, CNSF_F64, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_NO_REFLECTION,  # noqa: F401
+                   CNSF_OPT_NO_SYMMETRY, CNSF_OPT_PLAIN_DIFFERENCES, AsdPocsParams, CnsfError, GeometryDesc, check,
+                   lib)
 
 __all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
            "count_nonzeros", "forward_project_noalloc", "asd_pocs", "Plan",
@@ -48,13 +49,15 @@ class Geometry:
 
     ``symmetry`` (default True) lets the FP32 single-image projections reuse each entry over
     the quarter turns of the acquisition when it has that symmetry (square image centred on
-    the rotation axis, views closed under a quarter turn); ``differences`` ("auto", "plain"
+    the rotation axis, views closed under a quarter turn) and over its reflections as well
+    (centred detector, views closed under theta -> -theta); "rotations" keeps to the quarter
+    turns, False uses no symmetry; ``differences`` ("auto", "plain"
     or "exact") selects how the FP32 kernels form the window difference of Eq. (18) (see
     ``cnsf_option`` in include/cnsf.h).  Neither changes the operator; ``paths`` reports the
     choice the library made.
     """
 
-    def __init__(self, desc=None, device=None, symmetry: bool = True, differences: str = "auto", **kw):
+    def __init__(self, desc=None, device=None, symmetry=True, differences: str = "auto", **kw):
         if desc is None:
             from types import SimpleNamespace
             base = dict(pixel=1.0, det_spacing=1.0, det_width=1.0, d_po=500.0, d_ps=1000.0,
@@ -76,7 +79,7 @@ class Geometry:
                          ctypes.cast(self._angles, ctypes.POINTER(ctypes.c_double)) if self._angles else None,
                          self.n_det, float(desc.det_spacing), float(desc.det_width), float(desc.det_offset),
                          float(desc.d_po), float(desc.d_ps), CNSF_DETECTOR[getattr(desc, "detector", "flat")],
-                         (0 if symmetry else CNSF_OPT_NO_SYMMETRY) |
+                         {True: 0, "rotations": CNSF_OPT_NO_REFLECTION, False: CNSF_OPT_NO_SYMMETRY}[symmetry] |
                          {"auto": 0, "plain": CNSF_OPT_PLAIN_DIFFERENCES, "exact": CNSF_OPT_EXACT_DIFFERENCES}[differences])
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -96,11 +99,12 @@ class Geometry:
     @property
     def paths(self) -> dict:
         """The evaluation paths of the FP32 single-image projections: ``symmetric`` (entries
-        reused over the quarter turns) and ``exact_differences`` (window differences formed
-        piece by piece)."""
+        reused over the acquisition's symmetries), ``symmetry_order`` (entries of A each
+        evaluated entry serves: 1, 4 or 8) and ``exact_differences`` (window differences
+        formed piece by piece)."""
         sym, ex = ctypes.c_int32(), ctypes.c_int32()
         check(lib.cnsf_geometry_paths(self.handle, ctypes.byref(sym), ctypes.byref(ex)), "cnsf_geometry_paths")
-        return {"symmetric": bool(sym.value), "exact_differences": bool(ex.value)}
+        return {"symmetric": sym.value > 1, "symmetry_order": int(sym.value), "exact_differences": bool(ex.value)}
 
     def view_angles(self):
         """The view angles (rad): the given ones, else 2 pi k / n_views."""

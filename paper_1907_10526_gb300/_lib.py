@@ -37,7 +37,7 @@ class AsdPocsParams(ctypes.Structure):
 CNSF_OK, CNSF_ERR_INVALID, CNSF_ERR_CUDA, CNSF_ERR_NOMEM, CNSF_ERR_UNSUPPORTED, CNSF_ERR_INTERNAL = range(6)
 CNSF_F32, CNSF_F64 = 0, 1
 CNSF_DETECTOR = {"flat": 0, "arc": 1, "parallel": 2}
-CNSF_OPT_NO_SYMMETRY, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_PLAIN_DIFFERENCES = 1, 2, 4
+CNSF_OPT_NO_SYMMETRY, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_PLAIN_DIFFERENCES, CNSF_OPT_NO_REFLECTION = 1, 2, 4, 8
 
 _P = ctypes.c_void_p
 _SIGNATURES = {

@@ -584,6 +584,203 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
     }
 }
 
+// ------------------------------------------------------------------ rotations and reflections
+// With the reflection symmetry as well (see fp_rot8_f32_kernel), the views -k + mV/4 add, per
+// pixel p, U_m(p) = sum_k sum_j y[-k + mV/4][n_det - 1 - j] a(k, j, p) over the views
+// k = 0 .. V/8 that are not their own mirror images, and
+//     (A^T y)[n] = sum_m T_m(R^-m n) + sum_m U_m(M R^-m n),   M (i, r) = (i, N-1-r).
+// The per-call table Y8[o][k][m] holds the 8 weighted pairs of a cell pair (2m + o,
+// 2m + o + 1): T part y[k + mV/4][j] w_j (m = 0..3), U part y[-k + mV/4][n_det - 1 - j] w_j
+// (zero for the self-mirror views k = 0 and 8k = V), 64 bytes; w_j = 2/B of (k, j).
+__global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *__restrict__ box,
+                                       float4 *__restrict__ y8, int nv, int nd)
+{
+    const int ndh = (nd + 1) >> 1, nk = nv / 8 + 1, v4 = nv >> 2;
+    const long long n = 2LL * nk * ndh;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(t / ((long long)nk * ndh));
+        const long long rem = t - (long long)o * nk * ndh;
+        const int k = (int)(rem / ndh), m = (int)(rem - (long long)k * ndh);
+        const bool self = k == 0 || 8 * k == nv;
+        const BoxF *br = box + (long long)k * nd;
+        float out[16];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int j = 2 * m + o + hh;
+            const float w = j < nd ? 1.f / (br[j].q - br[j].hC) : 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float *yt = y + (long long)(k + r * v4) * nd;
+                const float *yu = y + (long long)((nv - k + r * v4) % nv) * nd;
+                out[2 * r + hh] = j < nd ? yt[j] * w : 0.f;
+                out[8 + 2 * r + hh] = (j < nd && !self) ? yu[nd - 1 - j] * w : 0.f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) y8[4 * t + c] = make_float4(out[4 * c], out[4 * c + 1], out[4 * c + 2], out[4 * c + 3]);
+    }
+}
+
+// bp_view2_rot4 with the eight values per cell pair (the merged constants and 64 bytes of
+// weighted sinogram); the two pixels' entries are added to their eight scalar accumulators.
+template <bool ARC, bool EXACT>
+__device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4 &Qb, float hwc, int J,
+                                              const BpArgs &a, int nd, const float *__restrict__ y8row,
+                                              const float *__restrict__ y8orow, const float *__restrict__ acrow,
+                                              long long ac_odd, float (&ta)[8], float (&tb)[8])
+{
+    int g0, g1;
+    pair_window(Qa.P, Qb.P, hwc, J, nd, g0, g1);
+    const int odd = g0 & 1;
+    const int m0 = g0 >> 1, m1 = (g1 - odd) >> 1;   // m0 > m1 when the window misses the detector
+    if (odd) {   // pairs (2m + 1, 2m + 2)
+        acrow += ac_odd;
+        y8row = y8orow;
+    }
+    const float off = (float)(2 * m0 + odd - J);
+    const float sa = ARC ? 1.f : Qa.P.Dn, sb = ARC ? 1.f : Qb.P.Dn;
+    float2 da = make_float2(sa * (Qa.P.sig - off), sa * (Qa.P.sig - off - 1.f));
+    float2 db = make_float2(sb * (Qb.P.sig - off), sb * (Qb.P.sig - off - 1.f));
+    const float2 sta = make_float2(-2.f * sa, -2.f * sa), stb = make_float2(-2.f * sb, -2.f * sb);
+    const float2 m1f = make_float2(-1.f, -1.f), mh = make_float2(-0.5f, -0.5f);
+    for (int m = m0; m <= m1; ++m) {
+        float A[8], Y[8], Z[8];
+        ldg256(acrow + 8 * m, A);          // q | 1/C | ds/L | c1, pairs
+        ldg256(y8row + 16 * m, Y);         // T part, pairs of the four rotations
+        ldg256(y8row + 16 * m + 8, Z);     // U part, pairs of the four mirrored views
+        const float2 iC = make_float2(A[2], A[3]);
+        const float2 piC = __ffma2_rn(make_float2(A[0], A[1]), iC, m1f);
+        const float2 nhC = __fmul2_rn(make_float2(rcp_approx(iC.x), rcp_approx(iC.y)), mh);
+        const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, piC, nhC, a);
+        const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, piC, nhC, a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ta[k] = fmaf(Y[2 * k + 1], wa.y, fmaf(Y[2 * k], wa.x, ta[k]));
+            tb[k] = fmaf(Y[2 * k + 1], wb.y, fmaf(Y[2 * k], wb.x, tb[k]));
+            ta[4 + k] = fmaf(Z[2 * k + 1], wa.y, fmaf(Z[2 * k], wa.x, ta[4 + k]));
+            tb[4 + k] = fmaf(Z[2 * k + 1], wb.y, fmaf(Z[2 * k], wb.x, tb[4 + k]));
+        }
+        da = __fadd2_rn(da, sta);
+        db = __fadd2_rn(db, stb);
+    }
+}
+
+// bp_rot4_f32_kernel over the views k = 0 .. V/8 with the eight accumulators T_0..3, U_0..3
+// per pixel: the partial images partial[8 s + c] of view part s.
+template <bool ARC, bool EXACT>
+__global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomConsts g, const float *__restrict__ ac,
+                                                                     const float *__restrict__ y8, BpArgs a,
+                                                                     const int *__restrict__ order, int ntx, int nsplit,
+                                                                     float *__restrict__ partial,
+                                                                     const double *__restrict__ view_cs,
+                                                                     const float4 *__restrict__ tvtab,
+                                                                     const int *__restrict__ tjtab)
+{
+    __shared__ TileViewS<float> tv[BP_CHUNK];
+    __shared__ int tj[BP_CHUNK];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = 2 * (lane & 7), ty = 8 * warp + 2 * (lane >> 3);
+    const int tile = order[blockIdx.x];   // tiles with the most work first
+    const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
+    const int nk = g.nv / 8 + 1, nv4 = g.nv >> 2;
+    const int vbeg = (int)((long long)nk * blockIdx.y / nsplit), vend = (int)((long long)nk * (blockIdx.y + 1) / nsplit);
+    const int i = it + tx, r = rt + ty;
+    const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
+    const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
+    const int ndh = (g.nd + 1) >> 1;
+    const double refx = tile_ref(it, g.nx), refy = tile_ref(rt, g.ny);
+    const float di = (float)(tx - refx), dr = (float)(ty - refy);
+    float t[4][8];   // [quad pixel][T_0..3, U_0..3]
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t[q][k] = 0.f;
+    for (int v0 = vbeg; v0 < vend; v0 += BP_CHUNK) {
+        const int nvc = min(BP_CHUNK, vend - v0);
+        __syncthreads();
+        for (int k = tid; k < nvc; k += BP_QUAD_THREADS) {
+            if (tvtab) {   // precomputed with the geometry
+                const long long tt = (long long)tile * g.nv + v0 + k;
+                const float4 u0 = __ldg(tvtab + 2 * tt), u1 = __ldg(tvtab + 2 * tt + 1);
+                TileViewS<float> T;
+                T.Dt = u0.x; T.yt = u0.y; T.a1 = u0.z; T.b1 = u0.w; T.rho = u1.x; T.phi = u1.y; T.hc = u1.z; T.hs = u1.w;
+                tv[k] = T;
+                tj[k] = __ldg(tjtab + tt);
+            } else {
+                tile_view_f32(g, view_cs[2 * (v0 + k)], view_cs[2 * (v0 + k) + 1], it + refx, rt + refy, tv[k],
+                              tj[k]);
+            }
+        }
+        __syncthreads();
+        if (!in0) continue;
+        for (int vv = 0; vv < nvc; ++vv) {
+            const int v = v0 + vv;
+            const TileViewS<float> T = tv[vv];
+            const int J = tj[vv];
+            const float *arow = ac + 8 * (long long)v * ndh;
+            const float *yrow = y8 + 16 * (long long)v * ndh, *yorow = y8 + 16 * (long long)(nk + v) * ndh;
+            const long long ac_odd = 8LL * nv4 * ndh;
+            const QuadView Q = quad_view_setup<ARC>(T, di, dr, in1, in2, in3, a);
+            const BpPixel4 P0 = bp_pixel4<ARC>(Q.P0, J, a), P1 = bp_pixel4<ARC>(Q.P1, J, a);
+            const BpPixel4 P2 = bp_pixel4<ARC>(Q.P2, J, a), P3 = bp_pixel4<ARC>(Q.P3, J, a);
+            if (Q.col) {   // P1 is quad pixel 2, P2 quad pixel 1
+                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[0], t[2]);
+                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[1], t[3]);
+            } else {
+                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[0], t[1]);
+                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[2], t[3]);
+            }
+        }
+    }
+    if (in0) {
+        const long long nn = (long long)g.nx * g.ny;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int iq = i + (q & 1), rq = r + (q >> 1);
+            if (iq >= g.nx || rq >= g.ny) continue;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                partial[(8LL * blockIdx.y + k) * nn + (long long)rq * g.nx + iq] = t[q][k] * a.h2q;
+        }
+    }
+}
+
+// img[n] = sum_m T_m(R^-m n) + sum_m U_m(M R^-m n), T_m and U_m the sums of partial[8 s + m]
+// and partial[8 s + 4 + m] over the view parts s (in part order), through eight 32 x 32
+// shared-memory tiles: M (i, r) = (i, N-1-r), M R^-1 (i, r) = (r, i), M R^-2 (i, r) =
+// (N-1-i, r), M R^-3 (i, r) = (N-1-r, N-1-i).
+__global__ void orbit_sum8_kernel(const float *__restrict__ partial, float *__restrict__ img, int n, int nsplit)
+{
+    __shared__ float s[8][32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    const long long nn = (long long)n * n;
+    auto at = [&](int c, int row, int col) {
+        if (row < 0 || row >= n || col < 0 || col >= n) return 0.f;
+        const long long idx = (long long)row * n + col;
+        float v = partial[(long long)c * nn + idx];
+        for (int sp = 1; sp < nsplit; ++sp) v += partial[(8LL * sp + c) * nn + idx];
+        return v;
+    };
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        s[0][a][tx] = at(0, r0 + a, i0 + tx);                       // T_0 at (i, r)
+        s[1][a][tx] = at(1, n - i0 - 32 + a, r0 + tx);              // T_1 at (r, N-1-i)
+        s[2][a][tx] = at(2, n - r0 - 32 + a, n - i0 - 32 + tx);     // T_2 at (N-1-i, N-1-r)
+        s[3][a][tx] = at(3, i0 + a, n - r0 - 32 + tx);              // T_3 at (N-1-r, i)
+        s[4][a][tx] = at(4, n - r0 - 32 + a, i0 + tx);              // U_0 at (i, N-1-r)
+        s[5][a][tx] = at(5, i0 + a, r0 + tx);                       // U_1 at (r, i)
+        s[6][a][tx] = at(6, r0 + a, n - i0 - 32 + tx);              // U_2 at (N-1-i, r)
+        s[7][a][tx] = at(7, n - i0 - 32 + a, n - r0 - 32 + tx);     // U_3 at (N-1-r, N-1-i)
+    }
+    __syncthreads();
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        if (i0 + tx < n && r0 + a < n) {
+            const float tsum = ((s[0][a][tx] + s[1][31 - tx][a]) + s[2][31 - a][31 - tx]) + s[3][tx][31 - a];
+            const float usum = ((s[4][31 - a][tx] + s[5][tx][a]) + s[6][a][31 - tx]) + s[7][31 - tx][31 - a];
+            img[(long long)(r0 + a) * n + i0 + tx] = tsum + usum;
+        }
+    }
+}
+
 // img[n] = sum_k T_k(R^-k n), T_k the sum of partial[4 s + k] over the view parts s (in part
 // order), through four 32 x 32 shared-memory tiles: R^-1 (i, r) = (r, N-1-i),
 // R^-2 (i, r) = (N-1-i, N-1-r), R^-3 (i, r) = (N-1-r, i).
@@ -720,6 +917,56 @@ static int bp_view_parts(const cnsf_geometry *geo, int batch)
     return nsplit;
 }
 
+// View parts of the eight-value gather (over the views 0 .. V/8).
+static int bp_view_parts_rot8(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geo->device);
+    const long long blocks = (long long)((g.nx + BP_T - 1) / BP_T) * ((g.ny + BP_T - 1) / BP_T);
+    int nsplit = 1;
+    while (nsplit < 32 && blocks * nsplit < 32LL * std::max(sms, 1) && (g.nv / 8 + 1) / (2 * nsplit) >= 8) nsplit *= 2;
+    return nsplit;
+}
+
+static size_t back_rot8_alloc_bytes(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    const size_t y8 = 2 * (size_t)(g.nv / 8 + 1) * ((g.nd + 1) / 2) * 16 * sizeof(float);
+    return y8 + (size_t)bp_view_parts_rot8(geo) * 8 * g.nx * g.ny * sizeof(float);
+}
+
+// FP32 back projection of one image by the eight-value gather (geo->sym8).
+static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *img, cudaStream_t st)
+{
+    const GeomConsts &g = geo->gc;
+    const int nk = g.nv / 8 + 1, ndh = (g.nd + 1) / 2, n = g.nx;
+    const int nsplit = bp_view_parts_rot8(geo);
+    const size_t ny8 = 2 * (size_t)nk * ndh * 16;
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, back_rot8_alloc_bytes(geo), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    const double dg = g.arc ? g.ds / g.dps : 0.0;
+    BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
+             (float)(g.arc ? g.dps / g.ds : 0.0), (float)dg, (float)(-dg * dg / 6.0), 8LL * g.nv * ndh, 8 * ndh,
+             (float)g.s0, (float)g.ds, (float)(g.par ? 0.0 : 1.0 / g.dps),
+             (float)(g.arc ? tan(0.5 * g.tau / g.dps) / (g.ds / g.dps) : 0.0), (float)(g.arc ? -0.5 * (g.ds / g.dps) * (g.ds / g.dps) : 0.0)};
+    const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
+    float *y8 = reinterpret_cast<float *>(buf), *partial = y8 + ny8;
+    const long long npair = 2LL * nk * ndh;
+    sino_pairs_rot8_kernel<<<(unsigned)std::min<long long>((npair + 255) / 256, 8192), 256, 0, st>>>(
+        sino, geo->d_box, reinterpret_cast<float4 *>(y8), g.nv, g.nd);
+    auto kern = g.arc ? (geo->exact ? bp_rot8_f32_kernel<true, true> : bp_rot8_f32_kernel<true, false>)
+                      : (geo->exact ? bp_rot8_f32_kernel<false, true> : bp_rot8_f32_kernel<false, false>);
+    kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y8, a, geo->d_bp_order, ntx, nsplit,
+                                                                 partial, geo->d_view_cs, geo->d_tv, geo->d_tj);
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    orbit_sum8_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(partial, img, n, nsplit);
+    cudaFreeAsync(buf, st);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
 // View parts of the four-rotation gather (over the first quarter of the views).
 static int bp_view_parts_rot4(const cnsf_geometry *geo)
 {
@@ -775,6 +1022,7 @@ size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 {
     if (batch <= 0 || dtype != CNSF_F32) return 0;
     if (batch >= 2) return back_batch_alloc_bytes(geo);
+    if (geo->sym8) return back_rot8_alloc_bytes(geo);
     if (geo->sym) return back_rot4_alloc_bytes(geo);
     const GeomConsts &g = geo->gc;
     const int nsplit = bp_view_parts(geo, batch);
@@ -787,6 +1035,7 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
 {
     if (batch == 0) return CNSF_OK;
     if (dtype == CNSF_F32 && batch >= 2) return launch_back_batch(geo, (const float *)sino, (float *)img, batch, st);
+    if (dtype == CNSF_F32 && geo->sym8) return launch_back_rot8(geo, (const float *)sino, (float *)img, st);
     if (dtype == CNSF_F32 && geo->sym) return launch_back_rot4(geo, (const float *)sino, (float *)img, st);
     const GeomConsts &g = geo->gc;
     dim3 blk(BP_T, BP_T), grd((g.nx + BP_T - 1) / BP_T, (g.ny + BP_T - 1) / BP_T, batch);

@@ -75,7 +75,7 @@ void cnsf_geometry_destroy(cnsf_geometry *geom)
 int cnsf_geometry_paths(const cnsf_geometry *geom, int32_t *symmetric, int32_t *exact_differences)
 {
     if (!geom) return CNSF_ERR_INVALID;
-    if (symmetric) *symmetric = geom->sym;
+    if (symmetric) *symmetric = geom->sym8 ? 8 : geom->sym ? 4 : 1;
     if (exact_differences) *exact_differences = geom->exact;
     return CNSF_OK;
 }

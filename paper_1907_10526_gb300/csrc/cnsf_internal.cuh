@@ -290,6 +290,7 @@ struct cnsf_geometry {
     int kc_max;               // largest candidate count per walked line
     size_t device_bytes;      // device memory held by the tables below
     int sym;                  // 1: FP32 single-image projections reuse entries over the quarter turn
+    int sym8;                 // 1: and over the reflection (views 0 .. nv/8 evaluated)
     int exact;                // 1: FP32 kernels form window differences piece by piece
     cnsf::BpWindow bw;        // back projector cell window
     // device tables
@@ -302,6 +303,7 @@ struct cnsf_geometry {
     // launch orders, heaviest blocks first (so that the tail of the grid is short work)
     int *d_fp_order;          // [ceil(nv*nd/128)] forward blocks of 128 rays
     int *d_fp_order4;         // [ceil(nv/4*nd/128)] the same over the rays of views < nv/4 (sym only)
+    int *d_fp_order8;         // [ceil((nv/8+1)*nd/128)] the same over views 0 .. nv/8 (sym8 only)
     float *d_ac;              // [2][nv/4][ceil(n_det/2)][8]: q, 1/C, ds/L, c1 of cells 2m + o, 2m + o + 1 (sym only)
     int *d_bp_order;          // [ceil(nx/16)*ceil(ny/16)] back-projection tiles
     float4 *d_tv;             // [tiles][nv][2] FP32 back-projection tile coefficients (when <= 1 GiB), or null

@@ -453,6 +453,195 @@ __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict_
     for (int k = 0; k < 4; ++k) dst[q + (long long)k * nr4] = out[k];
 }
 
+// ------------------------------------------------------------------ FP32 walk, rotations and reflections
+// With a centred detector and views closed under theta -> -theta as well, the mirror image M
+// of the acquisition of view k in the x axis is view -k with cell j at n_det - 1 - j, and M
+// maps pixel (i, r) to (i, N-1-r): a(-k, n_det - 1 - j, M n) = a(k, j, n).  So for a ray
+// (k, j) of the views k = 0 .. V/8,
+//     y[k + mV/4][j]                = sum_q a(k, j, q) c[R^m q],
+//     y[-k + mV/4][n_det - 1 - j]   = sum_q a(k, j, q) c[R^m M q],
+// eight sinogram values from one walk over c8[q] = (c[R^m q], c[R^m M q]), m = 0..3 (32
+// bytes per pixel).  Views k = 0 and k = V/8 (when V/8 is whole) are their own mirror images
+// up to a quarter turn: their four rotation values are all they produce.
+
+// c8 in both zero-padded layouts, 32 bytes per pixel (two float4), through eight 32 x 32
+// shared-memory tiles of the image.
+__global__ void pad_rot8_kernel(const float *__restrict__ img, float4 *__restrict__ P8, float4 *__restrict__ T8, int n,
+                                int pad, int pitch)
+{
+    __shared__ float s[8][32][33];
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    auto at = [&](int row, int col) { return (row >= 0 && row < n && col >= 0 && col < n) ? img[(long long)row * n + col] : 0.f; };
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        s[0][a][tx] = at(r0 + a, i0 + tx);                      // c[q]        = img[r][i]
+        s[1][a][tx] = at(i0 + a, n - r0 - 32 + tx);             // c[R q]      = img[i][n-1-r]
+        s[2][a][tx] = at(n - r0 - 32 + a, n - i0 - 32 + tx);    // c[R^2 q]    = img[n-1-r][n-1-i]
+        s[3][a][tx] = at(n - i0 - 32 + a, r0 + tx);             // c[R^3 q]    = img[n-1-i][r]
+        s[4][a][tx] = at(n - r0 - 32 + a, i0 + tx);             // c[M q]      = img[n-1-r][i]
+        s[5][a][tx] = at(i0 + a, r0 + tx);                      // c[R M q]    = img[i][r]
+        s[6][a][tx] = at(r0 + a, n - i0 - 32 + tx);             // c[R^2 M q]  = img[r][n-1-i]
+        s[7][a][tx] = at(n - i0 - 32 + a, n - r0 - 32 + tx);    // c[R^3 M q]  = img[n-1-i][n-1-r]
+    }
+    __syncthreads();
+    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
+        // rows layout: pixel (i0 + tx, r0 + a): ix = tx, ry = a
+        if (i0 + tx < n && r0 + a < n) {
+            float4 *o = P8 + 2 * ((long long)(r0 + a) * pitch + pad + i0 + tx);
+            o[0] = make_float4(s[0][a][tx], s[1][tx][31 - a], s[2][31 - a][31 - tx], s[3][31 - tx][a]);
+            o[1] = make_float4(s[4][31 - a][tx], s[5][tx][a], s[6][a][31 - tx], s[7][31 - tx][31 - a]);
+        }
+        // transposed layout: pixel (i0 + a, r0 + tx): ix = a, ry = tx
+        if (i0 + a < n && r0 + tx < n) {
+            float4 *o = T8 + 2 * ((long long)(i0 + a) * pitch + pad + r0 + tx);
+            o[0] = make_float4(s[0][tx][a], s[1][a][31 - tx], s[2][31 - tx][31 - a], s[3][31 - a][tx]);
+            o[1] = make_float4(s[4][31 - tx][a], s[5][a][tx], s[6][tx][31 - a], s[7][31 - a][31 - tx]);
+        }
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int tid = threadIdx.y * 32 + tx, nt = 32 * blockDim.y;
+    if (blockIdx.x == 0 || blockIdx.x == gridDim.x - 1)
+        for (int t = tid; t < 32 * pad; t += nt) {
+            const int a = t / pad, c = t - a * pad;
+            if (r0 + a >= n) continue;
+            if (blockIdx.x == 0) { float4 *o = P8 + 2 * ((long long)(r0 + a) * pitch + c); o[0] = z; o[1] = z; }
+            if (blockIdx.x == gridDim.x - 1) { float4 *o = P8 + 2 * ((long long)(r0 + a) * pitch + pad + n + c); o[0] = z; o[1] = z; }
+        }
+    if (blockIdx.y == 0 || blockIdx.y == gridDim.y - 1)
+        for (int t = tid; t < 32 * pad; t += nt) {
+            const int a = t / pad, c = t - a * pad;
+            if (i0 + a >= n) continue;
+            if (blockIdx.y == 0) { float4 *o = T8 + 2 * ((long long)(i0 + a) * pitch + c); o[0] = z; o[1] = z; }
+            if (blockIdx.y == gridDim.y - 1) { float4 *o = T8 + 2 * ((long long)(i0 + a) * pitch + pad + n + c); o[0] = z; o[1] = z; }
+        }
+}
+
+// line_pair_sum_rot4 with the eight values per pixel (one 256-bit load per candidate and line).
+template <int KC, bool EXACT>
+__device__ __forceinline__ void line_pair_sum_rot8(const float *__restrict__ rp0, const float *__restrict__ rp1, int kc,
+                                                   float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1, float q,
+                                                   float piC, float iC, float2 nhC2, float2 (&s)[8])
+{
+    float2 xs = __fmul2_rn(B2, u), e = __ffma2_rn(kap2, u, er2);
+#pragma unroll
+    for (int m = 0; m < (KC > 0 ? KC : kc); ++m) {
+        const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));
+        const float2 d = wdiff2<EXACT>(x, e, ne1, q, piC, iC, nhC2);
+        const float2 w = __fmul2_rn(d, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
+        float c0[8], c1[8];
+        ldg256(rp0 + 8 * m, c0);
+        ldg256(rp1 + 8 * m, c1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] = __ffma2_rn(make_float2(c0[k], c1[k]), w, s[k]);
+        xs = __fadd2_rn(xs, B2);
+        e = __fadd2_rn(e, kap2);
+    }
+}
+
+template <int KC, bool EXACT>
+__device__ __forceinline__ void walk2_rot8(const RayF &R, const float *__restrict__ base, int pitch8, float B, float q,
+                                           float piC, float iC, float hC, float (&out)[8])
+{
+    long long A = R.A0 + 0xFFFFFFFFLL;   // ceil-ready walk state (fx_window)
+    const long long G = R.G;
+    const int kc = KC > 0 ? KC : R.kc;
+    float2 er2 = make_float2(R.e0, R.e0 + R.de);
+    const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);
+    const float2 B2 = make_float2(B, B), ne1 = make_float2(-1.0f, -1.0f), nhC2 = make_float2(-hC, -hC);
+    const float hw = R.hw;
+    float2 acc[8], part[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = part[k] = make_float2(0.f, 0.f);
+    int rr = 0;
+    for (; rr + 1 < R.nrows; rr += 2) {
+        int ilo0, ilo1;
+        float rho0, rho1;
+        fx_window(A, ilo0, rho0);
+        fx_window(A + G, ilo1, rho1);
+        line_pair_sum_rot8<KC, EXACT>(base + 8LL * ilo0, base + pitch8 + 8LL * ilo1, kc,
+                                      make_float2(rho0 - hw, rho1 - hw), er2, kap2, B2, ne1, q, piC, iC, nhC2, part);
+        A += 2 * G;
+        er2 = __fadd2_rn(er2, de2);
+        base += 2 * pitch8;
+        if ((rr & 15) == 14) {   // blocked summation: partial sums of 16 lines
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc[k] = __fadd2_rn(acc[k], part[k]);
+                part[k] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        acc[k] = __fadd2_rn(acc[k], part[k]);
+        out[k] = acc[k].x + acc[k].y;
+    }
+    if (rr < R.nrows) {   // odd line count: the last line alone
+        int ilo;
+        float rho;
+        fx_window(A, ilo, rho);
+        float um = rho - hw;
+        for (int m = 0; m < kc; ++m, um += 1.0f) {
+            const float e = fmaf(R.kap, um, er2.x);
+            const float w = wdiff<EXACT>(fabsf(B * um), e, q, piC, iC, hC) * rcp_approx(e);
+            float c[8];
+            ldg256(base + 8LL * (ilo + m), c);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) out[k] = fmaf(c[k], w, out[k]);
+        }
+    }
+}
+
+// One thread per ray (k, j) of the views k = 0 .. V/8 (and line part): rotation values at rows
+// k + mV/4, mirror values at rows -k + mV/4 (mod V), cell n_det - 1 - j.
+template <bool EXACT>
+__global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
+                                                          const BoxF *__restrict__ box, float h2q,
+                                                          const float *__restrict__ imgP, const float *__restrict__ imgT,
+                                                          int pitch, int pad, int nv, int nd, int nr8,
+                                                          float *__restrict__ sino, int nsplit,
+                                                          float *__restrict__ partial)
+{
+    const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
+    if (q >= nr8) return;
+    RayF R = rays[q];
+    if (nsplit > 1) {
+        const int l0 = (int)((long long)R.nrows * blockIdx.z / nsplit), l1 = (int)((long long)R.nrows * (blockIdx.z + 1) / nsplit);
+        R.A0 += (long long)l0 * R.G;
+        R.e0 += (float)l0 * R.de;
+        R.r0 += l0;
+        R.nrows = l1 - l0;
+    }
+    float out[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (R.nrows > 0) {
+        const float4 bx = __ldg(reinterpret_cast<const float4 *>(box + q));
+        const float qw = bx.x, piC = bx.y, iC = bx.z, hC = bx.w;
+        const float B = 2.f * (qw - hC);
+        tighten_window(R, qw, B);
+        const float *base = ((R.flags & 1) ? imgT : imgP) + 8LL * (pad + (long long)R.r0 * pitch);
+        const int pitch8 = 8 * pitch;
+        switch (R.kc) {
+            case 1: walk2_rot8<1, EXACT>(R, base, pitch8, B, qw, piC, iC, hC, out); break;
+            case 2: walk2_rot8<2, EXACT>(R, base, pitch8, B, qw, piC, iC, hC, out); break;
+            case 3: walk2_rot8<3, EXACT>(R, base, pitch8, B, qw, piC, iC, hC, out); break;
+            case 4: walk2_rot8<4, EXACT>(R, base, pitch8, B, qw, piC, iC, hC, out); break;
+            case 5: walk2_rot8<5, EXACT>(R, base, pitch8, B, qw, piC, iC, hC, out); break;
+            case 6: walk2_rot8<6, EXACT>(R, base, pitch8, B, qw, piC, iC, hC, out); break;
+            default: walk2_rot8<0, EXACT>(R, base, pitch8, B, qw, piC, iC, hC, out); break;
+        }
+        const float nrm = h2q / (qw - hC);   // h^2/(2B)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[k] *= nrm;
+    }
+    float *dst = nsplit > 1 ? partial + (long long)blockIdx.z * nv * nd : sino;
+    const int k = q / nd, j = q - k * nd, v4 = nv >> 2;
+    const bool self = k == 0 || 8 * k == nv;   // its own mirror image up to a quarter turn
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        dst[(long long)(k + m * v4) * nd + j] = out[m];
+        if (!self) dst[(long long)((nv - k + m * v4) % nv) * nd + (nd - 1 - j)] = out[4 + m];
+    }
+}
+
 // ------------------------------------------------------------------ FP64 walk
 // Same enumeration (fixed-point windows of the ray table); the arithmetic, including the
 // crossing f = f0 + rb g, is recomputed in FP64 from the view and cell angles.
@@ -554,6 +743,50 @@ static size_t forward_rot4_alloc_bytes(const cnsf_geometry *geo)
     return img4 + (nsplit > 1 ? (size_t)nsplit * g.nv * g.nd * sizeof(float) : 0);
 }
 
+// Line parts of the eight-value walk (views 0 .. V/8).
+static int fp_line_parts_rot8(const cnsf_geometry *geo)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geo->device);
+    const long long blocks = ((long long)(geo->gc.nv / 8 + 1) * geo->gc.nd + 127) / 128;
+    int nsplit = 1;
+    while (nsplit < 8 && blocks * nsplit < 128LL * std::max(sms, 1)) nsplit *= 2;
+    return nsplit;
+}
+
+static size_t forward_rot8_alloc_bytes(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    const int nsplit = fp_line_parts_rot8(geo);
+    const size_t img8 = 2 * (size_t)g.nx * (g.nx + 2 * geo->pad) * 2 * sizeof(float4);
+    return img8 + (nsplit > 1 ? (size_t)nsplit * g.nv * g.nd * sizeof(float) : 0);
+}
+
+// FP32 forward projection of one image by the eight-value kernel (geo->sym8).
+static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float *sino, cudaStream_t st)
+{
+    const GeomConsts &g = geo->gc;
+    const int n = g.nx, pad = geo->pad, pitch = n + 2 * pad;
+    const int nr = g.nv * g.nd, nr8 = (g.nv / 8 + 1) * g.nd;
+    const int nsplit = fp_line_parts_rot8(geo);
+    char *buf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&buf, forward_rot8_alloc_bytes(geo), st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
+    float4 *P8 = reinterpret_cast<float4 *>(buf), *T8 = P8 + 2 * (size_t)n * pitch;
+    float *partial = nsplit > 1 ? reinterpret_cast<float *>(T8 + 2 * (size_t)n * pitch) : nullptr;
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    pad_rot8_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(img, P8, T8, n, pad, pitch);
+    (geo->exact ? fp_rot8_f32_kernel<true> : fp_rot8_f32_kernel<false>)<<<dim3((nr8 + 127) / 128, 1, nsplit), 128, 0, st>>>(
+        geo->d_fp_order8, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), reinterpret_cast<const float *>(P8),
+        reinterpret_cast<const float *>(T8), pitch, pad, g.nv, g.nd, nr8, sino, nsplit, partial);
+    if (nsplit > 1)
+        fp_sum_parts_kernel<<<(unsigned)std::min<long long>((nr + 255) / 256, 4096), 256, 0, st>>>(partial, sino, nr,
+                                                                                                   nsplit);
+    cudaFreeAsync(buf, st);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+}
+
 // FP32 forward projection of one image by the four-rotation kernel (geo->sym).
 static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float *sino, cudaStream_t st)
 {
@@ -583,6 +816,7 @@ size_t forward_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 {
     if (batch <= 0) return 0;
     if (dtype == CNSF_F32 && batch >= 2) return forward_batch_alloc_bytes(geo);
+    if (dtype == CNSF_F32 && geo->sym8) return forward_rot8_alloc_bytes(geo);
     if (dtype == CNSF_F32 && geo->sym) return forward_rot4_alloc_bytes(geo);
     size_t bytes = forward_scratch_bytes(geo, batch, dtype);   // padded copies
     if (dtype == CNSF_F32) {
@@ -596,6 +830,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
 {
     if (batch == 0) return CNSF_OK;
     if (dtype == CNSF_F32 && batch >= 2) return launch_forward_batch(geo, (const float *)img, (float *)sino, batch, st);
+    if (dtype == CNSF_F32 && geo->sym8) return launch_forward_rot8(geo, (const float *)img, (float *)sino, st);
     if (dtype == CNSF_F32 && geo->sym) return launch_forward_rot4(geo, (const float *)img, (float *)sino, st);
     const GeomConsts &g = geo->gc;
     const int nr = g.nv * g.nd;

@@ -52,7 +52,8 @@ static int validate(const cnsf_geometry_desc *d)
     if (d->angles_rad)
         for (int k = 0; k < d->n_views; ++k)
             if (!std::isfinite(d->angles_rad[k])) return CNSF_ERR_INVALID;
-    const int known = CNSF_OPT_NO_SYMMETRY | CNSF_OPT_EXACT_DIFFERENCES | CNSF_OPT_PLAIN_DIFFERENCES;
+    const int known = CNSF_OPT_NO_SYMMETRY | CNSF_OPT_EXACT_DIFFERENCES | CNSF_OPT_PLAIN_DIFFERENCES |
+                      CNSF_OPT_NO_REFLECTION;
     if ((d->options & ~known) != 0) return CNSF_ERR_INVALID;
     if ((d->options & CNSF_OPT_EXACT_DIFFERENCES) && (d->options & CNSF_OPT_PLAIN_DIFFERENCES)) return CNSF_ERR_INVALID;
     return CNSF_OK;
@@ -70,6 +71,23 @@ static bool quarter_turn_symmetric(const cnsf_geometry_desc *d)
     const int q = d->n_views / 4;
     for (int k = 0; k + q < d->n_views; ++k) {
         const double r = std::remainder(d->angles_rad[k + q] - d->angles_rad[k] - 0.5 * M_PI, 2.0 * M_PI);
+        if (!(std::fabs(r) <= 1e-12)) return false;
+    }
+    return true;
+}
+
+// The reflection symmetry on top of the quarter turns: a centred detector (cells mirror
+// onto cells) and views closed under theta -> -theta, view (V - k) mod V at -theta_k.
+// Mirroring the acquisition of view k in the x axis gives view -k with cell j at
+// n_det - 1 - j and pixel (i, r) at (i, n_y - 1 - r) (Sec. II.A conventions).
+static bool reflection_symmetric(const cnsf_geometry_desc *d)
+{
+    if (d->options & CNSF_OPT_NO_REFLECTION) return false;
+    if (d->det_offset_mm != 0.0) return false;
+    if (!d->angles_rad) return true;
+    const int V = d->n_views;
+    for (int k = 0; k < V; ++k) {
+        const double r = std::remainder(d->angles_rad[(V - k) % V] + d->angles_rad[k], 2.0 * M_PI);
         if (!(std::fabs(r) <= 1e-12)) return false;
     }
     return true;
@@ -234,6 +252,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     // (lines x candidates).  Back: 16 x 16 tiles by descending mean magnification of their
     // centre over the views, 1/sqrt(D_po^2 - rho^2) for a tile at radius rho.
     const bool sym = quarter_turn_symmetric(d);
+    const bool sym8 = sym && reflection_symmetric(d);
+    const size_t nr8 = sym8 ? (size_t)(nv / 8 + 1) * nd : 0;
     if (sym) {
         const size_t np4 = (size_t)(nv / 4) * ndh;
         ac.assign(2 * 8 * np4, 0.0f);
@@ -249,7 +269,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
                 }
     }
     const size_t nr4 = sym ? (size_t)(nv / 4) * nd : 0;
-    std::vector<int> fp_order((nr + 127) / 128), fp_order4((nr4 + 127) / 128), bp_order;
+    std::vector<int> fp_order((nr + 127) / 128), fp_order4((nr4 + 127) / 128), fp_order8((nr8 + 127) / 128), bp_order;
     {
         auto order_blocks = [&](size_t nrays, std::vector<int> &order) {
             std::vector<std::pair<double, int>> w(order.size());
@@ -263,6 +283,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         };
         order_blocks(nr, fp_order);
         order_blocks(nr4, fp_order4);
+        order_blocks(nr8, fp_order8);
         const int tx = (g.nx + 15) / 16, ty = (g.ny + 15) / 16;
         std::vector<std::pair<double, int>> t((size_t)tx * ty);
         for (int b = 0; b < ty; ++b)
@@ -284,6 +305,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
     geo->pad = pad;
     geo->kc_max = kc_max;
     geo->sym = sym ? 1 : 0;
+    geo->sym8 = sym8 ? 1 : 0;
     // Window differences: the plain form loses about log2(B / tau') bits (B <= h); take the
     // exact form when the thinnest effective blur of any entry -- the cell seen at the depth of
     // the image point nearest the source (Eq. 17), tau itself for parallel rays -- falls below
@@ -335,6 +357,7 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         {(void **)&geo->d_fp_order, fp_order.data(), fp_order.size() * sizeof(int)},
         {(void **)&geo->d_bp_order, bp_order.data(), bp_order.size() * sizeof(int)},
         {(void **)&geo->d_fp_order4, fp_order4.data(), fp_order4.size() * sizeof(int)},
+        {(void **)&geo->d_fp_order8, fp_order8.data(), fp_order8.size() * sizeof(int)},
         {(void **)&geo->d_ac, ac.data(), ac.size() * sizeof(float)},
     };
     for (const Up &u : ups) {
@@ -359,7 +382,7 @@ void destroy_geometry(cnsf_geometry *geo)
     if (!geo) return;
     void *ptrs[] = {geo->d_view_cs, geo->d_cell_d, geo->d_box, geo->d_cellf, geo->d_ray,
                     geo->d_fp_order, geo->d_bp_order, geo->d_box2, geo->d_cell2, geo->d_tv, geo->d_tj,
-                    geo->d_fp_order4, geo->d_ac};
+                    geo->d_fp_order4, geo->d_ac, geo->d_fp_order8};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete geo;

@@ -68,7 +68,7 @@ def test_invalid_geometries_refused_without_gpu():
     d = GeometryDesc(8, 8, 1.0, 0, 0, 4, ang, 8, 1, 1, 0, 30, 60, 0)
     assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
     # unknown option bits, and both window-difference forms at once, are refused
-    for opt in (8, 1 << 20, 2 | 4):
+    for opt in (16, 1 << 20, 2 | 4):
         d = GeometryDesc(8, 8, 1.0, 0, 0, 4, None, 8, 1, 1, 0, 30, 60, 0, opt)
         assert lib.cnsf_geometry_create(ctypes.byref(d), ctypes.byref(h)) == CNSF_ERR_INVALID
     # queries refuse missing arguments before touching a device

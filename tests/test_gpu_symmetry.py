@@ -1,4 +1,4 @@
-"""Entries reused over the quarter turns of the acquisition (GPU).
+"""Entries reused over the quarter turns and reflections of the acquisition (GPU).
 
 A square image centred on the rotation axis, with views closed under a quarter turn
 (view k + V/4 at theta_k + pi/2), has every entry of Eq. (18) repeated four times:
@@ -7,7 +7,10 @@ projections then evaluate each entry once.  These tests hold that path, on every
 to the FP64 oracle (1e-5 relative L2, the FP32 bar) and to the general kernels of the same
 geometry (1e-6: the two differ only by FP32 rounding), check the adjoint identity between
 its two directions, and check that the library takes it exactly when the geometry has the
-symmetry.
+symmetry.  With a centred detector and views closed under theta -> -theta the mirror image
+in the x axis is used as well (each distinct entry then serves 8 entries of A, 4 at the
+views that are their own mirror images); those geometries are also held to their
+quarter-turn-only evaluation.
 """
 import math
 
@@ -34,7 +37,13 @@ SYMMETRIC = {
     # cells 6x the pixel size: more than 8 candidates per line (the generic walk)
     "wide_cells": FanGeometry(nx=40, ny=40, n_views=16, n_det=24, det_spacing=6.0, det_width=6.0, d_po=100.0,
                               d_ps=200.0),
+    # V = 20 (V/8 not whole: no view at 45 degrees), V = 8 (view 1 is its own mirror image)
+    "views_20": FanGeometry(nx=44, ny=44, n_views=20, n_det=90, d_po=200.0, d_ps=420.0),
+    "views_8": FanGeometry(nx=30, ny=30, n_views=8, n_det=64, d_po=150.0, d_ps=300.0, detector="arc"),
 }
+# the order each case takes: 8 with a centred detector and views closed under reflection
+ORDER = {"flat_72": 8, "flat_odd_offset": 4, "arc": 8, "parallel": 8, "angles_offset": 4, "wide_cells": 8,
+         "views_20": 8, "views_8": 8}
 
 NOT_SYMMETRIC = {
     "views_not_multiple_of_4": config_geometry(1),                                 # 90 views
@@ -43,6 +52,7 @@ NOT_SYMMETRIC = {
     "angles_not_closed": FanGeometry(nx=32, ny=32, n_views=24, n_det=64,
                                      angles=tuple(2.0 * math.pi * k / 24 + 1e-3 * (k == 7) for k in range(24))),
 }
+
 
 
 @pytest.fixture(scope="module")
@@ -72,16 +82,20 @@ def test_symmetric_path_matches_oracle_and_general(cnsf, name):
     g = SYMMETRIC[name]
     geom = cnsf.Geometry(g)
     gen = cnsf.Geometry(g, symmetry=False)
-    assert geom.paths["symmetric"] and not gen.paths["symmetric"]
+    rot = cnsf.Geometry(g, symmetry="rotations")
+    assert geom.paths["symmetry_order"] == ORDER[name]
+    assert not gen.paths["symmetric"] and rot.paths["symmetry_order"] == 4
     rng = np.random.default_rng(50 + len(name))
     img = rng.uniform(0.0, 1.0, (g.ny, g.nx))
     sino = rng.uniform(0.0, 1.0, (g.n_views, g.n_det))
     y, yg, yo = _fwd(cnsf, geom, img), _fwd(cnsf, gen, img), oracle.forward(g, img)
     assert rel(y, yo) < 1e-5
     assert rel(y, yg) < 1e-6
+    assert rel(_fwd(cnsf, rot, img), yg) < 1e-6
     c, cg, co = _bwd(cnsf, geom, sino), _bwd(cnsf, gen, sino), oracle.back(g, sino)
     assert rel(c, co) < 1e-5
     assert rel(c, cg) < 1e-6
+    assert rel(_bwd(cnsf, rot, sino), cg) < 1e-6
     # adjoint identity <A x, s> = <x, A^T s> between the two symmetric kernels
     lhs, rhs = float(np.vdot(y, sino)), float(np.vdot(img, c))
     assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(y) * np.linalg.norm(sino)
@@ -99,7 +113,7 @@ def test_general_path_when_not_symmetric(cnsf, name):
 
 def test_headline_workload_takes_symmetric_path(cnsf):
     geom = cnsf.Geometry(config_geometry(2))
-    assert geom.paths == {"symmetric": True, "exact_differences": False}
+    assert geom.paths == {"symmetric": True, "symmetry_order": 8, "exact_differences": False}
 
 
 def test_symmetric_repeats_bitwise(cnsf):
@@ -114,3 +128,13 @@ def test_symmetric_repeats_bitwise(cnsf):
     c1 = cnsf.back_project(geom, y1)
     c2 = cnsf.back_project(geom, y1)
     assert torch.equal(c1, c2)
+
+
+def test_symmetric_repeats_bitwise_rotations_only(cnsf):
+    g = SYMMETRIC["flat_72"]
+    geom = cnsf.Geometry(g, symmetry="rotations")
+    rng = np.random.default_rng(4)
+    x = torch.tensor(rng.uniform(0, 1, (g.ny, g.nx)), dtype=torch.float32, device="cuda")
+    y1, y2 = cnsf.forward_project(geom, x), cnsf.forward_project(geom, x)
+    assert torch.equal(y1, y2)
+    assert torch.equal(cnsf.back_project(geom, y1), cnsf.back_project(geom, y1))

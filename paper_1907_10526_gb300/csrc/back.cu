@@ -749,65 +749,69 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
 // and partial[8 s + 4 + m] over the view parts s (in part order), through eight 32 x 32
 // shared-memory tiles: M (i, r) = (i, N-1-r), M R^-1 (i, r) = (r, i), M R^-2 (i, r) =
 // (N-1-i, r), M R^-3 (i, r) = (N-1-r, N-1-i).
-__global__ void orbit_sum8_kernel(const float *__restrict__ partial, float *__restrict__ img, int n, int nsplit)
+template <int NS>
+__global__ void __launch_bounds__(1024) orbit_sum8_kernel(const float *__restrict__ partial, float *__restrict__ img,
+                                                          int n)
 {
     __shared__ float s[8][32][33];
-    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, a = threadIdx.y;
     const long long nn = (long long)n * n;
-    auto at = [&](int c, int row, int col) {
-        if (row < 0 || row >= n || col < 0 || col >= n) return 0.f;
-        const long long idx = (long long)row * n + col;
-        float v = partial[(long long)c * nn + idx];
-        for (int sp = 1; sp < nsplit; ++sp) v += partial[(8LL * sp + c) * nn + idx];
-        return v;
-    };
-    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
-        s[0][a][tx] = at(0, r0 + a, i0 + tx);                       // T_0 at (i, r)
-        s[1][a][tx] = at(1, n - i0 - 32 + a, r0 + tx);              // T_1 at (r, N-1-i)
-        s[2][a][tx] = at(2, n - r0 - 32 + a, n - i0 - 32 + tx);     // T_2 at (N-1-i, N-1-r)
-        s[3][a][tx] = at(3, i0 + a, n - r0 - 32 + tx);              // T_3 at (N-1-r, i)
-        s[4][a][tx] = at(4, n - r0 - 32 + a, i0 + tx);              // U_0 at (i, N-1-r)
-        s[5][a][tx] = at(5, i0 + a, r0 + tx);                       // U_1 at (r, i)
-        s[6][a][tx] = at(6, r0 + a, n - i0 - 32 + tx);              // U_2 at (N-1-i, r)
-        s[7][a][tx] = at(7, n - i0 - 32 + a, n - r0 - 32 + tx);     // U_3 at (N-1-r, N-1-i)
+    // source rows and columns of the eight tiles at (a, tx)
+    const int rows[8] = {r0 + a, n - i0 - 32 + a, n - r0 - 32 + a, i0 + a,
+                         n - r0 - 32 + a, i0 + a, r0 + a, n - i0 - 32 + a};
+    const int cols[8] = {i0 + tx, r0 + tx, n - i0 - 32 + tx, n - r0 - 32 + tx,
+                         i0 + tx, r0 + tx, n - i0 - 32 + tx, n - r0 - 32 + tx};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float v = 0.f;
+        if (rows[c] >= 0 && rows[c] < n && cols[c] >= 0 && cols[c] < n) {
+            const float *src = partial + (long long)c * nn + (long long)rows[c] * n + cols[c];
+            float w[NS];
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) w[sp] = __ldg(src + 8LL * sp * nn);   // all loads in flight
+            v = w[0];
+#pragma unroll
+            for (int sp = 1; sp < NS; ++sp) v += w[sp];
+        }
+        s[c][a][tx] = v;
     }
     __syncthreads();
-    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
-        if (i0 + tx < n && r0 + a < n) {
-            const float tsum = ((s[0][a][tx] + s[1][31 - tx][a]) + s[2][31 - a][31 - tx]) + s[3][tx][31 - a];
-            const float usum = ((s[4][31 - a][tx] + s[5][tx][a]) + s[6][a][31 - tx]) + s[7][31 - tx][31 - a];
-            img[(long long)(r0 + a) * n + i0 + tx] = tsum + usum;
-        }
+    if (i0 + tx < n && r0 + a < n) {
+        const float tsum = ((s[0][a][tx] + s[1][31 - tx][a]) + s[2][31 - a][31 - tx]) + s[3][tx][31 - a];
+        const float usum = ((s[4][31 - a][tx] + s[5][tx][a]) + s[6][a][31 - tx]) + s[7][31 - tx][31 - a];
+        img[(long long)(r0 + a) * n + i0 + tx] = tsum + usum;
     }
 }
 
 // img[n] = sum_k T_k(R^-k n), T_k the sum of partial[4 s + k] over the view parts s (in part
 // order), through four 32 x 32 shared-memory tiles: R^-1 (i, r) = (r, N-1-i),
 // R^-2 (i, r) = (N-1-i, N-1-r), R^-3 (i, r) = (N-1-r, i).
-__global__ void orbit_sum_kernel(const float *__restrict__ partial, float *__restrict__ img, int n, int nsplit)
+template <int NS>
+__global__ void __launch_bounds__(1024) orbit_sum_kernel(const float *__restrict__ partial, float *__restrict__ img,
+                                                         int n)
 {
     __shared__ float s[4][32][33];
-    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, a = threadIdx.y;
     const long long nn = (long long)n * n;
-    auto at = [&](int k, int row, int col) {
-        if (row < 0 || row >= n || col < 0 || col >= n) return 0.f;
-        const long long idx = (long long)row * n + col;
-        float v = partial[(long long)k * nn + idx];
-        for (int sp = 1; sp < nsplit; ++sp) v += partial[(4LL * sp + k) * nn + idx];
-        return v;
-    };
-    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
-        s[0][a][tx] = at(0, r0 + a, i0 + tx);                       // T_0 at (i, r)
-        s[1][a][tx] = at(1, n - i0 - 32 + a, r0 + tx);              // T_1 at (r, N-1-i)
-        s[2][a][tx] = at(2, n - r0 - 32 + a, n - i0 - 32 + tx);     // T_2 at (N-1-i, N-1-r)
-        s[3][a][tx] = at(3, i0 + a, n - r0 - 32 + tx);              // T_3 at (N-1-r, i)
+    const int rows[4] = {r0 + a, n - i0 - 32 + a, n - r0 - 32 + a, i0 + a};
+    const int cols[4] = {i0 + tx, r0 + tx, n - i0 - 32 + tx, n - r0 - 32 + tx};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float v = 0.f;
+        if (rows[c] >= 0 && rows[c] < n && cols[c] >= 0 && cols[c] < n) {
+            const float *src = partial + (long long)c * nn + (long long)rows[c] * n + cols[c];
+            float w[NS];
+#pragma unroll
+            for (int sp = 0; sp < NS; ++sp) w[sp] = __ldg(src + 4LL * sp * nn);   // all loads in flight
+            v = w[0];
+#pragma unroll
+            for (int sp = 1; sp < NS; ++sp) v += w[sp];
+        }
+        s[c][a][tx] = v;
     }
     __syncthreads();
-    for (int a = threadIdx.y; a < 32; a += blockDim.y) {
-        if (i0 + tx < n && r0 + a < n)
-            img[(long long)(r0 + a) * n + i0 + tx] =
-                ((s[0][a][tx] + s[1][31 - tx][a]) + s[2][31 - a][31 - tx]) + s[3][tx][31 - a];
-    }
+    if (i0 + tx < n && r0 + a < n)
+        img[(long long)(r0 + a) * n + i0 + tx] = ((s[0][a][tx] + s[1][31 - tx][a]) + s[2][31 - a][31 - tx]) + s[3][tx][31 - a];
 }
 
 // FP64: same tiling and window; every per-pair constant is recomputed in FP64 from the view
@@ -881,6 +885,35 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
         }
     }
     if (inside) img[(b * g.ny + r) * g.nx + i] = acc;
+}
+
+// The orbit sums for the view-part counts the launchers use (powers of two up to 32).
+static void launch_orbit_sum8(const float *partial, float *img, int n, int nsplit, cudaStream_t st)
+{
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    const dim3 grd(nt, nt), blk(32, 32);
+    switch (nsplit) {
+        case 1: orbit_sum8_kernel<1><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 2: orbit_sum8_kernel<2><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 4: orbit_sum8_kernel<4><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 8: orbit_sum8_kernel<8><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 16: orbit_sum8_kernel<16><<<grd, blk, 0, st>>>(partial, img, n); break;
+        default: orbit_sum8_kernel<32><<<grd, blk, 0, st>>>(partial, img, n); break;
+    }
+}
+
+static void launch_orbit_sum4(const float *partial, float *img, int n, int nsplit, cudaStream_t st)
+{
+    const unsigned nt = (unsigned)((n + 31) / 32);
+    const dim3 grd(nt, nt), blk(32, 32);
+    switch (nsplit) {
+        case 1: orbit_sum_kernel<1><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 2: orbit_sum_kernel<2><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 4: orbit_sum_kernel<4><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 8: orbit_sum_kernel<8><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 16: orbit_sum_kernel<16><<<grd, blk, 0, st>>>(partial, img, n); break;
+        default: orbit_sum_kernel<32><<<grd, blk, 0, st>>>(partial, img, n); break;
+    }
 }
 
 // The sinogram as weighted cell pairs of parity o: y2[b][v][m] = (w y[b][v][2m + o],
@@ -960,8 +993,7 @@ static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *
                       : (geo->exact ? bp_rot8_f32_kernel<false, true> : bp_rot8_f32_kernel<false, false>);
     kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y8, a, geo->d_bp_order, ntx, nsplit,
                                                                  partial, geo->d_view_cs, geo->d_tv, geo->d_tj);
-    const unsigned nt = (unsigned)((n + 31) / 32);
-    orbit_sum8_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(partial, img, n, nsplit);
+    launch_orbit_sum8(partial, img, n, nsplit, st);
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
@@ -1011,8 +1043,7 @@ static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *
     kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y4, a, geo->d_bp_order, ntx,
                                                                  nsplit, partial, geo->d_view_cs, geo->d_tv,
                                                                  geo->d_tj);
-    const unsigned nt = (unsigned)((n + 31) / 32);
-    orbit_sum_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(partial, img, n, nsplit);
+    launch_orbit_sum4(partial, img, n, nsplit, st);
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);

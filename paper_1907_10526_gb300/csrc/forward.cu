@@ -260,13 +260,29 @@ __global__ void __launch_bounds__(128) fp_f32_kernel(const int *__restrict__ ord
         sino[b * nr + q] = acc;
 }
 
-// sino = sum over the line parts, in part order
-__global__ void fp_sum_parts_kernel(const float *__restrict__ partial, float *__restrict__ sino, long long n, int nsplit)
+// sino = sum over the line parts, in part order (NS parts, every load issued at once)
+template <int NS>
+__global__ void fp_sum_parts_kernel(const float *__restrict__ partial, float *__restrict__ sino, long long n)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        float s = partial[t];
-        for (int k = 1; k < nsplit; ++k) s += partial[k * n + t];
+        float w[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) w[k] = __ldg(partial + k * n + t);
+        float s = w[0];
+#pragma unroll
+        for (int k = 1; k < NS; ++k) s += w[k];
         sino[t] = s;
+    }
+}
+
+// The part sum for the part counts of the launchers (powers of two up to 8).
+static void launch_fp_sum_parts(const float *partial, float *sino, long long n, int nsplit, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 4096);
+    switch (nsplit) {
+        case 2: fp_sum_parts_kernel<2><<<blocks, 256, 0, st>>>(partial, sino, n); break;
+        case 4: fp_sum_parts_kernel<4><<<blocks, 256, 0, st>>>(partial, sino, n); break;
+        default: fp_sum_parts_kernel<8><<<blocks, 256, 0, st>>>(partial, sino, n); break;
     }
 }
 
@@ -775,13 +791,12 @@ static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float
     float4 *P8 = reinterpret_cast<float4 *>(buf), *T8 = P8 + 2 * (size_t)n * pitch;
     float *partial = nsplit > 1 ? reinterpret_cast<float *>(T8 + 2 * (size_t)n * pitch) : nullptr;
     const unsigned nt = (unsigned)((n + 31) / 32);
-    pad_rot8_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(img, P8, T8, n, pad, pitch);
+    pad_rot8_kernel<<<dim3(nt, nt), dim3(32, 32), 0, st>>>(img, P8, T8, n, pad, pitch);
     (geo->exact ? fp_rot8_f32_kernel<true> : fp_rot8_f32_kernel<false>)<<<dim3((nr8 + 127) / 128, 1, nsplit), 128, 0, st>>>(
         geo->d_fp_order8, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), reinterpret_cast<const float *>(P8),
         reinterpret_cast<const float *>(T8), pitch, pad, g.nv, g.nd, nr8, sino, nsplit, partial);
     if (nsplit > 1)
-        fp_sum_parts_kernel<<<(unsigned)std::min<long long>((nr + 255) / 256, 4096), 256, 0, st>>>(partial, sino, nr,
-                                                                                                   nsplit);
+        launch_fp_sum_parts(partial, sino, nr, nsplit, st);
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
@@ -800,13 +815,12 @@ static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float
     float4 *P4 = reinterpret_cast<float4 *>(buf), *T4 = P4 + (size_t)n * pitch;
     float *partial = nsplit > 1 ? reinterpret_cast<float *>(T4 + (size_t)n * pitch) : nullptr;
     const unsigned nt = (unsigned)((n + 31) / 32);
-    pad_rot4_kernel<<<dim3(nt, nt), dim3(32, 8), 0, st>>>(img, P4, T4, n, pad, pitch);
+    pad_rot4_kernel<<<dim3(nt, nt), dim3(32, 32), 0, st>>>(img, P4, T4, n, pad, pitch);
     (geo->exact ? fp_rot4_f32_kernel<true> : fp_rot4_f32_kernel<false>)<<<dim3((nr4 + 127) / 128, 1, nsplit), 128, 0, st>>>(
         geo->d_fp_order4, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P4, T4, pitch, pad, nr, nr4, sino,
         nsplit, partial);
     if (nsplit > 1)
-        fp_sum_parts_kernel<<<(unsigned)std::min<long long>((nr + 255) / 256, 4096), 256, 0, st>>>(partial, sino, nr,
-                                                                                                   nsplit);
+        launch_fp_sum_parts(partial, sino, nr, nsplit, st);
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
@@ -852,8 +866,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
             geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + (size_t)batch * strideP,
             pitchP, pitchT, strideP, strideT, geo->pad, nr, (float *)sino, nsplit, partial);
         if (nsplit > 1) {
-            fp_sum_parts_kernel<<<(unsigned)std::min<long long>((nout + 255) / 256, 4096), 256, 0, st>>>(
-                partial, (float *)sino, nout, nsplit);
+            launch_fp_sum_parts(partial, (float *)sino, nout, nsplit, st);
             cudaFreeAsync(partial, st);
         }
         cudaFreeAsync(buf, st);

@@ -100,9 +100,10 @@ typedef struct {
  *     angles, angles_rad[k + n_views/4] = angles_rad[k] + pi/2 to 1e-12 rad), the view
  *     v + k n_views/4 sees the image of view v turned by k quarter turns, a quarter turn maps
  *     the pixel lattice onto itself, and so every entry a(v + k n_views/4, j, n) equals
- *     a(v, j, n turned back by k quarter turns).  The FP32 single-image projections then
- *     evaluate each distinct entry once and apply it to the four (view, pixel) pairs it
- *     belongs to.  When moreover the detector is centred (det_offset = 0) and the views are
+ *     a(v, j, n turned back by k quarter turns).  The FP32 projections then evaluate each
+ *     distinct entry once and apply it to the four (view, pixel) pairs it belongs to (a
+ *     batch image by image, each with the bits of its single-image call, in launch groups
+ *     whose scratch stays within 256 MiB).  When moreover the detector is centred (det_offset = 0) and the views are
  *     closed under reflection (angles_rad[(n_views - k) mod n_views] = -angles_rad[k] to
  *     1e-12 rad, true of the default angles), mirroring the acquisition of view v in the x
  *     axis gives view -v with cell j at n_det - 1 - j and pixel row r at n_y - 1 - r, so each
@@ -139,7 +140,7 @@ CNSF_API int cnsf_geometry_create(const cnsf_geometry_desc *desc, cnsf_geometry 
  * work launched with it is still pending. */
 CNSF_API void cnsf_geometry_destroy(cnsf_geometry *geom);
 
-/* The evaluation paths a geometry's FP32 single-image projections take (the paper has no
+/* The evaluation paths a geometry's FP32 projections take (the paper has no
  * counterpart): *symmetric = the number of entries of A each evaluated entry serves -- 1
  * (no symmetry used), 4 (quarter turns) or 8 (quarter turns and reflections);
  * *exact_differences = 1 when the window differences are formed piece by piece (see
@@ -158,8 +159,12 @@ CNSF_API int cnsf_geometry_shape(const cnsf_geometry *geom, int32_t *n_x, int32_
 /* Forward projection y = A c (Eq. 6 with the entries of Eq. 18), detector-driven
  * gather without atomics.  image: device [batch][n_y][n_x]; sino: device
  * [batch][n_views][n_det], overwritten.  batch >= 0 (0 launches nothing).
- * Allocates its scratch (zero-padded copies of the image) stream-ordered on
- * `stream` and frees it the same way. */
+ * Allocates its scratch (zero-padded copies of the image, partial sinograms of line
+ * parts) stream-ordered on `stream` and frees it the same way
+ * (cnsf_projection_scratch_bytes gives its size).  FP32 batches on a symmetric geometry
+ * give every image the bits of its single-image call; other FP32 batches evaluate each
+ * entry once for a chunk of up to 16 images (results equal to single-image calls to FP32
+ * rounding). */
 CNSF_API int cnsf_forward_project(const cnsf_geometry *geom, const void *image, void *sino, int32_t batch,
                          int32_t dtype, void *stream);
 
@@ -169,7 +174,8 @@ CNSF_API int cnsf_forward_project(const cnsf_geometry *geom, const void *image, 
  * allocates scratch stream-ordered on `stream` (the sinogram as odd-aligned cell pairs,
  * and as even-aligned pairs too when n_det is odd or the pointer is not 8-byte aligned;
  * partial images of groups of views, summed in a fixed order; interleaved copies for
- * batch >= 2) and frees it the same way.  FP64 uses no scratch. */
+ * batch >= 2 off the symmetric path) and frees it the same way.  Batches as
+ * cnsf_forward_project.  FP64 uses no scratch. */
 CNSF_API int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch,
                       int32_t dtype, void *stream);
 
@@ -219,10 +225,11 @@ CNSF_API int cnsf_cgls(const cnsf_geometry *geom, const void *sino, void *image,
 /* CGLS on `batch` independent problems that share the geometry (the same A): sino device
  * [batch][n_views][n_det], image device [batch][n_y][n_x] (x0 in, result out), each image
  * with its own FP64 state and step lengths, the projections run once per iteration over
- * the batch.  In FP32 the projections always take the batched kernels, whose arithmetic
- * for one image does not depend on the batch's size or other members: an image's iterates
- * are bitwise the same whichever problems it is batched with (they may differ from
- * cnsf_cgls's at the FP32 rounding level).  Workspace: device, 256-byte aligned, of
+ * the batch.  In FP32 the projections take the symmetric kernels when the geometry has the
+ * symmetry (see cnsf_option) and the batched kernels otherwise, whatever the batch size;
+ * in both the arithmetic for one image does not depend on the batch's size or other
+ * members: an image's iterates are bitwise the same whichever problems it is batched with
+ * (they may differ from cnsf_cgls's at the FP32 rounding level).  Workspace: device, 256-byte aligned, of
  * cnsf_cgls_batched_workspace_bytes; `resume` continues from the state it holds.
  * batch in [0, 65535]. */
 CNSF_API size_t cnsf_cgls_batched_workspace_bytes(const cnsf_geometry *geom, int32_t batch, int32_t dtype);

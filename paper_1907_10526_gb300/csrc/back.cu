@@ -342,6 +342,8 @@ __global__ void sino_pairs_rot4_kernel(const float *__restrict__ y, const BoxF *
 {
     const int ndh = (nd + 1) >> 1, nv4 = nv >> 2;
     const long long n = 2LL * nv4 * ndh;
+    y += (long long)blockIdx.y * nv * nd;   // image y of a batch
+    y4 += 2 * n * blockIdx.y;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int o = (int)(t / ((long long)nv4 * ndh));
         const long long rem = t - (long long)o * nv4 * ndh;
@@ -523,6 +525,8 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const int nv4 = g.nv >> 2;
     const int vbeg = (int)((long long)nv4 * blockIdx.y / nsplit), vend = (int)((long long)nv4 * (blockIdx.y + 1) / nsplit);
+    y4 += 16LL * blockIdx.z * nv4 * ((g.nd + 1) >> 1);   // image z of a batch
+    partial += 4LL * blockIdx.z * nsplit * g.nx * g.ny;
     const int i = it + tx, r = rt + ty;
     const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
     const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
@@ -597,6 +601,8 @@ __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *
 {
     const int ndh = (nd + 1) >> 1, nk = nv / 8 + 1, v4 = nv >> 2;
     const long long n = 2LL * nk * ndh;
+    y += (long long)blockIdx.y * nv * nd;   // image y of a batch
+    y8 += 4 * n * blockIdx.y;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
         const int o = (int)(t / ((long long)nk * ndh));
         const long long rem = t - (long long)o * nk * ndh;
@@ -684,6 +690,8 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const int nk = g.nv / 8 + 1, nv4 = g.nv >> 2;
     const int vbeg = (int)((long long)nk * blockIdx.y / nsplit), vend = (int)((long long)nk * (blockIdx.y + 1) / nsplit);
+    y8 += 32LL * blockIdx.z * nk * ((g.nd + 1) >> 1);   // image z of a batch
+    partial += 8LL * blockIdx.z * nsplit * g.nx * g.ny;
     const int i = it + tx, r = rt + ty;
     const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
     const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
@@ -756,6 +764,8 @@ __global__ void __launch_bounds__(1024) orbit_sum8_kernel(const float *__restric
     __shared__ float s[8][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, a = threadIdx.y;
     const long long nn = (long long)n * n;
+    partial += 8LL * NS * nn * blockIdx.z;   // image z of a batch
+    img += nn * blockIdx.z;
     // source rows and columns of the eight tiles at (a, tx)
     const int rows[8] = {r0 + a, n - i0 - 32 + a, n - r0 - 32 + a, i0 + a,
                          n - r0 - 32 + a, i0 + a, r0 + a, n - i0 - 32 + a};
@@ -793,6 +803,8 @@ __global__ void __launch_bounds__(1024) orbit_sum_kernel(const float *__restrict
     __shared__ float s[4][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, a = threadIdx.y;
     const long long nn = (long long)n * n;
+    partial += 4LL * NS * nn * blockIdx.z;   // image z of a batch
+    img += nn * blockIdx.z;
     const int rows[4] = {r0 + a, n - i0 - 32 + a, n - r0 - 32 + a, i0 + a};
     const int cols[4] = {i0 + tx, r0 + tx, n - i0 - 32 + tx, n - r0 - 32 + tx};
 #pragma unroll
@@ -888,10 +900,10 @@ __global__ void __launch_bounds__(256) bp_f64_kernel(GeomConsts g, const double 
 }
 
 // The orbit sums for the view-part counts the launchers use (powers of two up to 32).
-static void launch_orbit_sum8(const float *partial, float *img, int n, int nsplit, cudaStream_t st)
+static void launch_orbit_sum8(const float *partial, float *img, int n, int nsplit, int nb, cudaStream_t st)
 {
     const unsigned nt = (unsigned)((n + 31) / 32);
-    const dim3 grd(nt, nt), blk(32, 32);
+    const dim3 grd(nt, nt, nb), blk(32, 32);
     switch (nsplit) {
         case 1: orbit_sum8_kernel<1><<<grd, blk, 0, st>>>(partial, img, n); break;
         case 2: orbit_sum8_kernel<2><<<grd, blk, 0, st>>>(partial, img, n); break;
@@ -902,10 +914,10 @@ static void launch_orbit_sum8(const float *partial, float *img, int n, int nspli
     }
 }
 
-static void launch_orbit_sum4(const float *partial, float *img, int n, int nsplit, cudaStream_t st)
+static void launch_orbit_sum4(const float *partial, float *img, int n, int nsplit, int nb, cudaStream_t st)
 {
     const unsigned nt = (unsigned)((n + 31) / 32);
-    const dim3 grd(nt, nt), blk(32, 32);
+    const dim3 grd(nt, nt, nb), blk(32, 32);
     switch (nsplit) {
         case 1: orbit_sum_kernel<1><<<grd, blk, 0, st>>>(partial, img, n); break;
         case 2: orbit_sum_kernel<2><<<grd, blk, 0, st>>>(partial, img, n); break;
@@ -962,22 +974,27 @@ static int bp_view_parts_rot8(const cnsf_geometry *geo)
     return nsplit;
 }
 
-static size_t back_rot8_alloc_bytes(const cnsf_geometry *geo)
+// Bytes of one image's scratch on the eight-value path (cell-pair records, partial images).
+static size_t back_rot8_image_bytes(const cnsf_geometry *geo)
 {
     const GeomConsts &g = geo->gc;
     const size_t y8 = 2 * (size_t)(g.nv / 8 + 1) * ((g.nd + 1) / 2) * 16 * sizeof(float);
     return y8 + (size_t)bp_view_parts_rot8(geo) * 8 * g.nx * g.ny * sizeof(float);
 }
 
-// FP32 back projection of one image by the eight-value gather (geo->sym8).
-static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *img, cudaStream_t st)
+// FP32 back projection of a batch by the eight-value gather (geo->sym8), in groups of
+// sym_batch_group() images (one grid layer per image); every image takes the kernel, view
+// parts and part order of a single-image call.
+static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t st)
 {
     const GeomConsts &g = geo->gc;
     const int nk = g.nv / 8 + 1, ndh = (g.nd + 1) / 2, n = g.nx;
     const int nsplit = bp_view_parts_rot8(geo);
     const size_t ny8 = 2 * (size_t)nk * ndh * 16;
+    const size_t per = back_rot8_image_bytes(geo);
+    const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, back_rot8_alloc_bytes(geo), st);
+    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     const double dg = g.arc ? g.ds / g.dps : 0.0;
     BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
@@ -985,15 +1002,19 @@ static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *
              (float)g.s0, (float)g.ds, (float)(g.par ? 0.0 : 1.0 / g.dps),
              (float)(g.arc ? tan(0.5 * g.tau / g.dps) / (g.ds / g.dps) : 0.0), (float)(g.arc ? -0.5 * (g.ds / g.dps) * (g.ds / g.dps) : 0.0)};
     const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
-    float *y8 = reinterpret_cast<float *>(buf), *partial = y8 + ny8;
+    float *y8 = reinterpret_cast<float *>(buf), *partial = y8 + grp * ny8;
     const long long npair = 2LL * nk * ndh;
-    sino_pairs_rot8_kernel<<<(unsigned)std::min<long long>((npair + 255) / 256, 8192), 256, 0, st>>>(
-        sino, geo->d_box, reinterpret_cast<float4 *>(y8), g.nv, g.nd);
     auto kern = g.arc ? (geo->exact ? bp_rot8_f32_kernel<true, true> : bp_rot8_f32_kernel<true, false>)
                       : (geo->exact ? bp_rot8_f32_kernel<false, true> : bp_rot8_f32_kernel<false, false>);
-    kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y8, a, geo->d_bp_order, ntx, nsplit,
-                                                                 partial, geo->d_view_cs, geo->d_tv, geo->d_tj);
-    launch_orbit_sum8(partial, img, n, nsplit, st);
+    for (int b0 = 0; b0 < batch; b0 += grp) {
+        const int gb = std::min(grp, batch - b0);
+        sino_pairs_rot8_kernel<<<dim3((unsigned)std::min<long long>((npair + 255) / 256, 8192), gb), 256, 0, st>>>(
+            sino + (size_t)b0 * g.nv * g.nd, geo->d_box, reinterpret_cast<float4 *>(y8), g.nv, g.nd);
+        kern<<<dim3(ntx * nty, nsplit, gb), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y8, a, geo->d_bp_order, ntx,
+                                                                         nsplit, partial, geo->d_view_cs, geo->d_tv,
+                                                                         geo->d_tj);
+        launch_orbit_sum8(partial, img + (size_t)b0 * n * n, n, nsplit, gb, st);
+    }
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
@@ -1011,22 +1032,25 @@ static int bp_view_parts_rot4(const cnsf_geometry *geo)
     return nsplit;
 }
 
-static size_t back_rot4_alloc_bytes(const cnsf_geometry *geo)
+static size_t back_rot4_image_bytes(const cnsf_geometry *geo)
 {
     const GeomConsts &g = geo->gc;
     const size_t y4 = 2 * (size_t)(g.nv / 4) * ((g.nd + 1) / 2) * 8 * sizeof(float);
     return y4 + (size_t)bp_view_parts_rot4(geo) * 4 * g.nx * g.ny * sizeof(float);
 }
 
-// FP32 back projection of one image by the four-rotation gather (geo->sym).
-static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *img, cudaStream_t st)
+// FP32 back projection of a batch by the four-rotation gather (geo->sym), grouped as
+// launch_back_rot8.
+static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t st)
 {
     const GeomConsts &g = geo->gc;
     const int nv4 = g.nv / 4, ndh = (g.nd + 1) / 2, n = g.nx;
     const int nsplit = bp_view_parts_rot4(geo);
     const size_t ny4 = 2 * (size_t)nv4 * ndh * 8;
+    const size_t per = back_rot4_image_bytes(geo);
+    const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, back_rot4_alloc_bytes(geo), st);
+    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     const double dg = g.arc ? g.ds / g.dps : 0.0;
     BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
@@ -1034,27 +1058,38 @@ static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *
              (float)g.s0, (float)g.ds, (float)(g.par ? 0.0 : 1.0 / g.dps),
              (float)(g.arc ? tan(0.5 * g.tau / g.dps) / (g.ds / g.dps) : 0.0), (float)(g.arc ? -0.5 * (g.ds / g.dps) * (g.ds / g.dps) : 0.0)};
     const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
-    float *y4 = reinterpret_cast<float *>(buf), *partial = y4 + ny4;
+    float *y4 = reinterpret_cast<float *>(buf), *partial = y4 + grp * ny4;
     const long long npair = 2LL * nv4 * ndh;
-    sino_pairs_rot4_kernel<<<(unsigned)std::min<long long>((npair + 255) / 256, 8192), 256, 0, st>>>(
-        sino, geo->d_box, reinterpret_cast<float4 *>(y4), g.nv, g.nd);
     auto kern = g.arc ? (geo->exact ? bp_rot4_f32_kernel<true, true> : bp_rot4_f32_kernel<true, false>)
                       : (geo->exact ? bp_rot4_f32_kernel<false, true> : bp_rot4_f32_kernel<false, false>);
-    kern<<<dim3(ntx * nty, nsplit), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y4, a, geo->d_bp_order, ntx,
-                                                                 nsplit, partial, geo->d_view_cs, geo->d_tv,
-                                                                 geo->d_tj);
-    launch_orbit_sum4(partial, img, n, nsplit, st);
+    for (int b0 = 0; b0 < batch; b0 += grp) {
+        const int gb = std::min(grp, batch - b0);
+        sino_pairs_rot4_kernel<<<dim3((unsigned)std::min<long long>((npair + 255) / 256, 8192), gb), 256, 0, st>>>(
+            sino + (size_t)b0 * g.nv * g.nd, geo->d_box, reinterpret_cast<float4 *>(y4), g.nv, g.nd);
+        kern<<<dim3(ntx * nty, nsplit, gb), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y4, a, geo->d_bp_order, ntx,
+                                                                         nsplit, partial, geo->d_view_cs, geo->d_tv,
+                                                                         geo->d_tj);
+        launch_orbit_sum4(partial, img + (size_t)b0 * n * n, n, nsplit, gb, st);
+    }
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
+int launch_back_sym(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t st)
+{
+    if (batch == 0) return CNSF_OK;
+    if (geo->sym8) return launch_back_rot8(geo, sino, img, batch, st);
+    if (geo->sym) return launch_back_rot4(geo, sino, img, batch, st);
+    return CNSF_ERR_UNSUPPORTED;
+}
+
 size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 {
     if (batch <= 0 || dtype != CNSF_F32) return 0;
+    if (geo->sym8) return (size_t)sym_batch_group(back_rot8_image_bytes(geo), batch) * back_rot8_image_bytes(geo);
+    if (geo->sym) return (size_t)sym_batch_group(back_rot4_image_bytes(geo), batch) * back_rot4_image_bytes(geo);
     if (batch >= 2) return back_batch_alloc_bytes(geo);
-    if (geo->sym8) return back_rot8_alloc_bytes(geo);
-    if (geo->sym) return back_rot4_alloc_bytes(geo);
     const GeomConsts &g = geo->gc;
     const int nsplit = bp_view_parts(geo, batch);
     const size_t npair = (size_t)batch * g.nv * ((g.nd + 1) / 2);
@@ -1065,9 +1100,9 @@ size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch, int dtype, cudaStream_t st)
 {
     if (batch == 0) return CNSF_OK;
+    if (dtype == CNSF_F32 && (geo->sym8 || geo->sym))
+        return launch_back_sym(geo, (const float *)sino, (float *)img, batch, st);
     if (dtype == CNSF_F32 && batch >= 2) return launch_back_batch(geo, (const float *)sino, (float *)img, batch, st);
-    if (dtype == CNSF_F32 && geo->sym8) return launch_back_rot8(geo, (const float *)sino, (float *)img, st);
-    if (dtype == CNSF_F32 && geo->sym) return launch_back_rot4(geo, (const float *)sino, (float *)img, st);
     const GeomConsts &g = geo->gc;
     dim3 blk(BP_T, BP_T), grd((g.nx + BP_T - 1) / BP_T, (g.ny + BP_T - 1) / BP_T, batch);
     if (dtype == CNSF_F32) {

@@ -47,6 +47,23 @@ size_t back_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype);
 size_t forward_batch_alloc_bytes(const cnsf_geometry *geo);
 size_t back_batch_alloc_bytes(const cnsf_geometry *geo);
 
+// FP32 projections of a batch through the symmetric kernels (geo->sym8 or geo->sym;
+// CNSF_ERR_UNSUPPORTED otherwise): each image as in a single-image call, so its result does
+// not depend on the batch.
+int launch_forward_sym(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t stream);
+int launch_back_sym(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t stream);
+
+// Images per launch group of the symmetric kernels: as many as keep the group's scratch
+// within 256 MiB, at least one, at most the batch.
+inline int sym_batch_group(size_t per_image_bytes, int batch)
+{
+    const size_t cap = (size_t)256 << 20;
+    size_t g = per_image_bytes > 0 ? cap / per_image_bytes : (size_t)batch;
+    if (g < 1) g = 1;
+    if (g > (size_t)batch) g = (size_t)batch;
+    return batch > 0 ? (int)g : 1;
+}
+
 // Batches of FP32 images (batch.cu): each entry evaluated once per chunk of <= 16 images.
 int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t stream);
 int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, int batch, cudaStream_t stream);

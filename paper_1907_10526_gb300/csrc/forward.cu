@@ -305,6 +305,9 @@ __global__ void pad_rot4_kernel(const float *__restrict__ img, float4 *__restric
 {
     __shared__ float s[4][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    img += (long long)blockIdx.z * n * n;   // image z of a batch: its own copies
+    P4 += (long long)blockIdx.z * n * pitch;
+    T4 += (long long)blockIdx.z * n * pitch;
     auto at = [&](int row, int col) { return (row >= 0 && row < n && col >= 0 && col < n) ? img[(long long)row * n + col] : 0.f; };
     for (int a = threadIdx.y; a < 32; a += blockDim.y) {
         s[0][a][tx] = at(r0 + a, i0 + tx);                      // c[m]       = img[r][i]
@@ -434,6 +437,9 @@ __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict_
 {
     const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
     if (q >= nr4) return;
+    const long long b = blockIdx.y;   // image of a batch (one kernel and part order for every image)
+    imgP += b * (pitch - 2 * pad) * pitch;
+    imgT += b * (pitch - 2 * pad) * pitch;
     RayF R = rays[q];
     if (nsplit > 1) {
         const int l0 = (int)((long long)R.nrows * blockIdx.z / nsplit), l1 = (int)((long long)R.nrows * (blockIdx.z + 1) / nsplit);
@@ -464,7 +470,7 @@ __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict_
 #pragma unroll
         for (int k = 0; k < 4; ++k) out[k] *= nrm;
     }
-    float *dst = nsplit > 1 ? partial + (long long)blockIdx.z * nr : sino;
+    float *dst = nsplit > 1 ? partial + ((long long)blockIdx.z * gridDim.y + b) * nr : sino + b * nr;
 #pragma unroll
     for (int k = 0; k < 4; ++k) dst[q + (long long)k * nr4] = out[k];
 }
@@ -487,6 +493,9 @@ __global__ void pad_rot8_kernel(const float *__restrict__ img, float4 *__restric
 {
     __shared__ float s[8][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
+    img += (long long)blockIdx.z * n * n;   // image z of a batch: its own copies
+    P8 += 2LL * blockIdx.z * n * pitch;
+    T8 += 2LL * blockIdx.z * n * pitch;
     auto at = [&](int row, int col) { return (row >= 0 && row < n && col >= 0 && col < n) ? img[(long long)row * n + col] : 0.f; };
     for (int a = threadIdx.y; a < 32; a += blockDim.y) {
         s[0][a][tx] = at(r0 + a, i0 + tx);                      // c[q]        = img[r][i]
@@ -564,9 +573,12 @@ __device__ __forceinline__ void walk2_rot8(const RayF &R, const float *__restric
     const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);
     const float2 B2 = make_float2(B, B), ne1 = make_float2(-1.0f, -1.0f), nhC2 = make_float2(-hC, -hC);
     const float hw = R.hw;
-    float2 acc[8], part[8];
+    // one sum per value and line parity, without the 16-line blocks of the other walks: the
+    // sixteen block registers would cost a third of the resident warps, and a line part (an
+    // eighth of the ray's lines, fp_line_parts_rot8) is short enough for plain FP32 sums
+    float2 acc[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = part[k] = make_float2(0.f, 0.f);
+    for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
     int rr = 0;
     for (; rr + 1 < R.nrows; rr += 2) {
         int ilo0, ilo1;
@@ -574,23 +586,13 @@ __device__ __forceinline__ void walk2_rot8(const RayF &R, const float *__restric
         fx_window(A, ilo0, rho0);
         fx_window(A + G, ilo1, rho1);
         line_pair_sum_rot8<KC, EXACT>(base + 8LL * ilo0, base + pitch8 + 8LL * ilo1, kc,
-                                      make_float2(rho0 - hw, rho1 - hw), er2, kap2, B2, ne1, q, piC, iC, nhC2, part);
+                                      make_float2(rho0 - hw, rho1 - hw), er2, kap2, B2, ne1, q, piC, iC, nhC2, acc);
         A += 2 * G;
         er2 = __fadd2_rn(er2, de2);
         base += 2 * pitch8;
-        if ((rr & 15) == 14) {   // blocked summation: partial sums of 16 lines
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                acc[k] = __fadd2_rn(acc[k], part[k]);
-                part[k] = make_float2(0.f, 0.f);
-            }
-        }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        acc[k] = __fadd2_rn(acc[k], part[k]);
-        out[k] = acc[k].x + acc[k].y;
-    }
+    for (int k = 0; k < 8; ++k) out[k] = acc[k].x + acc[k].y;
     if (rr < R.nrows) {   // odd line count: the last line alone
         int ilo;
         float rho;
@@ -619,6 +621,9 @@ __global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict_
 {
     const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
     if (q >= nr8) return;
+    const long long b = blockIdx.y;   // image of a batch (one kernel and part order for every image)
+    imgP += 8 * b * (pitch - 2 * pad) * pitch;
+    imgT += 8 * b * (pitch - 2 * pad) * pitch;
     RayF R = rays[q];
     if (nsplit > 1) {
         const int l0 = (int)((long long)R.nrows * blockIdx.z / nsplit), l1 = (int)((long long)R.nrows * (blockIdx.z + 1) / nsplit);
@@ -648,7 +653,7 @@ __global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict_
 #pragma unroll
         for (int k = 0; k < 8; ++k) out[k] *= nrm;
     }
-    float *dst = nsplit > 1 ? partial + (long long)blockIdx.z * nv * nd : sino;
+    float *dst = nsplit > 1 ? partial + ((long long)blockIdx.z * gridDim.y + b) * nv * nd : sino + b * nv * nd;
     const int k = q / nd, j = q - k * nd, v4 = nv >> 2;
     const bool self = k == 0 || 8 * k == nv;   // its own mirror image up to a quarter turn
 #pragma unroll
@@ -751,26 +756,16 @@ static int fp_line_parts_rot4(const cnsf_geometry *geo)
     return nsplit;
 }
 
-static size_t forward_rot4_alloc_bytes(const cnsf_geometry *geo)
+// Line parts of the eight-value walk (views 0 .. V/8): always 8.  They fill the GPU (the
+// base views alone give few rays) and keep each of the walk's unblocked sums to an eighth
+// of a ray's lines.
+static int fp_line_parts_rot8(const cnsf_geometry *)
 {
-    const GeomConsts &g = geo->gc;
-    const int nsplit = fp_line_parts_rot4(geo);
-    const size_t img4 = 2 * (size_t)g.nx * (g.nx + 2 * geo->pad) * sizeof(float4);
-    return img4 + (nsplit > 1 ? (size_t)nsplit * g.nv * g.nd * sizeof(float) : 0);
+    return 8;
 }
 
-// Line parts of the eight-value walk (views 0 .. V/8).
-static int fp_line_parts_rot8(const cnsf_geometry *geo)
-{
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, geo->device);
-    const long long blocks = ((long long)(geo->gc.nv / 8 + 1) * geo->gc.nd + 127) / 128;
-    int nsplit = 1;
-    while (nsplit < 8 && blocks * nsplit < 128LL * std::max(sms, 1)) nsplit *= 2;
-    return nsplit;
-}
-
-static size_t forward_rot8_alloc_bytes(const cnsf_geometry *geo)
+// Bytes of one image's scratch on the eight-value path (its copies and part sums).
+static size_t forward_rot8_image_bytes(const cnsf_geometry *geo)
 {
     const GeomConsts &g = geo->gc;
     const int nsplit = fp_line_parts_rot8(geo);
@@ -778,60 +773,96 @@ static size_t forward_rot8_alloc_bytes(const cnsf_geometry *geo)
     return img8 + (nsplit > 1 ? (size_t)nsplit * g.nv * g.nd * sizeof(float) : 0);
 }
 
-// FP32 forward projection of one image by the eight-value kernel (geo->sym8).
-static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float *sino, cudaStream_t st)
+static size_t forward_rot4_image_bytes(const cnsf_geometry *geo)
+{
+    const GeomConsts &g = geo->gc;
+    const int nsplit = fp_line_parts_rot4(geo);
+    const size_t img4 = 2 * (size_t)g.nx * (g.nx + 2 * geo->pad) * sizeof(float4);
+    return img4 + (nsplit > 1 ? (size_t)nsplit * g.nv * g.nd * sizeof(float) : 0);
+}
+
+// FP32 forward projection of a batch by the eight-value kernel (geo->sym8): groups of
+// sym_batch_group() images, each launch covering a group (one grid row per image).  Every
+// image takes the kernel, line parts and part order of a single-image call, so its result
+// does not depend on the batch or the group.
+static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t st)
 {
     const GeomConsts &g = geo->gc;
     const int n = g.nx, pad = geo->pad, pitch = n + 2 * pad;
     const int nr = g.nv * g.nd, nr8 = (g.nv / 8 + 1) * g.nd;
     const int nsplit = fp_line_parts_rot8(geo);
+    const size_t per = forward_rot8_image_bytes(geo);
+    const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, forward_rot8_alloc_bytes(geo), st);
+    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
-    float4 *P8 = reinterpret_cast<float4 *>(buf), *T8 = P8 + 2 * (size_t)n * pitch;
-    float *partial = nsplit > 1 ? reinterpret_cast<float *>(T8 + 2 * (size_t)n * pitch) : nullptr;
+    float4 *P8 = reinterpret_cast<float4 *>(buf), *T8 = P8 + 2 * (size_t)grp * n * pitch;
+    float *partial = nsplit > 1 ? reinterpret_cast<float *>(T8 + 2 * (size_t)grp * n * pitch) : nullptr;
     const unsigned nt = (unsigned)((n + 31) / 32);
-    pad_rot8_kernel<<<dim3(nt, nt), dim3(32, 32), 0, st>>>(img, P8, T8, n, pad, pitch);
-    (geo->exact ? fp_rot8_f32_kernel<true> : fp_rot8_f32_kernel<false>)<<<dim3((nr8 + 127) / 128, 1, nsplit), 128, 0, st>>>(
-        geo->d_fp_order8, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), reinterpret_cast<const float *>(P8),
-        reinterpret_cast<const float *>(T8), pitch, pad, g.nv, g.nd, nr8, sino, nsplit, partial);
-    if (nsplit > 1)
-        launch_fp_sum_parts(partial, sino, nr, nsplit, st);
+    for (int b0 = 0; b0 < batch; b0 += grp) {
+        const int gb = std::min(grp, batch - b0);
+        const float *im = img + (size_t)b0 * n * n;
+        float *sn = sino + (size_t)b0 * nr;
+        pad_rot8_kernel<<<dim3(nt, nt, gb), dim3(32, 32), 0, st>>>(im, P8, T8, n, pad, pitch);
+        (geo->exact ? fp_rot8_f32_kernel<true> : fp_rot8_f32_kernel<false>)<<<dim3((nr8 + 127) / 128, gb, nsplit), 128, 0, st>>>(
+            geo->d_fp_order8, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), reinterpret_cast<const float *>(P8),
+            reinterpret_cast<const float *>(T8), pitch, pad, g.nv, g.nd, nr8, sn, nsplit, partial);
+        if (nsplit > 1)
+            launch_fp_sum_parts(partial, sn, (long long)gb * nr, nsplit, st);
+    }
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
-// FP32 forward projection of one image by the four-rotation kernel (geo->sym).
-static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float *sino, cudaStream_t st)
+// FP32 forward projection of a batch by the four-rotation kernel (geo->sym), grouped as
+// launch_forward_rot8.
+static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t st)
 {
     const GeomConsts &g = geo->gc;
     const int n = g.nx, pad = geo->pad, pitch = n + 2 * pad;
     const int nr = g.nv * g.nd, nr4 = (g.nv / 4) * g.nd;
     const int nsplit = fp_line_parts_rot4(geo);
+    const size_t per = forward_rot4_image_bytes(geo);
+    const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, forward_rot4_alloc_bytes(geo), st);
+    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
-    float4 *P4 = reinterpret_cast<float4 *>(buf), *T4 = P4 + (size_t)n * pitch;
-    float *partial = nsplit > 1 ? reinterpret_cast<float *>(T4 + (size_t)n * pitch) : nullptr;
+    float4 *P4 = reinterpret_cast<float4 *>(buf), *T4 = P4 + (size_t)grp * n * pitch;
+    float *partial = nsplit > 1 ? reinterpret_cast<float *>(T4 + (size_t)grp * n * pitch) : nullptr;
     const unsigned nt = (unsigned)((n + 31) / 32);
-    pad_rot4_kernel<<<dim3(nt, nt), dim3(32, 32), 0, st>>>(img, P4, T4, n, pad, pitch);
-    (geo->exact ? fp_rot4_f32_kernel<true> : fp_rot4_f32_kernel<false>)<<<dim3((nr4 + 127) / 128, 1, nsplit), 128, 0, st>>>(
-        geo->d_fp_order4, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P4, T4, pitch, pad, nr, nr4, sino,
-        nsplit, partial);
-    if (nsplit > 1)
-        launch_fp_sum_parts(partial, sino, nr, nsplit, st);
+    for (int b0 = 0; b0 < batch; b0 += grp) {
+        const int gb = std::min(grp, batch - b0);
+        const float *im = img + (size_t)b0 * n * n;
+        float *sn = sino + (size_t)b0 * nr;
+        pad_rot4_kernel<<<dim3(nt, nt, gb), dim3(32, 32), 0, st>>>(im, P4, T4, n, pad, pitch);
+        (geo->exact ? fp_rot4_f32_kernel<true> : fp_rot4_f32_kernel<false>)<<<dim3((nr4 + 127) / 128, gb, nsplit), 128, 0, st>>>(
+            geo->d_fp_order4, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P4, T4, pitch, pad, nr, nr4, sn,
+            nsplit, partial);
+        if (nsplit > 1)
+            launch_fp_sum_parts(partial, sn, (long long)gb * nr, nsplit, st);
+    }
     cudaFreeAsync(buf, st);
     e = cudaGetLastError();
     return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
 }
 
+int launch_forward_sym(const cnsf_geometry *geo, const float *img, float *sino, int batch, cudaStream_t st)
+{
+    if (batch == 0) return CNSF_OK;
+    if (geo->sym8) return launch_forward_rot8(geo, img, sino, batch, st);
+    if (geo->sym) return launch_forward_rot4(geo, img, sino, batch, st);
+    return CNSF_ERR_UNSUPPORTED;
+}
+
 size_t forward_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 {
     if (batch <= 0) return 0;
+    if (dtype == CNSF_F32 && geo->sym8)
+        return (size_t)sym_batch_group(forward_rot8_image_bytes(geo), batch) * forward_rot8_image_bytes(geo);
+    if (dtype == CNSF_F32 && geo->sym)
+        return (size_t)sym_batch_group(forward_rot4_image_bytes(geo), batch) * forward_rot4_image_bytes(geo);
     if (dtype == CNSF_F32 && batch >= 2) return forward_batch_alloc_bytes(geo);
-    if (dtype == CNSF_F32 && geo->sym8) return forward_rot8_alloc_bytes(geo);
-    if (dtype == CNSF_F32 && geo->sym) return forward_rot4_alloc_bytes(geo);
     size_t bytes = forward_scratch_bytes(geo, batch, dtype);   // padded copies
     if (dtype == CNSF_F32) {
         const int nsplit = fp_line_parts(geo);
@@ -843,9 +874,9 @@ size_t forward_alloc_bytes(const cnsf_geometry *geo, int batch, int dtype)
 int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int batch, int dtype, cudaStream_t st)
 {
     if (batch == 0) return CNSF_OK;
+    if (dtype == CNSF_F32 && (geo->sym8 || geo->sym))
+        return launch_forward_sym(geo, (const float *)img, (float *)sino, batch, st);
     if (dtype == CNSF_F32 && batch >= 2) return launch_forward_batch(geo, (const float *)img, (float *)sino, batch, st);
-    if (dtype == CNSF_F32 && geo->sym8) return launch_forward_rot8(geo, (const float *)img, (float *)sino, st);
-    if (dtype == CNSF_F32 && geo->sym) return launch_forward_rot4(geo, (const float *)img, (float *)sino, st);
     const GeomConsts &g = geo->gc;
     const int nr = g.nv * g.nd;
     int pitchP, pitchT;

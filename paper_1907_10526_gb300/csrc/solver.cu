@@ -315,9 +315,11 @@ static int cgls_impl(const cnsf_geometry *geo, const T *y, T *x, int iters, int 
 // ================================================================ batched CGLS
 // CGLS on a batch of independent problems with one geometry (the same A): each image keeps
 // its own FP64 state and step lengths; the projections run once per iteration over the
-// whole batch.  In FP32 they always take the batched kernels (batch.cu), whose arithmetic
-// per image does not depend on the batch's size or other members, so every iterate is the
-// same whichever requests it is batched with.
+// whole batch.  In FP32 they take the symmetric kernels when the geometry has the symmetry
+// (each image projected as in a single-image call) and the batched kernels (batch.cu)
+// otherwise, whatever the batch size; in both the arithmetic per image does not depend on
+// the batch's size or other members, so every iterate is the same whichever requests it is
+// batched with.
 
 // workspace: [ scal (B x 8) | part (B x RED_BLOCKS) | x64 | p64 | r64 | pT | sT | qT | rT ], each B x
 static size_t cglsb_layout(const cnsf_geometry *geo, int B, int dtype, SolverWs *w, void *base)
@@ -443,6 +445,7 @@ static void sumsq_batched(const T *a, size_t n, int B, double *part, double *sca
 template <typename T>
 static int proj_fwd_b(const cnsf_geometry *geo, const T *x, T *y, int B, int dtype, cudaStream_t st)
 {
+    if (dtype == CNSF_F32 && (geo->sym8 || geo->sym)) return launch_forward_sym(geo, (const float *)x, (float *)y, B, st);
     if (dtype == CNSF_F32) return launch_forward_batch(geo, (const float *)x, (float *)y, B, st);
     return launch_forward(geo, x, y, B, dtype, st);
 }
@@ -450,6 +453,7 @@ static int proj_fwd_b(const cnsf_geometry *geo, const T *x, T *y, int B, int dty
 template <typename T>
 static int proj_back_b(const cnsf_geometry *geo, const T *y, T *x, int B, int dtype, cudaStream_t st)
 {
+    if (dtype == CNSF_F32 && (geo->sym8 || geo->sym)) return launch_back_sym(geo, (const float *)y, (float *)x, B, st);
     if (dtype == CNSF_F32) return launch_back_batch(geo, (const float *)y, (float *)x, B, st);
     return launch_back(geo, y, x, B, dtype, st);
 }

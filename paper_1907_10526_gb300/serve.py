@@ -137,11 +137,13 @@ class ReconServer:
 
     def batch_footprint(self, n: int, n_views: int, batch: int) -> int:
         """Device bytes of a batched job: sinograms, images, batched workspace and the
-        batched projectors' interleaved copies (chunks of up to 16 images)."""
+        projections' scratch (the symmetric kernels' copies of a launch group of the batch,
+        or the batched kernels' interleaved copies of a chunk of up to 16 images)."""
         g = self.geometry(n, n_views)
         ws = int(_lib.lib.cnsf_cgls_batched_workspace_bytes(g.handle, batch, CNSF_F32))
-        # batched CGLS projects through the batched kernels whatever the batch
-        chunk = max(g.scratch_bytes("forward", 2), g.scratch_bytes("back", 2))
+        # batched CGLS takes the batch path even for one image: the larger of the batch's
+        # own scratch and a two-image batch's covers both kinds of kernels
+        chunk = max(g.scratch_bytes(op, b) for op in ("forward", "back") for b in (2, max(batch, 2)))
         return batch * (g.n_views * g.n_det * 4 + n * n * 4) + ws + 512 + chunk
 
     # ------------------------------------------------------------------ serving

@@ -399,15 +399,25 @@ def run_cnsf(args):
     if world == 1:
         line["general_kernels_512x720"] = bench_general(dev, img, nnz, peak_ops)
     if world == 1 and not args.no_extras:   # the extra lines are single-GPU measurements
-        line["serving"] = bench_serving(args, dev)
-        line["reconstruction_2048"] = bench_solvers(dev)
-        line["batch16_512x360"] = bench_batch16(dev)
-        line["e4_ladder"] = bench_e4_ladder(dev)
-        line["reference_projector"] = bench_reference(dev)
-        line["asd_pocs_limited_view"] = bench_asd_pocs(dev)
-        line["detector_kinds_512x720"] = bench_detector_kinds(dev)
-        line["p50_recon_latency_s"] = line["serving"]["batched"].get("p50_s")
-        line["p99_recon_latency_s"] = line["serving"]["batched"].get("p99_s")
+        want = set(args.extras.split(",")) if args.extras else set(EXTRAS)
+        if "serving" in want:
+            line["serving"] = bench_serving(args, dev)
+            served = line["serving"][SERVED_MODE]
+            line["p50_recon_latency_s"] = served.get("p50_s")
+            line["p99_recon_latency_s"] = served.get("p99_s")
+            line["served_mode"] = SERVED_MODE
+        if "solvers" in want:
+            line["reconstruction_2048"] = bench_solvers(dev)
+        if "batch16" in want:
+            line["batch16_512x360"] = bench_batch16(dev)
+        if "e4" in want:
+            line["e4_ladder"] = bench_e4_ladder(dev)
+        if "reference" in want:
+            line["reference_projector"] = bench_reference(dev)
+        if "asd_pocs" in want:
+            line["asd_pocs_limited_view"] = bench_asd_pocs(dev)
+        if "kinds" in want:
+            line["detector_kinds_512x720"] = bench_detector_kinds(dev)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         r, dt, thr, desc = oracle_sample_rate(720)
@@ -708,6 +718,11 @@ def bench_asd_pocs(dev, iters: int = 200):
     return out
 
 
+EXTRAS = ("serving", "solvers", "batch16", "e4", "reference", "asd_pocs", "kinds")
+# the serving mode whose latencies the line's p50/p99 keys report (the server's default)
+SERVED_MODE = "continuous"
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,6 +732,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip serving / reconstruction / batch lines")
     ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--extras", default="", help="comma-separated subset of the extra lines: " + ",".join(EXTRAS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -162,14 +162,15 @@ def test_symmetric_batches_bitwise_single(cnsf, name, nb):
 
 
 def test_symmetric_batch_in_groups(cnsf):
-    """At 512^2 x 720 x 888 a batch's scratch is held to 256 MiB by launching it in groups
-    (3 images per back-projection group): images in every group, the last one ragged, keep
-    the bits of their single-image calls."""
-    g = config_geometry(2)
+    """At 512^2 x 360 x 888 a batch of 11 keeps its scratch within 256 MiB by launching in
+    groups, the last one ragged; every image keeps the bits of its single-image call."""
+    g = config_geometry(4)
     geom = cnsf.Geometry(g)
-    nb = 7
-    assert geom.scratch_bytes("back", nb) < geom.scratch_bytes("back", 1) * nb
-    assert geom.scratch_bytes("back", nb) <= 256 << 20
+    nb = 11
+    for op in ("forward", "back"):
+        one, many = geom.scratch_bytes(op, 1), geom.scratch_bytes(op, nb)
+        assert many <= 256 << 20 and many % one == 0
+        assert 1 < many // one < nb and nb % (many // one) != 0
     rng = np.random.default_rng(11)
     xb = torch.tensor(rng.uniform(0.0, 1.0, (nb, g.ny, g.nx)), dtype=torch.float32, device="cuda")
     yb = cnsf.forward_project(geom, xb)

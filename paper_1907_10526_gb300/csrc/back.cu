@@ -508,7 +508,7 @@ __device__ __forceinline__ void bp_view2_rot4(const BpPixel4 &Qa, const BpPixel4
 // partial images T_k (view part s: partial[(4 s + k)][N][N]).  The quad's pixel pairs are
 // gathered along the axis that moves the projection least, the two pairings in two
 // branches (uniform over the block) so that every accumulator keeps its register.
-template <bool ARC, bool EXACT>
+template <bool ARC, bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomConsts g, const float *__restrict__ ac,
                                                                      const float *__restrict__ y4, BpArgs a,
                                                                      const int *__restrict__ order, int ntx, int nsplit,
@@ -525,8 +525,10 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const int nv4 = g.nv >> 2;
     const int vbeg = (int)((long long)nv4 * blockIdx.y / nsplit), vend = (int)((long long)nv4 * (blockIdx.y + 1) / nsplit);
-    y4 += 16LL * blockIdx.z * nv4 * ((g.nd + 1) >> 1);   // image z of a batch
-    partial += 4LL * blockIdx.z * nsplit * g.nx * g.ny;
+    if (BATCH) {   // image z of a batch (the single-image instantiation has no offsets)
+        y4 += 16LL * blockIdx.z * nv4 * ((g.nd + 1) >> 1);
+        partial += 4LL * blockIdx.z * nsplit * g.nx * g.ny;
+    }
     const int i = it + tx, r = rt + ty;
     const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
     const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
@@ -673,7 +675,7 @@ __device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4
 
 // bp_rot4_f32_kernel over the views k = 0 .. V/8 with the eight accumulators T_0..3, U_0..3
 // per pixel: the partial images partial[8 s + c] of view part s.
-template <bool ARC, bool EXACT>
+template <bool ARC, bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomConsts g, const float *__restrict__ ac,
                                                                      const float *__restrict__ y8, BpArgs a,
                                                                      const int *__restrict__ order, int ntx, int nsplit,
@@ -690,8 +692,10 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const int nk = g.nv / 8 + 1, nv4 = g.nv >> 2;
     const int vbeg = (int)((long long)nk * blockIdx.y / nsplit), vend = (int)((long long)nk * (blockIdx.y + 1) / nsplit);
-    y8 += 32LL * blockIdx.z * nk * ((g.nd + 1) >> 1);   // image z of a batch
-    partial += 8LL * blockIdx.z * nsplit * g.nx * g.ny;
+    if (BATCH) {   // image z of a batch (the single-image instantiation has no offsets)
+        y8 += 32LL * blockIdx.z * nk * ((g.nd + 1) >> 1);
+        partial += 8LL * blockIdx.z * nsplit * g.nx * g.ny;
+    }
     const int i = it + tx, r = rt + ty;
     const bool in0 = i < g.nx && r < g.ny, in1 = i + 1 < g.nx && r < g.ny;
     const bool in2 = i < g.nx && r + 1 < g.ny, in3 = i + 1 < g.nx && r + 1 < g.ny;
@@ -757,15 +761,17 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
 // and partial[8 s + 4 + m] over the view parts s (in part order), through eight 32 x 32
 // shared-memory tiles: M (i, r) = (i, N-1-r), M R^-1 (i, r) = (r, i), M R^-2 (i, r) =
 // (N-1-i, r), M R^-3 (i, r) = (N-1-r, N-1-i).
-template <int NS>
+template <int NS, bool BATCH>
 __global__ void __launch_bounds__(1024) orbit_sum8_kernel(const float *__restrict__ partial, float *__restrict__ img,
                                                           int n)
 {
     __shared__ float s[8][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, a = threadIdx.y;
     const long long nn = (long long)n * n;
-    partial += 8LL * NS * nn * blockIdx.z;   // image z of a batch
-    img += nn * blockIdx.z;
+    if (BATCH) {   // image z of a batch
+        partial += 8LL * NS * nn * blockIdx.z;
+        img += nn * blockIdx.z;
+    }
     // source rows and columns of the eight tiles at (a, tx)
     const int rows[8] = {r0 + a, n - i0 - 32 + a, n - r0 - 32 + a, i0 + a,
                          n - r0 - 32 + a, i0 + a, r0 + a, n - i0 - 32 + a};
@@ -796,15 +802,17 @@ __global__ void __launch_bounds__(1024) orbit_sum8_kernel(const float *__restric
 // img[n] = sum_k T_k(R^-k n), T_k the sum of partial[4 s + k] over the view parts s (in part
 // order), through four 32 x 32 shared-memory tiles: R^-1 (i, r) = (r, N-1-i),
 // R^-2 (i, r) = (N-1-i, N-1-r), R^-3 (i, r) = (N-1-r, i).
-template <int NS>
+template <int NS, bool BATCH>
 __global__ void __launch_bounds__(1024) orbit_sum_kernel(const float *__restrict__ partial, float *__restrict__ img,
                                                          int n)
 {
     __shared__ float s[4][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x, a = threadIdx.y;
     const long long nn = (long long)n * n;
-    partial += 4LL * NS * nn * blockIdx.z;   // image z of a batch
-    img += nn * blockIdx.z;
+    if (BATCH) {   // image z of a batch
+        partial += 4LL * NS * nn * blockIdx.z;
+        img += nn * blockIdx.z;
+    }
     const int rows[4] = {r0 + a, n - i0 - 32 + a, n - r0 - 32 + a, i0 + a};
     const int cols[4] = {i0 + tx, r0 + tx, n - i0 - 32 + tx, n - r0 - 32 + tx};
 #pragma unroll
@@ -905,12 +913,12 @@ static void launch_orbit_sum8(const float *partial, float *img, int n, int nspli
     const unsigned nt = (unsigned)((n + 31) / 32);
     const dim3 grd(nt, nt, nb), blk(32, 32);
     switch (nsplit) {
-        case 1: orbit_sum8_kernel<1><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 2: orbit_sum8_kernel<2><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 4: orbit_sum8_kernel<4><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 8: orbit_sum8_kernel<8><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 16: orbit_sum8_kernel<16><<<grd, blk, 0, st>>>(partial, img, n); break;
-        default: orbit_sum8_kernel<32><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 1: (nb > 1 ? orbit_sum8_kernel<1, true> : orbit_sum8_kernel<1, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 2: (nb > 1 ? orbit_sum8_kernel<2, true> : orbit_sum8_kernel<2, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 4: (nb > 1 ? orbit_sum8_kernel<4, true> : orbit_sum8_kernel<4, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 8: (nb > 1 ? orbit_sum8_kernel<8, true> : orbit_sum8_kernel<8, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 16: (nb > 1 ? orbit_sum8_kernel<16, true> : orbit_sum8_kernel<16, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        default: (nb > 1 ? orbit_sum8_kernel<32, true> : orbit_sum8_kernel<32, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
     }
 }
 
@@ -919,12 +927,12 @@ static void launch_orbit_sum4(const float *partial, float *img, int n, int nspli
     const unsigned nt = (unsigned)((n + 31) / 32);
     const dim3 grd(nt, nt, nb), blk(32, 32);
     switch (nsplit) {
-        case 1: orbit_sum_kernel<1><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 2: orbit_sum_kernel<2><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 4: orbit_sum_kernel<4><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 8: orbit_sum_kernel<8><<<grd, blk, 0, st>>>(partial, img, n); break;
-        case 16: orbit_sum_kernel<16><<<grd, blk, 0, st>>>(partial, img, n); break;
-        default: orbit_sum_kernel<32><<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 1: (nb > 1 ? orbit_sum_kernel<1, true> : orbit_sum_kernel<1, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 2: (nb > 1 ? orbit_sum_kernel<2, true> : orbit_sum_kernel<2, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 4: (nb > 1 ? orbit_sum_kernel<4, true> : orbit_sum_kernel<4, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 8: (nb > 1 ? orbit_sum_kernel<8, true> : orbit_sum_kernel<8, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        case 16: (nb > 1 ? orbit_sum_kernel<16, true> : orbit_sum_kernel<16, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
+        default: (nb > 1 ? orbit_sum_kernel<32, true> : orbit_sum_kernel<32, false>)<<<grd, blk, 0, st>>>(partial, img, n); break;
     }
 }
 
@@ -1004,10 +1012,13 @@ static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *
     const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
     float *y8 = reinterpret_cast<float *>(buf), *partial = y8 + grp * ny8;
     const long long npair = 2LL * nk * ndh;
-    auto kern = g.arc ? (geo->exact ? bp_rot8_f32_kernel<true, true> : bp_rot8_f32_kernel<true, false>)
-                      : (geo->exact ? bp_rot8_f32_kernel<false, true> : bp_rot8_f32_kernel<false, false>);
+    auto kern1 = g.arc ? (geo->exact ? bp_rot8_f32_kernel<true, true, false> : bp_rot8_f32_kernel<true, false, false>)
+                       : (geo->exact ? bp_rot8_f32_kernel<false, true, false> : bp_rot8_f32_kernel<false, false, false>);
+    auto kernb = g.arc ? (geo->exact ? bp_rot8_f32_kernel<true, true, true> : bp_rot8_f32_kernel<true, false, true>)
+                       : (geo->exact ? bp_rot8_f32_kernel<false, true, true> : bp_rot8_f32_kernel<false, false, true>);
     for (int b0 = 0; b0 < batch; b0 += grp) {
         const int gb = std::min(grp, batch - b0);
+        auto kern = gb > 1 ? kernb : kern1;
         sino_pairs_rot8_kernel<<<dim3((unsigned)std::min<long long>((npair + 255) / 256, 8192), gb), 256, 0, st>>>(
             sino + (size_t)b0 * g.nv * g.nd, geo->d_box, reinterpret_cast<float4 *>(y8), g.nv, g.nd);
         kern<<<dim3(ntx * nty, nsplit, gb), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y8, a, geo->d_bp_order, ntx,
@@ -1060,10 +1071,13 @@ static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *
     const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
     float *y4 = reinterpret_cast<float *>(buf), *partial = y4 + grp * ny4;
     const long long npair = 2LL * nv4 * ndh;
-    auto kern = g.arc ? (geo->exact ? bp_rot4_f32_kernel<true, true> : bp_rot4_f32_kernel<true, false>)
-                      : (geo->exact ? bp_rot4_f32_kernel<false, true> : bp_rot4_f32_kernel<false, false>);
+    auto kern1 = g.arc ? (geo->exact ? bp_rot4_f32_kernel<true, true, false> : bp_rot4_f32_kernel<true, false, false>)
+                       : (geo->exact ? bp_rot4_f32_kernel<false, true, false> : bp_rot4_f32_kernel<false, false, false>);
+    auto kernb = g.arc ? (geo->exact ? bp_rot4_f32_kernel<true, true, true> : bp_rot4_f32_kernel<true, false, true>)
+                       : (geo->exact ? bp_rot4_f32_kernel<false, true, true> : bp_rot4_f32_kernel<false, false, true>);
     for (int b0 = 0; b0 < batch; b0 += grp) {
         const int gb = std::min(grp, batch - b0);
+        auto kern = gb > 1 ? kernb : kern1;
         sino_pairs_rot4_kernel<<<dim3((unsigned)std::min<long long>((npair + 255) / 256, 8192), gb), 256, 0, st>>>(
             sino + (size_t)b0 * g.nv * g.nd, geo->d_box, reinterpret_cast<float4 *>(y4), g.nv, g.nd);
         kern<<<dim3(ntx * nty, nsplit, gb), dim3(BP_QUAD_THREADS), 0, st>>>(g, geo->d_ac, y4, a, geo->d_bp_order, ntx,

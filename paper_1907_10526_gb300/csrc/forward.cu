@@ -300,14 +300,17 @@ static void launch_fp_sum_parts(const float *partial, float *sino, long long n, 
 
 // c4 in both zero-padded layouts (rows: P4[r][pad + i]; transposed: T4[i][pad + r]), through
 // four 32 x 32 shared-memory tiles of the image (the rotated reads stay coalesced).
+template <bool BATCH>
 __global__ void pad_rot4_kernel(const float *__restrict__ img, float4 *__restrict__ P4, float4 *__restrict__ T4, int n,
                                 int pad, int pitch)
 {
     __shared__ float s[4][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
-    img += (long long)blockIdx.z * n * n;   // image z of a batch: its own copies
-    P4 += (long long)blockIdx.z * n * pitch;
-    T4 += (long long)blockIdx.z * n * pitch;
+    if (BATCH) {   // image z of a batch: its own copies
+        img += (long long)blockIdx.z * n * n;
+        P4 += (long long)blockIdx.z * n * pitch;
+        T4 += (long long)blockIdx.z * n * pitch;
+    }
     auto at = [&](int row, int col) { return (row >= 0 && row < n && col >= 0 && col < n) ? img[(long long)row * n + col] : 0.f; };
     for (int a = threadIdx.y; a < 32; a += blockDim.y) {
         s[0][a][tx] = at(r0 + a, i0 + tx);                      // c[m]       = img[r][i]
@@ -427,7 +430,7 @@ __device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restri
 
 // One thread per ray (v, j) of views v < V/4 (and line part): the four sinogram values
 // y[v + kV/4][j], k = 0..3, written to rows v + kV/4 (nr4 = V/4 n_det rays apart).
-template <bool EXACT>
+template <bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
                                                           const BoxF *__restrict__ box, float h2q,
                                                           const float4 *__restrict__ imgP, const float4 *__restrict__ imgT,
@@ -437,9 +440,13 @@ __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict_
 {
     const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
     if (q >= nr4) return;
-    const long long b = blockIdx.y;   // image of a batch (one kernel and part order for every image)
-    imgP += b * (pitch - 2 * pad) * pitch;
-    imgT += b * (pitch - 2 * pad) * pitch;
+    // image of a batch (one kernel and part order for every image); the single-image
+    // instantiation carries no offsets (they cost the kernel its constant-bank addressing)
+    const long long b = BATCH ? blockIdx.y : 0;
+    if (BATCH) {
+        imgP += b * (pitch - 2 * pad) * pitch;
+        imgT += b * (pitch - 2 * pad) * pitch;
+    }
     RayF R = rays[q];
     if (nsplit > 1) {
         const int l0 = (int)((long long)R.nrows * blockIdx.z / nsplit), l1 = (int)((long long)R.nrows * (blockIdx.z + 1) / nsplit);
@@ -470,7 +477,7 @@ __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict_
 #pragma unroll
         for (int k = 0; k < 4; ++k) out[k] *= nrm;
     }
-    float *dst = nsplit > 1 ? partial + ((long long)blockIdx.z * gridDim.y + b) * nr : sino + b * nr;
+    float *dst = nsplit > 1 ? partial + ((long long)blockIdx.z * (BATCH ? gridDim.y : 1) + b) * nr : sino + b * nr;
 #pragma unroll
     for (int k = 0; k < 4; ++k) dst[q + (long long)k * nr4] = out[k];
 }
@@ -488,14 +495,17 @@ __global__ void __launch_bounds__(128) fp_rot4_f32_kernel(const int *__restrict_
 
 // c8 in both zero-padded layouts, 32 bytes per pixel (two float4), through eight 32 x 32
 // shared-memory tiles of the image.
+template <bool BATCH>
 __global__ void pad_rot8_kernel(const float *__restrict__ img, float4 *__restrict__ P8, float4 *__restrict__ T8, int n,
                                 int pad, int pitch)
 {
     __shared__ float s[8][32][33];
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, tx = threadIdx.x;
-    img += (long long)blockIdx.z * n * n;   // image z of a batch: its own copies
-    P8 += 2LL * blockIdx.z * n * pitch;
-    T8 += 2LL * blockIdx.z * n * pitch;
+    if (BATCH) {   // image z of a batch: its own copies
+        img += (long long)blockIdx.z * n * n;
+        P8 += 2LL * blockIdx.z * n * pitch;
+        T8 += 2LL * blockIdx.z * n * pitch;
+    }
     auto at = [&](int row, int col) { return (row >= 0 && row < n && col >= 0 && col < n) ? img[(long long)row * n + col] : 0.f; };
     for (int a = threadIdx.y; a < 32; a += blockDim.y) {
         s[0][a][tx] = at(r0 + a, i0 + tx);                      // c[q]        = img[r][i]
@@ -611,7 +621,7 @@ __device__ __forceinline__ void walk2_rot8(const RayF &R, const float *__restric
 
 // One thread per ray (k, j) of the views k = 0 .. V/8 (and line part): rotation values at rows
 // k + mV/4, mirror values at rows -k + mV/4 (mod V), cell n_det - 1 - j.
-template <bool EXACT>
+template <bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
                                                           const BoxF *__restrict__ box, float h2q,
                                                           const float *__restrict__ imgP, const float *__restrict__ imgT,
@@ -621,9 +631,11 @@ __global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict_
 {
     const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
     if (q >= nr8) return;
-    const long long b = blockIdx.y;   // image of a batch (one kernel and part order for every image)
-    imgP += 8 * b * (pitch - 2 * pad) * pitch;
-    imgT += 8 * b * (pitch - 2 * pad) * pitch;
+    const long long b = BATCH ? blockIdx.y : 0;   // image of a batch, as fp_rot4_f32_kernel
+    if (BATCH) {
+        imgP += 8 * b * (pitch - 2 * pad) * pitch;
+        imgT += 8 * b * (pitch - 2 * pad) * pitch;
+    }
     RayF R = rays[q];
     if (nsplit > 1) {
         const int l0 = (int)((long long)R.nrows * blockIdx.z / nsplit), l1 = (int)((long long)R.nrows * (blockIdx.z + 1) / nsplit);
@@ -653,7 +665,8 @@ __global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict_
 #pragma unroll
         for (int k = 0; k < 8; ++k) out[k] *= nrm;
     }
-    float *dst = nsplit > 1 ? partial + ((long long)blockIdx.z * gridDim.y + b) * nv * nd : sino + b * nv * nd;
+    float *dst = nsplit > 1 ? partial + ((long long)blockIdx.z * (BATCH ? gridDim.y : 1) + b) * nv * nd
+                            : sino + b * nv * nd;
     const int k = q / nd, j = q - k * nd, v4 = nv >> 2;
     const bool self = k == 0 || 8 * k == nv;   // its own mirror image up to a quarter turn
 #pragma unroll
@@ -803,8 +816,11 @@ static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float
         const int gb = std::min(grp, batch - b0);
         const float *im = img + (size_t)b0 * n * n;
         float *sn = sino + (size_t)b0 * nr;
-        pad_rot8_kernel<<<dim3(nt, nt, gb), dim3(32, 32), 0, st>>>(im, P8, T8, n, pad, pitch);
-        (geo->exact ? fp_rot8_f32_kernel<true> : fp_rot8_f32_kernel<false>)<<<dim3((nr8 + 127) / 128, gb, nsplit), 128, 0, st>>>(
+        (gb > 1 ? pad_rot8_kernel<true> : pad_rot8_kernel<false>)<<<dim3(nt, nt, gb), dim3(32, 32), 0, st>>>(
+            im, P8, T8, n, pad, pitch);
+        auto kern = gb > 1 ? (geo->exact ? fp_rot8_f32_kernel<true, true> : fp_rot8_f32_kernel<false, true>)
+                           : (geo->exact ? fp_rot8_f32_kernel<true, false> : fp_rot8_f32_kernel<false, false>);
+        kern<<<dim3((nr8 + 127) / 128, gb, nsplit), 128, 0, st>>>(
             geo->d_fp_order8, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), reinterpret_cast<const float *>(P8),
             reinterpret_cast<const float *>(T8), pitch, pad, g.nv, g.nd, nr8, sn, nsplit, partial);
         if (nsplit > 1)
@@ -835,8 +851,11 @@ static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float
         const int gb = std::min(grp, batch - b0);
         const float *im = img + (size_t)b0 * n * n;
         float *sn = sino + (size_t)b0 * nr;
-        pad_rot4_kernel<<<dim3(nt, nt, gb), dim3(32, 32), 0, st>>>(im, P4, T4, n, pad, pitch);
-        (geo->exact ? fp_rot4_f32_kernel<true> : fp_rot4_f32_kernel<false>)<<<dim3((nr4 + 127) / 128, gb, nsplit), 128, 0, st>>>(
+        (gb > 1 ? pad_rot4_kernel<true> : pad_rot4_kernel<false>)<<<dim3(nt, nt, gb), dim3(32, 32), 0, st>>>(
+            im, P4, T4, n, pad, pitch);
+        auto kern = gb > 1 ? (geo->exact ? fp_rot4_f32_kernel<true, true> : fp_rot4_f32_kernel<false, true>)
+                           : (geo->exact ? fp_rot4_f32_kernel<true, false> : fp_rot4_f32_kernel<false, false>);
+        kern<<<dim3((nr4 + 127) / 128, gb, nsplit), 128, 0, st>>>(
             geo->d_fp_order4, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), P4, T4, pitch, pad, nr, nr4, sn,
             nsplit, partial);
         if (nsplit > 1)

@@ -283,6 +283,20 @@ struct BpWindow {
 }  // namespace cnsf
 
 // Host-side geometry object behind the opaque handle.
+// Blocks of the eight-value forward walk: FP8_VT consecutive base views x FP8_CT consecutive
+// cells (128 threads).  Rays of neighbouring views and cells cross nearly the same pixels, so
+// a block of a few views over fewer cells walks a narrower band of the image than 128 cells of
+// one view, and more of its loads hit L1.
+constexpr int FP8_VT = 4;
+constexpr int FP8_CT = 128 / FP8_VT;
+#ifdef __CUDACC__
+#define CNSF_HD __host__ __device__
+#else
+#define CNSF_HD
+#endif
+CNSF_HD inline int fp8_cell_tiles(int nd) { return (nd + FP8_CT - 1) / FP8_CT; }
+CNSF_HD inline int fp8_blocks(int nv, int nd) { return ((nv / 8 + 1 + FP8_VT - 1) / FP8_VT) * fp8_cell_tiles(nd); }
+
 struct cnsf_geometry {
     cnsf::GeomConsts gc;
     int device;

@@ -619,18 +619,21 @@ __device__ __forceinline__ void walk2_rot8(const RayF &R, const float *__restric
     }
 }
 
-// One thread per ray (k, j) of the views k = 0 .. V/8 (and line part): rotation values at rows
-// k + mV/4, mirror values at rows -k + mV/4 (mod V), cell n_det - 1 - j.
+// One thread per ray (k, j) of the views k = 0 .. V/8 (and line part), blocks of FP8_VT views x
+// FP8_CT cells: rotation values at rows k + mV/4, mirror values at rows -k + mV/4 (mod V),
+// cell n_det - 1 - j.
 template <bool EXACT, bool BATCH>
 __global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict__ order, const RayF *__restrict__ rays,
                                                           const BoxF *__restrict__ box, float h2q,
                                                           const float *__restrict__ imgP, const float *__restrict__ imgT,
-                                                          int pitch, int pad, int nv, int nd, int nr8,
+                                                          int pitch, int pad, int nv, int nd,
                                                           float *__restrict__ sino, int nsplit,
                                                           float *__restrict__ partial)
 {
-    const int q = order[blockIdx.x] * 128 + threadIdx.x;   // longest walks first
-    if (q >= nr8) return;
+    const int tile = order[blockIdx.x], ntc = fp8_cell_tiles(nd);   // blocks with the longest walks first
+    const int k = (tile / ntc) * FP8_VT + threadIdx.x / FP8_CT, j = (tile % ntc) * FP8_CT + threadIdx.x % FP8_CT;
+    if (k > nv / 8 || j >= nd) return;
+    const int q = k * nd + j;
     const long long b = BATCH ? blockIdx.y : 0;   // image of a batch, as fp_rot4_f32_kernel
     if (BATCH) {
         imgP += 8 * b * (pitch - 2 * pad) * pitch;
@@ -667,7 +670,7 @@ __global__ void __launch_bounds__(128) fp_rot8_f32_kernel(const int *__restrict_
     }
     float *dst = nsplit > 1 ? partial + ((long long)blockIdx.z * (BATCH ? gridDim.y : 1) + b) * nv * nd
                             : sino + b * nv * nd;
-    const int k = q / nd, j = q - k * nd, v4 = nv >> 2;
+    const int v4 = nv >> 2;
     const bool self = k == 0 || 8 * k == nv;   // its own mirror image up to a quarter turn
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -802,7 +805,7 @@ static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float
 {
     const GeomConsts &g = geo->gc;
     const int n = g.nx, pad = geo->pad, pitch = n + 2 * pad;
-    const int nr = g.nv * g.nd, nr8 = (g.nv / 8 + 1) * g.nd;
+    const int nr = g.nv * g.nd;
     const int nsplit = fp_line_parts_rot8(geo);
     const size_t per = forward_rot8_image_bytes(geo);
     const int grp = sym_batch_group(per, batch);
@@ -820,9 +823,9 @@ static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float
             im, P8, T8, n, pad, pitch);
         auto kern = gb > 1 ? (geo->exact ? fp_rot8_f32_kernel<true, true> : fp_rot8_f32_kernel<false, true>)
                            : (geo->exact ? fp_rot8_f32_kernel<true, false> : fp_rot8_f32_kernel<false, false>);
-        kern<<<dim3((nr8 + 127) / 128, gb, nsplit), 128, 0, st>>>(
+        kern<<<dim3(fp8_blocks(g.nv, g.nd), gb, nsplit), 128, 0, st>>>(
             geo->d_fp_order8, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), reinterpret_cast<const float *>(P8),
-            reinterpret_cast<const float *>(T8), pitch, pad, g.nv, g.nd, nr8, sn, nsplit, partial);
+            reinterpret_cast<const float *>(T8), pitch, pad, g.nv, g.nd, sn, nsplit, partial);
         if (nsplit > 1)
             launch_fp_sum_parts(partial, sn, (long long)gb * nr, nsplit, st);
     }

@@ -269,7 +269,8 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
                 }
     }
     const size_t nr4 = sym ? (size_t)(nv / 4) * nd : 0;
-    std::vector<int> fp_order((nr + 127) / 128), fp_order4((nr4 + 127) / 128), fp_order8((nr8 + 127) / 128), bp_order;
+    std::vector<int> fp_order((nr + 127) / 128), fp_order4((nr4 + 127) / 128), fp_order8(sym8 ? fp8_blocks(nv, nd) : 0),
+        bp_order;
     {
         auto order_blocks = [&](size_t nrays, std::vector<int> &order) {
             std::vector<std::pair<double, int>> w(order.size());
@@ -283,7 +284,20 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         };
         order_blocks(nr, fp_order);
         order_blocks(nr4, fp_order4);
-        order_blocks(nr8, fp_order8);
+        {   // the eight-value walk's blocks of FP8_VT views x FP8_CT cells
+            const int nk = nv / 8 + 1, ntc = sym8 ? fp8_cell_tiles(nd) : 1;
+            std::vector<std::pair<double, int>> w(fp_order8.size());
+            for (size_t bi = 0; bi < w.size(); ++bi) {
+                const int k0 = (int)(bi / ntc) * FP8_VT, j0 = (int)(bi % ntc) * FP8_CT;
+                double s = 0.0;
+                for (int k = k0; k < std::min(nk, k0 + FP8_VT); ++k)
+                    for (int j = j0; j < std::min(nd, j0 + FP8_CT); ++j)
+                        s += (double)rays[(size_t)k * nd + j].nrows * rays[(size_t)k * nd + j].kc;
+                w[bi] = {-s, (int)bi};
+            }
+            std::stable_sort(w.begin(), w.end());
+            for (size_t bi = 0; bi < w.size(); ++bi) fp_order8[bi] = w[bi].second;
+        }
         const int tx = (g.nx + 15) / 16, ty = (g.ny + 15) / 16;
         std::vector<std::pair<double, int>> t((size_t)tx * ty);
         for (int b = 0; b < ty; ++b)

@@ -107,7 +107,7 @@ int build_tile_view_table(cnsf_geometry *geo)
 // the angle from the ray through the tile's reference point, atan of
 // (y' Dt - yt D_n)/(D_n Dt + y' yt) (a numerator without constant term), in cells.
 struct BpPixel {
-    float Dn, yp, sig, G;
+    float Dn, yp, sig, G, iDn;   // iDn = 1/D_n (flat, parallel), reused by the blur factors
 };
 
 template <bool ARC>
@@ -117,8 +117,9 @@ __device__ __forceinline__ BpPixel bp_pixel_f32(const TileViewS<float> &T, float
     BpPixel P;
     P.Dn = Dn;
     P.yp = yp;
+    P.iDn = ARC ? 0.f : rcp_approx(Dn);
     P.sig = ARC ? fmaf(atan_small(num * rcp_approx(fmaf(Dn, T.Dt, yp * T.yt))), a.kscale, T.phi)
-                : fmaf(num, rcp_approx(Dn), T.phi);
+                : fmaf(num, P.iDn, T.phi);
     P.G = ARC ? sqrtf(fmaf(Dn, Dn, yp * yp)) * a.dg : 0.f;
     return P;
 }
@@ -431,7 +432,7 @@ __device__ __forceinline__ BpPixel4 bp_pixel4(const BpPixel &P, int J, const BpA
     } else {
         const float ssig = fmaf((float)J + P.sig, a.ds, a.s0);
         Q.K = fmaf(P.yp * ssig, a.idps, P.Dn);
-        Q.L = P.yp * a.ds * a.idps * rcp_approx(P.Dn);
+        Q.L = P.yp * a.ds * a.idps * P.iDn;
     }
     return Q;
 }

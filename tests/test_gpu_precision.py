@@ -3,7 +3,7 @@
 The plain form subtracts two antiderivative values of size ~B, so its relative error grows
 like 6e-8 B / tau' as the effective blur tau' thins; the exact form adds non-negative pieces
 with cut points relative to |s'| and keeps ~1e-7 at any tau'.  Each kernel family (general
-single-image, quarter-turn symmetric, batched, arc detector) is run in both forms on thin
+single-image, eight-fold symmetric, batched, arc detector) is run in both forms on thin
 cells and held to the oracle: the exact form within the FP32 bar (1e-5 relative L2) at every
 width, the plain form measurably worse at the thinnest (the cancellation it leaves), both
 forms equal to FP32 rounding on ordinary cells.
@@ -33,9 +33,9 @@ def rel(a, b):
 
 
 CASES = {
-    # 48 views: the quarter-turn symmetric kernels
+    # 48 views, centred: the eight-fold symmetric kernels (a batch of 2: image by image)
     "symmetric": dict(nx=64, ny=64, n_views=48, n_det=128),
-    # off-centre image: the general kernels
+    # off-centre image: the general kernels (a batch of 2: the batched kernels)
     "general": dict(nx=64, ny=64, n_views=45, n_det=128, center_x=0.7),
     "arc": dict(nx=48, ny=48, n_views=40, n_det=110, d_po=300.0, d_ps=600.0, detector="arc", center_y=-0.4),
 }

@@ -140,13 +140,18 @@ def test_symmetric_repeats_bitwise_rotations_only(cnsf):
     assert torch.equal(cnsf.back_project(geom, y1), cnsf.back_project(geom, y1))
 
 
-@pytest.mark.parametrize("name,nb", [("flat_72", 2), ("arc", 5), ("flat_odd_offset", 3), ("views_20", 4)])
+THIN = FanGeometry(nx=40, ny=40, n_views=32, n_det=80, d_po=200.0, d_ps=450.0, det_width=0.01)
+
+
+@pytest.mark.parametrize("name,nb", [("flat_72", 2), ("arc", 5), ("flat_odd_offset", 3), ("views_20", 4),
+                                     ("thin", 3)])
 def test_symmetric_batches_bitwise_single(cnsf, name, nb):
     """A batch on the symmetric path projects every image with the single-image kernels, line
     and view parts: each image of the batch has the bits of its own call, and the oracle's
-    values within the FP32 bar."""
-    g = SYMMETRIC[name]
+    values within the FP32 bar.  "thin": cells of 0.01 mm, the exact window differences."""
+    g = THIN if name == "thin" else SYMMETRIC[name]
     geom = cnsf.Geometry(g)
+    assert geom.paths["exact_differences"] == (name == "thin")
     rng = np.random.default_rng(80 + nb)
     imgs = rng.uniform(0.0, 1.0, (nb, g.ny, g.nx))
     sinos = rng.uniform(0.0, 1.0, (nb, g.n_views, g.n_det))

@@ -40,10 +40,14 @@ SYMMETRIC = {
     # V = 20 (V/8 not whole: no view at 45 degrees), V = 8 (view 1 is its own mirror image)
     "views_20": FanGeometry(nx=44, ny=44, n_views=20, n_det=90, d_po=200.0, d_ps=420.0),
     "views_8": FanGeometry(nx=30, ny=30, n_views=8, n_det=64, d_po=150.0, d_ps=300.0, detector="arc"),
+    # odd side and odd cell count on the eight-fold path: the centre pixel and the centre cell
+    # are their own mirror images
+    "odd_odd": FanGeometry(nx=37, ny=37, n_views=32, n_det=91, d_po=200.0, d_ps=450.0),
+    "odd_odd_arc": FanGeometry(nx=33, ny=33, n_views=40, n_det=77, d_po=180.0, d_ps=400.0, detector="arc"),
 }
 # the order each case takes: 8 with a centred detector and views closed under reflection
 ORDER = {"flat_72": 8, "flat_odd_offset": 4, "arc": 8, "parallel": 8, "angles_offset": 4, "wide_cells": 8,
-         "views_20": 8, "views_8": 8}
+         "views_20": 8, "views_8": 8, "odd_odd": 8, "odd_odd_arc": 8}
 
 NOT_SYMMETRIC = {
     "views_not_multiple_of_4": config_geometry(1),                                 # 90 views
@@ -144,7 +148,7 @@ THIN = FanGeometry(nx=40, ny=40, n_views=32, n_det=80, d_po=200.0, d_ps=450.0, d
 
 
 @pytest.mark.parametrize("name,nb", [("flat_72", 2), ("arc", 5), ("flat_odd_offset", 3), ("views_20", 4),
-                                     ("thin", 3)])
+                                     ("thin", 3), ("odd_odd", 3)])
 def test_symmetric_batches_bitwise_single(cnsf, name, nb):
     """A batch on the symmetric path projects every image with the single-image kernels, line
     and view parts: each image of the batch has the bits of its own call, and the oracle's

@@ -24,9 +24,11 @@ def _turn(img):
     return out
 
 
-@pytest.mark.parametrize("detector", ["flat", "arc", "parallel"])
-def test_quarter_turn_and_reflection(detector):
-    n, V, nd = 10, 16, 26
+@pytest.mark.parametrize("detector,n,nd", [("flat", 10, 26), ("arc", 10, 26), ("parallel", 10, 26),
+                                           ("flat", 9, 23), ("arc", 9, 23)])
+def test_quarter_turn_and_reflection(detector, n, nd):
+    """Even and odd sides and cell counts (odd: the centre pixel and cell map to themselves)."""
+    V = 16
     g = FanGeometry(nx=n, ny=n, n_views=V, n_det=nd, d_po=55.0, d_ps=120.0, detector=detector)
     A = oracle.matrix(g).reshape(V, nd, n, n)
     peak = np.abs(A).max()

@@ -596,9 +596,10 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
 // pixel p, U_m(p) = sum_k sum_j y[-k + mV/4][n_det - 1 - j] a(k, j, p) over the views
 // k = 0 .. V/8 that are not their own mirror images, and
 //     (A^T y)[n] = sum_m T_m(R^-m n) + sum_m U_m(M R^-m n),   M (i, r) = (i, N-1-r).
-// The per-call table Y8[o][k][m] holds the 8 weighted pairs of a cell pair (2m + o,
-// 2m + o + 1): T part y[k + mV/4][j] w_j (m = 0..3), U part y[-k + mV/4][n_det - 1 - j] w_j
-// (zero for the self-mirror views k = 0 and 8k = V), 64 bytes; w_j = 2/B of (k, j).
+// The per-call table Y8[o][k][m] holds the 16 weighted values of a cell pair (2m + o,
+// 2m + o + 1), 64 bytes: T part y[k + rV/4][j] w_j (r = 0..3), U part
+// y[-k + rV/4][n_det - 1 - j] w_j (zero for the self-mirror views k = 0 and 8k = V), each
+// part the first cell's four values, then the second's; w_j = 2/B of (k, j).
 __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *__restrict__ box,
                                        float4 *__restrict__ y8, int nv, int nd)
 {
@@ -621,8 +622,8 @@ __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *
             for (int r = 0; r < 4; ++r) {
                 const float *yt = y + (long long)(k + r * v4) * nd;
                 const float *yu = y + (long long)((nv - k + r * v4) % nv) * nd;
-                out[2 * r + hh] = j < nd ? yt[j] * w : 0.f;
-                out[8 + 2 * r + hh] = (j < nd && !self) ? yu[nd - 1 - j] * w : 0.f;
+                out[4 * hh + r] = j < nd ? yt[j] * w : 0.f;
+                out[8 + 4 * hh + r] = (j < nd && !self) ? yu[nd - 1 - j] * w : 0.f;
             }
         }
 #pragma unroll
@@ -631,12 +632,14 @@ __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *
 }
 
 // bp_view2_rot4 with the eight values per cell pair (the merged constants and 64 bytes of
-// weighted sinogram); the two pixels' entries are added to their eight scalar accumulators.
+// weighted sinogram); each pixel's two entries are applied to the pair's sixteen values as
+// packed pairs of neighbouring values (adjacent registers of the 256-bit loads): ta[i],
+// tb[i] accumulate the values 2i and 2i + 1 of T_0..3, U_0..3.
 template <bool ARC, bool EXACT>
 __device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4 &Qb, float hwc, int J,
                                               const BpArgs &a, int nd, const float *__restrict__ y8row,
                                               const float *__restrict__ y8orow, const float *__restrict__ acrow,
-                                              long long ac_odd, float (&ta)[8], float (&tb)[8])
+                                              long long ac_odd, float2 (&ta)[4], float2 (&tb)[4])
 {
     int g0, g1;
     pair_window(Qa.P, Qb.P, hwc, J, nd, g0, g1);
@@ -662,12 +665,16 @@ __device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4
         const float2 nhC = __fmul2_rn(make_float2(rcp_approx(iC.x), rcp_approx(iC.y)), mh);
         const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, piC, nhC, a);
         const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, piC, nhC, a);
+        const float2 wa0 = make_float2(wa.x, wa.x), wa1 = make_float2(wa.y, wa.y);
+        const float2 wb0 = make_float2(wb.x, wb.x), wb1 = make_float2(wb.y, wb.y);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            ta[k] = fmaf(Y[2 * k + 1], wa.y, fmaf(Y[2 * k], wa.x, ta[k]));
-            tb[k] = fmaf(Y[2 * k + 1], wb.y, fmaf(Y[2 * k], wb.x, tb[k]));
-            ta[4 + k] = fmaf(Z[2 * k + 1], wa.y, fmaf(Z[2 * k], wa.x, ta[4 + k]));
-            tb[4 + k] = fmaf(Z[2 * k + 1], wb.y, fmaf(Z[2 * k], wb.x, tb[4 + k]));
+        for (int i = 0; i < 2; ++i) {
+            const float2 y0 = make_float2(Y[2 * i], Y[2 * i + 1]), y1 = make_float2(Y[4 + 2 * i], Y[5 + 2 * i]);
+            const float2 z0 = make_float2(Z[2 * i], Z[2 * i + 1]), z1 = make_float2(Z[4 + 2 * i], Z[5 + 2 * i]);
+            ta[i] = __ffma2_rn(y1, wa1, __ffma2_rn(y0, wa0, ta[i]));
+            tb[i] = __ffma2_rn(y1, wb1, __ffma2_rn(y0, wb0, tb[i]));
+            ta[2 + i] = __ffma2_rn(z1, wa1, __ffma2_rn(z0, wa0, ta[2 + i]));
+            tb[2 + i] = __ffma2_rn(z1, wb1, __ffma2_rn(z0, wb0, tb[2 + i]));
         }
         da = __fadd2_rn(da, sta);
         db = __fadd2_rn(db, stb);
@@ -703,11 +710,11 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
     const int ndh = (g.nd + 1) >> 1;
     const double refx = tile_ref(it, g.nx), refy = tile_ref(rt, g.ny);
     const float di = (float)(tx - refx), dr = (float)(ty - refy);
-    float t[4][8];   // [quad pixel][T_0..3, U_0..3]
+    float2 t[4][4];   // [quad pixel][(T_0, T_1), (T_2, T_3), (U_0, U_1), (U_2, U_3)]
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) t[q][k] = 0.f;
+        for (int k = 0; k < 4; ++k) t[q][k] = make_float2(0.f, 0.f);
     for (int v0 = vbeg; v0 < vend; v0 += BP_CHUNK) {
         const int nvc = min(BP_CHUNK, vend - v0);
         __syncthreads();
@@ -753,7 +760,8 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
             if (iq >= g.nx || rq >= g.ny) continue;
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                partial[(8LL * blockIdx.y + k) * nn + (long long)rq * g.nx + iq] = t[q][k] * a.h2q;
+                partial[(8LL * blockIdx.y + k) * nn + (long long)rq * g.nx + iq] =
+                    ((k & 1) ? t[q][k >> 1].y : t[q][k >> 1].x) * a.h2q;
         }
     }
 }

@@ -348,13 +348,14 @@ __global__ void pad_rot4_kernel(const float *__restrict__ img, float4 *__restric
         }
 }
 
-// The candidates of two consecutive lines, packed as in line_pair_sum, each entry applied to
-// the four rotated values of its pixel; s[k] accumulates rotation k (lanes: the two lines).
-// KC = 0: kc candidates (wide cells).
+// The candidates of two consecutive lines, evaluated packed as in line_pair_sum, each entry
+// applied to the four rotated values of its pixel as two packed pairs of neighbouring values
+// (adjacent registers of the 16-byte load); s[i] accumulates rotations 2i and 2i + 1 over
+// both lines.  KC = 0: kc candidates (wide cells).
 template <int KC, bool EXACT>
 __device__ __forceinline__ void line_pair_sum_rot4(const float4 *__restrict__ rp0, const float4 *__restrict__ rp1,
                                                    int kc, float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1,
-                                                   float q, float piC, float iC, float2 nhC2, float2 (&s)[4])
+                                                   float q, float piC, float iC, float2 nhC2, float2 (&s)[2])
 {
     float2 xs = __fmul2_rn(B2, u), e = __ffma2_rn(kap2, u, er2);
 #pragma unroll
@@ -363,10 +364,9 @@ __device__ __forceinline__ void line_pair_sum_rot4(const float4 *__restrict__ rp
         const float2 d = wdiff2<EXACT>(x, e, ne1, q, piC, iC, nhC2);
         const float2 w = __fmul2_rn(d, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
         const float4 c0 = __ldg(rp0 + m), c1 = __ldg(rp1 + m);
-        s[0] = __ffma2_rn(make_float2(c0.x, c1.x), w, s[0]);
-        s[1] = __ffma2_rn(make_float2(c0.y, c1.y), w, s[1]);
-        s[2] = __ffma2_rn(make_float2(c0.z, c1.z), w, s[2]);
-        s[3] = __ffma2_rn(make_float2(c0.w, c1.w), w, s[3]);
+        const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
+        s[0] = __ffma2_rn(make_float2(c1.x, c1.y), w1, __ffma2_rn(make_float2(c0.x, c0.y), w0, s[0]));
+        s[1] = __ffma2_rn(make_float2(c1.z, c1.w), w1, __ffma2_rn(make_float2(c0.z, c0.w), w0, s[1]));
         xs = __fadd2_rn(xs, B2);
         e = __fadd2_rn(e, kap2);
     }
@@ -384,9 +384,9 @@ __device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restri
     const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);
     const float2 B2 = make_float2(B, B), ne1 = make_float2(-1.0f, -1.0f), nhC2 = make_float2(-hC, -hC);
     const float hw = R.hw;
-    float2 acc[4], part[4];
+    float2 acc[2], part[2];   // rotations (0, 1) and (2, 3)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = part[k] = make_float2(0.f, 0.f);
+    for (int k = 0; k < 2; ++k) acc[k] = part[k] = make_float2(0.f, 0.f);
     int rr = 0;
     for (; rr + 1 < R.nrows; rr += 2) {
         int ilo0, ilo1;
@@ -400,16 +400,17 @@ __device__ __forceinline__ void walk2_rot4(const RayF &R, const float4 *__restri
         base += 2 * pitch;
         if ((rr & 15) == 14) {   // blocked summation: partial sums of 16 lines
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < 2; ++k) {
                 acc[k] = __fadd2_rn(acc[k], part[k]);
                 part[k] = make_float2(0.f, 0.f);
             }
         }
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 2; ++k) {
         acc[k] = __fadd2_rn(acc[k], part[k]);
-        out[k] = acc[k].x + acc[k].y;
+        out[2 * k] = acc[k].x;
+        out[2 * k + 1] = acc[k].y;
     }
     if (rr < R.nrows) {   // odd line count: the last line alone
         int ilo;
@@ -550,11 +551,14 @@ __global__ void pad_rot8_kernel(const float *__restrict__ img, float4 *__restric
         }
 }
 
-// line_pair_sum_rot4 with the eight values per pixel (one 256-bit load per candidate and line).
+// line_pair_sum_rot4 with the eight values per pixel (one 256-bit load per candidate and
+// line): the two lines' entries are evaluated packed, then each is applied to its pixel's
+// eight values as four packed pairs of neighbouring values (the pairs a 256-bit load leaves
+// in adjacent registers); s[i] accumulates values 2i and 2i + 1 over both lines.
 template <int KC, bool EXACT>
 __device__ __forceinline__ void line_pair_sum_rot8(const float *__restrict__ rp0, const float *__restrict__ rp1, int kc,
                                                    float2 u, float2 er2, float2 kap2, float2 B2, float2 ne1, float q,
-                                                   float piC, float iC, float2 nhC2, float2 (&s)[8])
+                                                   float piC, float iC, float2 nhC2, float2 (&s)[4])
 {
     float2 xs = __fmul2_rn(B2, u), e = __ffma2_rn(kap2, u, er2);
 #pragma unroll
@@ -565,8 +569,12 @@ __device__ __forceinline__ void line_pair_sum_rot8(const float *__restrict__ rp0
         float c0[8], c1[8];
         ldg256(rp0 + 8 * m, c0);
         ldg256(rp1 + 8 * m, c1);
+        const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s[k] = __ffma2_rn(make_float2(c0[k], c1[k]), w, s[k]);
+        for (int i = 0; i < 4; ++i) {
+            s[i] = __ffma2_rn(make_float2(c0[2 * i], c0[2 * i + 1]), w0, s[i]);
+            s[i] = __ffma2_rn(make_float2(c1[2 * i], c1[2 * i + 1]), w1, s[i]);
+        }
         xs = __fadd2_rn(xs, B2);
         e = __fadd2_rn(e, kap2);
     }
@@ -583,12 +591,12 @@ __device__ __forceinline__ void walk2_rot8(const RayF &R, const float *__restric
     const float2 de2 = make_float2(2.f * R.de, 2.f * R.de), kap2 = make_float2(R.kap, R.kap);
     const float2 B2 = make_float2(B, B), ne1 = make_float2(-1.0f, -1.0f), nhC2 = make_float2(-hC, -hC);
     const float hw = R.hw;
-    // one sum per value and line parity, without the 16-line blocks of the other walks: the
-    // sixteen block registers would cost a third of the resident warps, and a line part (an
-    // eighth of the ray's lines, fp_line_parts_rot8) is short enough for plain FP32 sums
-    float2 acc[8];
+    // one sum per value, without the 16-line blocks of the other walks: the block registers
+    // would cost resident warps, and a line part (an eighth of the ray's lines,
+    // fp_line_parts_rot8) is short enough for plain FP32 sums
+    float2 acc[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 4; ++i) acc[i] = make_float2(0.f, 0.f);
     int rr = 0;
     for (; rr + 1 < R.nrows; rr += 2) {
         int ilo0, ilo1;
@@ -602,7 +610,10 @@ __device__ __forceinline__ void walk2_rot8(const RayF &R, const float *__restric
         base += 2 * pitch8;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) out[k] = acc[k].x + acc[k].y;
+    for (int i = 0; i < 4; ++i) {
+        out[2 * i] = acc[i].x;
+        out[2 * i + 1] = acc[i].y;
+    }
     if (rr < R.nrows) {   // odd line count: the last line alone
         int ilo;
         float rho;

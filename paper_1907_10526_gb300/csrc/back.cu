@@ -437,26 +437,31 @@ __device__ __forceinline__ BpPixel4 bp_pixel4(const BpPixel &P, int J, const BpA
     return Q;
 }
 
-// The two entries of one cell pair for one pixel from the merged entry A = (q | 1/C | ds/L |
-// c1, pairs) with p/C and -C/2 formed by the caller; d: flat and parallel d' = D_n d, arc d
-// (cells).  Without 2/B and h^2/4, as bp_pair_f32.
+// The two entries of one cell pair for one pixel from the merged entry A (pairs), all in
+// units of the cell's C (the narrower trapezoid width of Eq. 16, clamped away from 0 as
+// 1/C is): q/C | p/C | ds/(L C) | c1/C, arc detector q/C | p/C | 1/C | unused.  In these
+// units the window difference of footprint.cuh takes 1/C = 1 and -C/2 = -1/2, and the
+// entry, a ratio of the difference to the half blur, is unchanged; d: flat and parallel
+// d' = D_n d, arc d (cells).  Without 2/B and h^2/4, as bp_pair_f32.
 template <bool ARC, bool EXACT>
-__device__ __forceinline__ float2 bp_pair_rot4(const BpPixel4 &Q, float2 d, const float (&A)[8], float2 piC, float2 nhC,
-                                               const BpArgs &a)
+__device__ __forceinline__ float2 bp_pair_rot4(const BpPixel4 &Q, float2 d, const float (&A)[8], const BpArgs &a)
 {
     const float2 ne1 = make_float2(-1.f, -1.f);
     float2 xs, e;
     if (ARC) {
-        const float2 d2 = __fmul2_rn(d, d);
+        const float2 d2 = __fmul2_rn(d, d), iC = make_float2(A[4], A[5]);
         xs = __fmul2_rn(__fmul2_rn(make_float2(Q.P.G, Q.P.G), d),
                         __ffma2_rn(d2, make_float2(a.nk6, a.nk6), make_float2(1.f, 1.f)));
         e = __fmul2_rn(make_float2(Q.K, Q.K), __ffma2_rn(d2, make_float2(a.nk2, a.nk2), make_float2(1.f, 1.f)));
+        xs = __fmul2_rn(xs, iC);
+        e = __fmul2_rn(e, iC);
     } else {
         xs = __fmul2_rn(make_float2(A[4], A[5]), d);
         e = __fmul2_rn(make_float2(A[6], A[7]), __ffma2_rn(d, make_float2(-Q.L, -Q.L), make_float2(Q.K, Q.K)));
     }
-    const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));   // |s'|
-    const float2 w = wdiff2p<EXACT>(x, e, ne1, make_float2(A[0], A[1]), piC, make_float2(A[2], A[3]), nhC);
+    const float2 x = make_float2(fabsf(xs.x), fabsf(xs.y));   // |s'| / C
+    const float2 w = wdiff2p<EXACT>(x, e, ne1, make_float2(A[0], A[1]), make_float2(A[2], A[3]),
+                                    make_float2(1.f, 1.f), make_float2(-0.5f, -0.5f));
     return __fmul2_rn(w, make_float2(rcp_approx(e.x), rcp_approx(e.y)));
 }
 
@@ -484,16 +489,12 @@ __device__ __forceinline__ void bp_view2_rot4(const BpPixel4 &Qa, const BpPixel4
     float2 da = make_float2(sa * (Qa.P.sig - off), sa * (Qa.P.sig - off - 1.f));
     float2 db = make_float2(sb * (Qb.P.sig - off), sb * (Qb.P.sig - off - 1.f));
     const float2 sta = make_float2(-2.f * sa, -2.f * sa), stb = make_float2(-2.f * sb, -2.f * sb);
-    const float2 m1f = make_float2(-1.f, -1.f), mh = make_float2(-0.5f, -0.5f);
     for (int m = m0; m <= m1; ++m) {
         float A[8], Y[8];
-        ldg256(acrow + 8 * m, A);     // q | 1/C | ds/L | c1, pairs
+        ldg256(acrow + 8 * m, A);     // q/C | p/C | ds/(L C) | c1/C, pairs
         ldg256(y4row + 8 * m, Y);     // y 2/B of the four rotations, pairs
-        const float2 iC = make_float2(A[2], A[3]);
-        const float2 piC = __ffma2_rn(make_float2(A[0], A[1]), iC, m1f);                       // q/C - 1
-        const float2 nhC = __fmul2_rn(make_float2(rcp_approx(iC.x), rcp_approx(iC.y)), mh);    // -C/2
-        const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, piC, nhC, a);
-        const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, piC, nhC, a);
+        const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, a);
+        const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, a);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const float2 yk = make_float2(Y[2 * k], Y[2 * k + 1]);
@@ -654,17 +655,13 @@ __device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4
     float2 da = make_float2(sa * (Qa.P.sig - off), sa * (Qa.P.sig - off - 1.f));
     float2 db = make_float2(sb * (Qb.P.sig - off), sb * (Qb.P.sig - off - 1.f));
     const float2 sta = make_float2(-2.f * sa, -2.f * sa), stb = make_float2(-2.f * sb, -2.f * sb);
-    const float2 m1f = make_float2(-1.f, -1.f), mh = make_float2(-0.5f, -0.5f);
     for (int m = m0; m <= m1; ++m) {
         float A[8], Y[8], Z[8];
-        ldg256(acrow + 8 * m, A);          // q | 1/C | ds/L | c1, pairs
+        ldg256(acrow + 8 * m, A);          // q/C | p/C | ds/(L C) | c1/C, pairs
         ldg256(y8row + 16 * m, Y);         // T part, pairs of the four rotations
         ldg256(y8row + 16 * m + 8, Z);     // U part, pairs of the four mirrored views
-        const float2 iC = make_float2(A[2], A[3]);
-        const float2 piC = __ffma2_rn(make_float2(A[0], A[1]), iC, m1f);
-        const float2 nhC = __fmul2_rn(make_float2(rcp_approx(iC.x), rcp_approx(iC.y)), mh);
-        const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, piC, nhC, a);
-        const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, piC, nhC, a);
+        const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, a);
+        const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, a);
         const float2 wa0 = make_float2(wa.x, wa.x), wa1 = make_float2(wa.y, wa.y);
         const float2 wb0 = make_float2(wb.x, wb.x), wb1 = make_float2(wb.y, wb.y);
 #pragma unroll

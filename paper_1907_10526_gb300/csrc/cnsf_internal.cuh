@@ -318,7 +318,7 @@ struct cnsf_geometry {
     int *d_fp_order;          // [ceil(nv*nd/128)] forward blocks of 128 rays
     int *d_fp_order4;         // [ceil(nv/4*nd/128)] the same over the rays of views < nv/4 (sym only)
     int *d_fp_order8;         // [ceil((nv/8+1)*nd/128)] the same over views 0 .. nv/8 (sym8 only)
-    float *d_ac;              // [2][nv/4][ceil(n_det/2)][8]: q, 1/C, ds/L, c1 of cells 2m + o, 2m + o + 1 (sym only)
+    float *d_ac;              // [2][nv/4][ceil(n_det/2)][8]: q/C, p/C, ds/(L C), c1/C of cells 2m + o, 2m + o + 1 (sym only)
     int *d_bp_order;          // [ceil(nx/16)*ceil(ny/16)] back-projection tiles
     float4 *d_tv;             // [tiles][nv][2] FP32 back-projection tile coefficients (when <= 1 GiB), or null
     int *d_tj;                // [tiles][nv] their integer cell offsets

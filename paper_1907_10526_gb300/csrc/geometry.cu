@@ -264,7 +264,13 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
                     for (int hh = 0; hh < 2; ++hh) {
                         const int j = std::min(2 * m + o + hh, nd - 1);
                         const BoxF &b = box[(size_t)k * nd + j];
-                        A[hh] = b.q; A[2 + hh] = b.iC; A[4 + hh] = cellf[j].g1; A[6 + hh] = cellf[j].c1;
+                        // in units of the cell's C (bp_pair_rot4): q/C, p/C, ds/(L C), c1/C; arc
+                        // detector q/C, p/C, 1/C
+                        const double iC = b.iC;
+                        A[hh] = (float)(b.q * iC);
+                        A[2 + hh] = b.piC;
+                        A[4 + hh] = g.arc ? b.iC : (float)(cellf[j].g1 * iC);
+                        A[6 + hh] = g.arc ? 0.0f : (float)(cellf[j].c1 * iC);
                     }
                 }
     }

@@ -302,9 +302,13 @@ CNSF_API int cnsf_asd_pocs(const cnsf_geometry *const *subsets, int32_t n_subset
  * the one array: calls whose work overlaps on the GPU (different streams without ordering
  * between them) race and may corrupt each other's results.  The array keeps the last
  * call's contents; nothing in it needs clearing because each call rewrites every element
- * it reads.  It runs the general forward kernel with each ray's lines in one part (no
- * partial sinograms to allocate) and without the quarter-turn reuse, so at large
- * n_views x n_det it is several times slower than cnsf_forward_project. */
+ * it reads.  Each ray's lines are walked in one part (no partial sinograms to allocate).
+ * In FP32 on a geometry with the quarter-turn symmetry (see cnsf_option) whose image copy
+ * with its four rotations, 2 * n_x * (n_x + 2*pad) * 16 bytes, fits the array (n_x up to
+ * ~700), the images of the batch are projected one after the other by the quarter-turn
+ * kernel in that copy, each with the bits of its single-image call; otherwise by the
+ * general kernel, several times slower than cnsf_forward_project at large
+ * n_views x n_det. */
 CNSF_API int cnsf_forward_project_noalloc(const cnsf_geometry *geom, const void *image, void *sino,
                                           int32_t batch, int32_t dtype, void *stream);
 

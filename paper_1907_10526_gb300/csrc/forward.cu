@@ -969,6 +969,25 @@ int launch_forward_with_scratch(const cnsf_geometry *geo, const void *img, void 
     dim3 blk(128), grdr((pitchP + 127) / 128, g.ny, batch);
     dim3 blkt(32, 8), grdt((pitchT + 31) / 32, (g.nx + 31) / 32, batch);
     dim3 grd((nr + 127) / 128, batch);
+    // FP32 on a geometry with the quarter-turn symmetry: the four-rotation walk with unsplit
+    // lines, image by image in one image's four-rotation copies when they fit (each image
+    // then takes exactly the arithmetic of a single-image call through this entry point)
+    const size_t img4 = 2 * (size_t)g.nx * pitchP * sizeof(float4);
+    if (dtype == CNSF_F32 && geo->sym && img4 <= scratch_bytes) {
+        float4 *P4 = (float4 *)scratch, *T4 = P4 + (size_t)g.nx * pitchP;
+        const int nr4 = (g.nv / 4) * g.nd;
+        const unsigned nt = (unsigned)((g.nx + 31) / 32);
+        auto kern = geo->exact ? fp_rot4_f32_kernel<true, false> : fp_rot4_f32_kernel<false, false>;
+        for (int b = 0; b < batch; ++b) {
+            pad_rot4_kernel<false><<<dim3(nt, nt), dim3(32, 32), 0, st>>>((const float *)img + (size_t)b * g.nx * g.ny,
+                                                                       P4, T4, g.nx, pad, pitchP);
+            kern<<<(nr4 + 127) / 128, 128, 0, st>>>(geo->d_fp_order4, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h),
+                                                    P4, T4, pitchP, pad, nr, nr4, (float *)sino + (size_t)b * nr, 1,
+                                                    nullptr);
+        }
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+    }
     if (dtype == CNSF_F32) {
         float *P = (float *)scratch, *Tt = P + (size_t)batch * strideP;
         pad_rows_kernel<float><<<grdr, blk, 0, st>>>((const float *)img, P, g.nx, g.ny, pad, pitchP, 0);

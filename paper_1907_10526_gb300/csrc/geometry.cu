@@ -248,12 +248,12 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
         }
     }
 
-    // Launch orders.  Forward: blocks of 128 consecutive rays by descending walk length
-    // (lines x candidates).  Back: 16 x 16 tiles by descending mean magnification of their
-    // centre over the views, 1/sqrt(D_po^2 - rho^2) for a tile at radius rho.
+    // Launch orders.  Forward: blocks of 128 consecutive rays (the eight-value walk: blocks
+    // of FP8_VT base views x FP8_CT cells) by descending walk length (lines x candidates).
+    // Back: 16 x 16 tiles by descending mean magnification of their centre over the views,
+    // 1/sqrt(D_po^2 - rho^2) for a tile at radius rho.
     const bool sym = quarter_turn_symmetric(d);
     const bool sym8 = sym && reflection_symmetric(d);
-    const size_t nr8 = sym8 ? (size_t)(nv / 8 + 1) * nd : 0;
     if (sym) {
         const size_t np4 = (size_t)(nv / 4) * ndh;
         ac.assign(2 * 8 * np4, 0.0f);

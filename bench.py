@@ -418,6 +418,8 @@ def run_cnsf(args):
             line["asd_pocs_limited_view"] = bench_asd_pocs(dev)
         if "kinds" in want:
             line["detector_kinds_512x720"] = bench_detector_kinds(dev)
+        if "forms" in want:
+            line["difference_forms_512x720"] = bench_difference_forms(dev)
     if world == 1 and not args.no_cpu_baseline:
         import oracle
         r, dt, thr, desc = oracle_sample_rate(720)
@@ -682,6 +684,42 @@ def bench_detector_kinds(dev, reps: int = 5):
     return out
 
 
+def bench_difference_forms(dev, calls: int = 10):
+    """The headline workload through the symmetric and the general kernels with each form of
+    the window difference (plain, and the cancellation-free exact form the geometry picks for
+    thin cells): FP32 forward and back ms per call, ``calls`` calls queued between two events
+    so that the host's per-call work stays hidden, best of 3."""
+    import torch
+    import paper_1907_10526_gb300 as cnsf
+    from synth import config_geometry, phantom_for_config
+    out = {}
+    g = config_geometry(2)
+    x = torch.tensor(phantom_for_config(2), dtype=torch.float32, device=dev)
+    for sym in (True, False):
+        for form in ("plain", "exact"):
+            geom = cnsf.Geometry(g, symmetry=sym, differences=form)
+            y = cnsf.forward_project(geom, x)
+            c = cnsf.back_project(geom, y)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            fp, bp = [], []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                ev[0].record()
+                for _ in range(calls):
+                    cnsf.forward_project(geom, x, out=y)
+                ev[1].record()
+                for _ in range(calls):
+                    cnsf.back_project(geom, y, out=c)
+                ev[2].record()
+                torch.cuda.synchronize()
+                fp.append(ev[0].elapsed_time(ev[1]) / calls)
+                bp.append(ev[1].elapsed_time(ev[2]) / calls)
+            out[f"{'symmetric' if sym else 'general'}_{form}"] = {"fp_ms": min(fp), "bp_ms": min(bp),
+                                                                  "paths": geom.paths}
+            geom.close()
+    return out
+
+
 def bench_asd_pocs(dev, iters: int = 200):
     """The limited-view reconstructions of Sec. IV-E: data from the reference projector,
     ASD-POCS (one subset per view, Sidky-Pan parameters) with the CNSF and with the exact
@@ -718,7 +756,7 @@ def bench_asd_pocs(dev, iters: int = 200):
     return out
 
 
-EXTRAS = ("serving", "solvers", "batch16", "e4", "reference", "asd_pocs", "kinds")
+EXTRAS = ("serving", "solvers", "batch16", "e4", "reference", "asd_pocs", "kinds", "forms")
 # the serving mode whose latencies the line's p50/p99 keys report (the server's default)
 SERVED_MODE = "continuous"
 

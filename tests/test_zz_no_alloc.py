@@ -4,9 +4,11 @@ It serves callers that may not allocate device memory during a projection (for
 example a plugin whose host framework owns the device-memory budget).  It is called
 here through the C ABI directly: its results are held to the FP64 oracle (FP32 1e-5,
 FP64 1e-12 relative L2) for batches of 1 to 7 images, each image of a batch is bitwise
-the result of a single-image call (the batch runs the same per-image kernel), two calls
-in a row reuse the shared array without one leaking into the other, and a request larger
-than the array is refused without launching anything.
+the result of a single-image call (the batch runs the same per-image kernel), both kernel
+families it takes (the quarter-turn walk, with an arc detector and with thin cells, and
+the general walk) agree with the oracle and the allocating forward, two calls in a row
+reuse the shared array without one leaking into the other, and a request larger than the
+array is refused without launching anything.
 """
 import ctypes
 
@@ -62,6 +64,31 @@ def test_noalloc_matches_oracle(api, batch, dt):
             one = torch.empty((1, g.n_views, g.n_det), dtype=dt, device="cuda")
             assert _noalloc(L.lib, geom, x[b:b + 1].contiguous(), one, 1, code) == 0
             assert torch.equal(one[0], y[b])
+
+
+@pytest.mark.parametrize("case", ["arc", "thin", "general"])
+def test_noalloc_kernel_families(api, case):
+    """The families the entry point takes: the quarter-turn walk (an arc detector; thin cells,
+    i.e. the exact window differences) and the general walk (an off-centre image), each held
+    to the oracle and to the allocating forward, and each batch member bitwise to its
+    single-image call."""
+    cnsf, L = api
+    g = {"arc": SMALL.with_(detector="arc"), "thin": SMALL.with_(det_width=0.01),
+         "general": SMALL.with_(center_x=0.4)}[case]
+    geom = cnsf.Geometry(g)
+    assert geom.paths["symmetric"] == (case != "general")
+    assert geom.paths["exact_differences"] == (case == "thin")
+    imgs = np.stack([ellipse_phantom(g.nx, 10, 1.0, seed=70 + b) for b in range(3)])
+    x = torch.tensor(imgs, dtype=torch.float32, device="cuda")
+    y = torch.full((3, g.n_views, g.n_det), float("nan"), device="cuda")
+    assert _noalloc(L.lib, geom, x, y, 3, L.CNSF_F32) == 0
+    ref = cnsf.forward_project(geom, x)
+    for b in range(3):
+        assert _rel(y[b].double().cpu().numpy(), oracle.forward(g, imgs[b])) < 1e-5
+        assert _rel(y[b].cpu().numpy(), ref[b].cpu().numpy()) < 1e-6
+        one = torch.empty((1, g.n_views, g.n_det), device="cuda")
+        assert _noalloc(L.lib, geom, x[b:b + 1].contiguous(), one, 1, L.CNSF_F32) == 0
+        assert torch.equal(one[0], y[b])
 
 
 def test_noalloc_forward_matches_allocating_forward(api):

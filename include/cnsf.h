@@ -152,6 +152,23 @@ CNSF_API int cnsf_geometry_paths(const cnsf_geometry *geom, int32_t *symmetric, 
  * geometries).  *bytes is a host pointer.  CNSF_ERR_INVALID for a NULL argument. */
 CNSF_API int cnsf_geometry_device_bytes(const cnsf_geometry *geom, size_t *bytes);
 
+/* Scratch pool.  Projections called outside stream capture take their stream-ordered
+ * scratch (cnsf_projection_scratch_bytes) from a device memory pool of the library's own,
+ * one per device, created on first use.  After a synchronisation the pool keeps up to
+ * CNSF_SCRATCH_KEEP_BYTES of freed scratch mapped for the next call (CUDA's default pool
+ * returns it to the driver, and the next call maps it again); scratch allocated while a
+ * stream is captured (plans, solvers) is the graph's own and never comes from the pool.
+ * cnsf_scratch_pool_stats: for the current device's pool, *reserved = device bytes it holds
+ * now (in use or kept) and *used_high = the most bytes in use at once since its creation or
+ * the last reset (host pointers, either may be NULL); reset_high != 0 resets that mark
+ * after reading it.  cnsf_scratch_trim: returns the current device's kept scratch to the
+ * driver (memory of calls still in flight stays).  Both create the pool if needed;
+ * CNSF_ERR_CUDA when a CUDA call fails.  (Not in the paper: device-memory management of
+ * this library.) */
+#define CNSF_SCRATCH_KEEP_BYTES (512ull << 20)
+CNSF_API int cnsf_scratch_pool_stats(size_t *reserved, size_t *used_high, int32_t reset_high);
+CNSF_API int cnsf_scratch_trim(void);
+
 /* Sizes of a geometry: any output pointer may be NULL. */
 CNSF_API int cnsf_geometry_shape(const cnsf_geometry *geom, int32_t *n_x, int32_t *n_y, int32_t *n_views,
                         int32_t *n_det);

@@ -16,11 +16,11 @@ from typing import Optional
 import torch
 
 from ._lib import (CNSF_DETECTOR, CNSF_F32, CNSF_F64, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_NO_REFLECTION,  # noqa: F401
-                   CNSF_OPT_NO_SYMMETRY, CNSF_OPT_PLAIN_DIFFERENCES, AsdPocsParams, CnsfError, GeometryDesc, check,
-                   lib)
+                   CNSF_OPT_NO_SYMMETRY, CNSF_OPT_PLAIN_DIFFERENCES, CNSF_SCRATCH_KEEP_BYTES, AsdPocsParams,
+                   CnsfError, GeometryDesc, check, lib)
 
 __all__ = ["Geometry", "forward_project", "back_project", "forward_project_ref", "back_project_ref",
-           "count_nonzeros", "forward_project_noalloc", "asd_pocs", "Plan",
+           "count_nonzeros", "forward_project_noalloc", "asd_pocs", "Plan", "scratch_pool_stats", "scratch_trim",
            "sirt", "cgls", "cgls_batched", "SolverWorkspace", "BatchedSolverWorkspace", "Projector", "ReferenceProjector", "project",
            "CnsfError"]
 
@@ -258,6 +258,23 @@ def count_nonzeros(geom: Geometry, stream: Optional[torch.cuda.Stream] = None) -
                                       ctypes.c_void_p(_stream_ptr(stream, geom.device))),
               "cnsf_count_nonzeros")
     return int(n.value)
+
+
+def scratch_pool_stats(device=None, reset_high: bool = False) -> tuple:
+    """(bytes held, most bytes in use at once) of the library's scratch pool on ``device``;
+    up to ``CNSF_SCRATCH_KEEP_BYTES`` freed scratch stays mapped after a synchronisation.
+    ``reset_high`` resets the high-water mark after reading it."""
+    held, high = ctypes.c_size_t(), ctypes.c_size_t()
+    with torch.cuda.device(torch.cuda.current_device() if device is None else device):
+        check(lib.cnsf_scratch_pool_stats(ctypes.byref(held), ctypes.byref(high), int(bool(reset_high))),
+              "cnsf_scratch_pool_stats")
+    return int(held.value), int(high.value)
+
+
+def scratch_trim(device=None) -> None:
+    """Return the scratch pool's kept memory on ``device`` to the driver."""
+    with torch.cuda.device(torch.cuda.current_device() if device is None else device):
+        check(lib.cnsf_scratch_trim(), "cnsf_scratch_trim")
 
 
 class Plan:

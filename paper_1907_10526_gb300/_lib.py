@@ -38,6 +38,7 @@ CNSF_OK, CNSF_ERR_INVALID, CNSF_ERR_CUDA, CNSF_ERR_NOMEM, CNSF_ERR_UNSUPPORTED, 
 CNSF_F32, CNSF_F64 = 0, 1
 CNSF_DETECTOR = {"flat": 0, "arc": 1, "parallel": 2}
 CNSF_OPT_NO_SYMMETRY, CNSF_OPT_EXACT_DIFFERENCES, CNSF_OPT_PLAIN_DIFFERENCES, CNSF_OPT_NO_REFLECTION = 1, 2, 4, 8
+CNSF_SCRATCH_KEEP_BYTES = 512 << 20
 
 _P = ctypes.c_void_p
 _SIGNATURES = {
@@ -69,6 +70,9 @@ _SIGNATURES = {
     "cnsf_projection_scratch_bytes": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                      ctypes.POINTER(ctypes.c_size_t)]),
     "cnsf_plan_destroy": (None, [_P]),
+    "cnsf_scratch_pool_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                               ctypes.c_int32]),
+    "cnsf_scratch_trim": (ctypes.c_int, []),
     "cnsf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "cnsf_last_cuda_error": (ctypes.c_char_p, []),
 }

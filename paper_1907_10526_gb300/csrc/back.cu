@@ -1008,7 +1008,7 @@ static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *
     const size_t per = back_rot8_image_bytes(geo);
     const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
+    cudaError_t e = scratch_alloc((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     const double dg = g.arc ? g.ds / g.dps : 0.0;
     BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
@@ -1067,7 +1067,7 @@ static int launch_back_rot4(const cnsf_geometry *geo, const float *sino, float *
     const size_t per = back_rot4_image_bytes(geo);
     const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
+    cudaError_t e = scratch_alloc((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     const double dg = g.arc ? g.ds / g.dps : 0.0;
     BpArgs a{(float)geo->bw.kz, (float)geo->bw.ke, (float)(2.0 * g.h), (float)(2.0 * g.h * g.h), (float)(0.25 * g.h * g.h),
@@ -1137,14 +1137,14 @@ int launch_back(const cnsf_geometry *geo, const void *sino, void *img, int batch
         float *partial = nullptr;
         const long long nimg = (long long)batch * g.nx * g.ny;
         if (nsplit > 1) {
-            cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nimg * sizeof(float), st);
+            cudaError_t e = scratch_alloc((void **)&partial, (size_t)nsplit * nimg * sizeof(float), st);
             if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
         }
         // the sinogram as weighted cell pairs in both alignments (copies: each value carries
         // the 2/B of its view and cell)
         const long long nrows = (long long)batch * g.nv, npair = nrows * ((g.nd + 1) / 2);
         float2 *copy = nullptr;
-        cudaError_t e = cudaMallocAsync((void **)&copy, (size_t)2 * npair * sizeof(float2), st);
+        cudaError_t e = scratch_alloc((void **)&copy, (size_t)2 * npair * sizeof(float2), st);
         if (e != cudaSuccess) {
             if (partial) cudaFreeAsync(partial, st);
             return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);

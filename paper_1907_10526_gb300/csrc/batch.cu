@@ -430,7 +430,7 @@ int launch_forward_batch(const cnsf_geometry *geo, const float *img, float *sino
     const int nr = g.nv * g.nd, pad = geo->pad;
     const int pitchP = g.nx + 2 * pad, pitchT = g.ny + 2 * pad;
     float *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, forward_batch_alloc_bytes(geo), st);
+    cudaError_t e = scratch_alloc((void **)&buf, forward_batch_alloc_bytes(geo), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     for (int b0 = 0; b0 < batch;) {
         const int nb4 = chunk_nb4(batch - b0), NB = 4 * nb4, used = std::min(NB, batch - b0);
@@ -461,7 +461,7 @@ int launch_back_batch(const cnsf_geometry *geo, const float *sino, float *img, i
     const GeomConsts &g = geo->gc;
     const long long nvd = (long long)g.nv * g.nd;
     float *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, back_batch_alloc_bytes(geo), st);
+    cudaError_t e = scratch_alloc((void **)&buf, back_batch_alloc_bytes(geo), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     const int ntx = (g.nx + BPB_T - 1) / BPB_T, nty = (g.ny + BPB_T - 1) / BPB_T;
     dim3 blk(BPB_THREADS), grd(ntx * nty);

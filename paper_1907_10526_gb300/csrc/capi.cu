@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -21,6 +22,53 @@ int record_cuda_error(cudaError_t e)
 {
     std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
     return CNSF_ERR_CUDA;
+}
+
+// Per-device memory pools of the library's own for the projections' stream-ordered scratch.
+// The default pool returns its free memory to the driver at every synchronisation, so a
+// call made after one mapped its scratch afresh (about 0.3 ms for the 90 MB of a 16-image
+// forward projection); these pools keep up to CNSF_SCRATCH_KEEP_BYTES mapped.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static cudaError_t scratch_pool(cudaMemPool_t *pool)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = CNSF_SCRATCH_KEEP_BYTES;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_pool[dev] = p;
+    }
+    *pool = g_pool[dev];
+    return cudaSuccess;
+}
+
+cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    // under capture the allocation becomes the graph's own (kept across its replays)
+    if (cs != cudaStreamCaptureStatusNone) return cudaMallocAsync(ptr, bytes, st);
+    cudaMemPool_t pool;
+    if ((e = scratch_pool(&pool)) != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
 }
 
 // The geometry's tables live on one device; calls must be made with that device current.
@@ -337,6 +385,39 @@ const char *cnsf_status_string(int status)
         case CNSF_ERR_UNSUPPORTED: return "unsupported request";
         case CNSF_ERR_INTERNAL: return "internal consistency check failed";
         default: return "unknown status";
+    }
+}
+
+int cnsf_scratch_pool_stats(size_t *reserved, size_t *used_high, int32_t reset_high)
+{
+    try {
+        cudaMemPool_t pool;
+        cudaError_t e = scratch_pool(&pool);
+        uint64_t r = 0, h = 0;
+        if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r);
+        if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &h);
+        if (e == cudaSuccess && reset_high) {
+            uint64_t zero = 0;   // the only value the attribute may be set to
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+        }
+        if (e != cudaSuccess) return record_cuda_error(e);
+        if (reserved) *reserved = (size_t)r;
+        if (used_high) *used_high = (size_t)h;
+        return CNSF_OK;
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
+    }
+}
+
+int cnsf_scratch_trim(void)
+{
+    try {
+        cudaMemPool_t pool;
+        cudaError_t e = scratch_pool(&pool);
+        if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+        return e == cudaSuccess ? CNSF_OK : record_cuda_error(e);
+    } catch (...) {
+        return CNSF_ERR_INTERNAL;
     }
 }
 

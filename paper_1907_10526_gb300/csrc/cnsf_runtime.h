@@ -12,6 +12,11 @@ namespace cnsf {
 // Remember the CUDA error text for cnsf_last_cuda_error (per host thread); returns CNSF_ERR_CUDA.
 int record_cuda_error(cudaError_t e = cudaGetLastError());
 
+// Stream-ordered scratch for one call: from the library's per-device pool (which keeps up to
+// CNSF_SCRATCH_KEEP_BYTES mapped across synchronisations), or the graph's own allocation
+// while `st` is being captured.  Freed with cudaFreeAsync.
+cudaError_t scratch_alloc(void **ptr, size_t bytes, cudaStream_t st);
+
 int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out);
 void destroy_geometry(cnsf_geometry *geo);
 // Precompute the back projector's per-(tile, view) coefficients when they fit 1 GiB (back.cu).

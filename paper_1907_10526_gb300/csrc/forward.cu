@@ -750,7 +750,7 @@ static int make_padded(const cnsf_geometry *geo, const T *img, int batch, int on
     *strideP = (long long)g.ny * *pitchP;
     *strideT = (long long)g.nx * *pitchT;
     size_t elems = (size_t)batch * (size_t)(*strideP + *strideT);
-    cudaError_t e = cudaMallocAsync((void **)buf, elems * sizeof(T), st);
+    cudaError_t e = scratch_alloc((void **)buf, elems * sizeof(T), st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     T *P = *buf, *Tt = *buf + (size_t)batch * *strideP;
     dim3 blk(128), grd((*pitchP + 127) / 128, g.ny, batch);
@@ -821,7 +821,7 @@ static int launch_forward_rot8(const cnsf_geometry *geo, const float *img, float
     const size_t per = forward_rot8_image_bytes(geo);
     const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
+    cudaError_t e = scratch_alloc((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     float4 *P8 = reinterpret_cast<float4 *>(buf), *T8 = P8 + 2 * (size_t)grp * n * pitch;
     float *partial = nsplit > 1 ? reinterpret_cast<float *>(T8 + 2 * (size_t)grp * n * pitch) : nullptr;
@@ -856,7 +856,7 @@ static int launch_forward_rot4(const cnsf_geometry *geo, const float *img, float
     const size_t per = forward_rot4_image_bytes(geo);
     const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, (size_t)grp * per, st);
+    cudaError_t e = scratch_alloc((void **)&buf, (size_t)grp * per, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (record_cuda_error(e), CNSF_ERR_NOMEM) : record_cuda_error(e);
     float4 *P4 = reinterpret_cast<float4 *>(buf), *T4 = P4 + (size_t)grp * n * pitch;
     float *partial = nsplit > 1 ? reinterpret_cast<float *>(T4 + (size_t)grp * n * pitch) : nullptr;
@@ -923,7 +923,7 @@ int launch_forward(const cnsf_geometry *geo, const void *img, void *sino, int ba
         float *partial = nullptr;
         const long long nout = (long long)nr * batch;
         if (nsplit > 1) {
-            cudaError_t e = cudaMallocAsync((void **)&partial, (size_t)nsplit * nout * sizeof(float), st);
+            cudaError_t e = scratch_alloc((void **)&partial, (size_t)nsplit * nout * sizeof(float), st);
             if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
         }
         (geo->exact ? fp_f32_kernel<false, true> : fp_f32_kernel<false, false>)<<<dim3(grd.x, grd.y, nsplit), blk, 0, st>>>(
@@ -1016,7 +1016,7 @@ int count_nonzeros(const cnsf_geometry *geo, uint64_t *count, cudaStream_t st)
     float *buf = nullptr, *out = nullptr;
     int s = make_padded<float>(geo, nullptr, 1, 1, st, &buf, &pitchP, &pitchT, &strideP, &strideT);
     if (s != CNSF_OK) return s;
-    cudaError_t e = cudaMallocAsync((void **)&out, (size_t)nr * sizeof(float), st);
+    cudaError_t e = scratch_alloc((void **)&out, (size_t)nr * sizeof(float), st);
     if (e != cudaSuccess) { cudaFreeAsync(buf, st); return record_cuda_error(e); }
     dim3 blk(128), grd((nr + 127) / 128, 1);
     fp_f32_kernel<true, false><<<grd, blk, 0, st>>>(geo->d_fp_order, geo->d_ray, geo->d_box, (float)(0.25 * g.h * g.h), buf, buf + strideP, pitchP,

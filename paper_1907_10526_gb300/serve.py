@@ -217,6 +217,11 @@ class ReconServer:
             # rebuilt inside the timed run when a request needs it
             self.geometry(r.n, r.n_views)
             self._fits(0, 0, {(r.n, r.n_views)})
+        # the jobs' footprints count their own scratch: nothing kept from earlier calls in
+        # the library's scratch pool stays mapped beside them
+        from . import scratch_trim
+        torch.cuda.synchronize(dev)
+        scratch_trim(dev)
         pending = deque(reqs)
         queue: deque = deque()
         active = {}                                # slot -> (job, done event, buffers, bytes)
@@ -284,6 +289,10 @@ class ReconServer:
                     time.sleep(poll_s)
                 elif pending:
                     time.sleep(max(0.0, min(pending[0].arrival_s - (time.perf_counter() - t0), 1e-3)))
+                elif queue:
+                    # nothing runs that could free memory: the head can never be admitted
+                    r = queue.popleft()
+                    results[r.rid] = ReconResult(r.rid, "rejected: exceeds HBM budget", arrival_s=r.arrival_s)
         torch.cuda.synchronize(dev)
         return [results[r.rid] for r in reqs]
 

@@ -91,3 +91,19 @@ def test_every_python_signature_is_exported():
     lib = ctypes.CDLL(_lib.LIB_PATH)
     for name in _lib._SIGNATURES:
         assert hasattr(lib, name), name
+
+
+def test_python_constants_match_the_header():
+    """The binding's copies of the header's enumerations and sizes."""
+    from paper_1907_10526_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "cnsf.h")).read()
+    keep = re.search(r"#define CNSF_SCRATCH_KEEP_BYTES \((\d+)ull << (\d+)\)", src)
+    assert keep and _lib.CNSF_SCRATCH_KEEP_BYTES == int(keep.group(1)) << int(keep.group(2))
+    for name in ("CNSF_OK", "CNSF_ERR_INVALID", "CNSF_ERR_CUDA", "CNSF_ERR_NOMEM", "CNSF_ERR_UNSUPPORTED",
+                 "CNSF_ERR_INTERNAL", "CNSF_F32", "CNSF_F64"):
+        m = re.search(name + r"\s*=\s*(\d+)", src)
+        assert m and getattr(_lib, name) == int(m.group(1)), name
+    for name in ("CNSF_OPT_NO_SYMMETRY", "CNSF_OPT_EXACT_DIFFERENCES", "CNSF_OPT_PLAIN_DIFFERENCES",
+                 "CNSF_OPT_NO_REFLECTION"):
+        m = re.search(r"#define " + name + r"\s+(\d+)", src) or re.search(name + r"\s*=\s*(\d+)", src)
+        assert m and getattr(_lib, name) == int(m.group(1)), name

@@ -1,9 +1,7 @@
-"""Scratch-size query (GPU): cnsf_projection_scratch_bytes bounds what a projection call
-allocates stream-ordered, read back from the device's default memory pool (the pool the
-library's stream-ordered allocations come from; torch's caching allocator does not use it)."""
-import ctypes
-import ctypes.util
-
+"""Scratch-size query and scratch pool (GPU): cnsf_projection_scratch_bytes bounds what a
+projection call allocates stream-ordered, read back from the library's scratch pool (the
+pool its uncaptured stream-ordered allocations come from), and the pool keeps freed scratch
+mapped across synchronisations up to CNSF_SCRATCH_KEEP_BYTES."""
 import numpy as np
 import pytest
 
@@ -11,8 +9,6 @@ from synth import FanGeometry
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-CU_MEMPOOL_ATTR_USED_MEM_HIGH = 8   # cuda.h, CUmemPool_attribute
 
 
 @pytest.fixture(scope="module")
@@ -24,26 +20,13 @@ def cnsf():
 
 
 @pytest.fixture(scope="module")
-def pool_high():
-    """Reset / read the high-water mark of the current device's default memory pool."""
-    try:
-        cu = ctypes.CDLL(ctypes.util.find_library("cuda") or "libcuda.so.1")
-    except OSError:
-        pytest.skip("driver library not found")
-    torch.cuda.init()
-    dev = ctypes.c_int()
-    assert cu.cuDeviceGet(ctypes.byref(dev), torch.cuda.current_device()) == 0
-    pool = ctypes.c_void_p()
-    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), dev) == 0
-
+def pool_high(cnsf):
+    """Reset / read the high-water mark of the library's scratch pool on the current device."""
     def reset():
-        zero = ctypes.c_uint64(0)
-        assert cu.cuMemPoolSetAttribute(pool, CU_MEMPOOL_ATTR_USED_MEM_HIGH, ctypes.byref(zero)) == 0
+        cnsf.scratch_pool_stats(reset_high=True)
 
     def read():
-        v = ctypes.c_uint64()
-        assert cu.cuMemPoolGetAttribute(pool, CU_MEMPOOL_ATTR_USED_MEM_HIGH, ctypes.byref(v)) == 0
-        return v.value
+        return cnsf.scratch_pool_stats()[1]
     return reset, read
 
 
@@ -90,3 +73,36 @@ def test_scratch_bytes_arguments(cnsf):
         geom.scratch_bytes("sideways")
     with pytest.raises(cnsf.CnsfError):
         geom.scratch_bytes("forward", -1)
+
+
+def test_pool_keeps_scratch_across_synchronisations(cnsf):
+    """Freed scratch stays in the pool after a synchronisation (so the next call does not map
+    it again), repeated calls give the same bits, a trim returns it to the driver, and a plan
+    (captured: the graph owns its scratch) takes nothing from the pool."""
+    g = FanGeometry(nx=200, ny=200, n_views=180, n_det=300, d_po=300.0, d_ps=600.0)
+    geom = cnsf.Geometry(g)
+    x = torch.tensor(np.random.default_rng(2).uniform(0, 1, (g.ny, g.nx)), dtype=torch.float32, device="cuda")
+    need = max(geom.scratch_bytes("forward"), geom.scratch_bytes("back"))
+    assert 0 < need <= cnsf.CNSF_SCRATCH_KEEP_BYTES
+    torch.cuda.synchronize()
+    cnsf.scratch_trim()
+    assert cnsf.scratch_pool_stats()[0] == 0
+    y0 = cnsf.forward_project(geom, x)
+    c0 = cnsf.back_project(geom, y0)
+    torch.cuda.synchronize()
+    held = cnsf.scratch_pool_stats()[0]
+    assert held >= need
+    for _ in range(3):
+        y = cnsf.forward_project(geom, x)
+        c = cnsf.back_project(geom, y)
+        torch.cuda.synchronize()
+        assert cnsf.scratch_pool_stats()[0] == held      # reused, not mapped again
+    assert torch.equal(y, y0) and torch.equal(c, c0)
+    cnsf.scratch_trim()
+    assert cnsf.scratch_pool_stats()[0] == 0
+    yp = torch.empty_like(y0)
+    plan = cnsf.Plan(geom, "forward", x, yp)
+    plan.run()
+    torch.cuda.synchronize()
+    assert torch.equal(yp, y0)
+    assert cnsf.scratch_pool_stats()[0] == 0

@@ -111,3 +111,4 @@ def test_admission_counts_cached_geometries_and_evicts_idle_ones():
     _cache(big, {(90, 180): 200})
     kind, job, _ = big._take_job(deque([_req(1, 90, 180)]), "continuous", used=0)
     assert kind == "reject"
+

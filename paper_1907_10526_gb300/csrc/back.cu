@@ -597,10 +597,13 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
 // pixel p, U_m(p) = sum_k sum_j y[-k + mV/4][n_det - 1 - j] a(k, j, p) over the views
 // k = 0 .. V/8 that are not their own mirror images, and
 //     (A^T y)[n] = sum_m T_m(R^-m n) + sum_m U_m(M R^-m n),   M (i, r) = (i, N-1-r).
-// The per-call table Y8[o][k][m] holds the 16 weighted values of a cell pair (2m + o,
-// 2m + o + 1), 64 bytes: T part y[k + rV/4][j] w_j (r = 0..3), U part
+// Two per-call tables hold the 16 weighted values of a cell pair (2m + o, 2m + o + 1):
+// T8[o][k][m], 32 bytes, y[k + rV/4][j] w_j (r = 0..3), and after it U8[o][k][m], 32 bytes,
 // y[-k + rV/4][n_det - 1 - j] w_j (zero for the self-mirror views k = 0 and 8k = V), each
-// part the first cell's four values, then the second's; w_j = 2/B of (k, j).
+// the first cell's four values, then the second's; w_j = 2/B of (k, j).  (Two 32-byte
+// tables rather than one of 64-byte records: the neighbouring lanes of a warp, about two
+// pairs apart, then share 128-byte lines, and the L1 data pipe, the back projector's
+// bound, moves fewer wavefronts.)
 __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *__restrict__ box,
                                        float4 *__restrict__ y8, int nv, int nd)
 {
@@ -628,19 +631,20 @@ __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *
             }
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) y8[4 * t + c] = make_float4(out[4 * c], out[4 * c + 1], out[4 * c + 2], out[4 * c + 3]);
+        for (int c = 0; c < 4; ++c)   // T8 at float4 2t, U8 at 2n + 2t
+            y8[(c < 2 ? 0 : 2 * n) + 2 * t + (c & 1)] = make_float4(out[4 * c], out[4 * c + 1], out[4 * c + 2], out[4 * c + 3]);
     }
 }
 
-// bp_view2_rot4 with the eight values per cell pair (the merged constants and 64 bytes of
-// weighted sinogram); each pixel's two entries are applied to the pair's sixteen values as
+// bp_view2_rot4 with the eight values per cell pair (the merged constants and 2 x 32 bytes
+// of weighted sinogram, uoff floats apart); each pixel's two entries are applied to the pair's sixteen values as
 // packed pairs of neighbouring values (adjacent registers of the 256-bit loads): ta[i],
 // tb[i] accumulate the values 2i and 2i + 1 of T_0..3, U_0..3.
 template <bool ARC, bool EXACT>
 __device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4 &Qb, float hwc, int J,
                                               const BpArgs &a, int nd, const float *__restrict__ y8row,
                                               const float *__restrict__ y8orow, const float *__restrict__ acrow,
-                                              long long ac_odd, float2 (&ta)[4], float2 (&tb)[4])
+                                              long long ac_odd, long long uoff, float2 (&ta)[4], float2 (&tb)[4])
 {
     int g0, g1;
     pair_window(Qa.P, Qb.P, hwc, J, nd, g0, g1);
@@ -658,8 +662,8 @@ __device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4
     for (int m = m0; m <= m1; ++m) {
         float A[8], Y[8], Z[8];
         ldg256(acrow + 8 * m, A);          // q/C | p/C | ds/(L C) | c1/C, pairs
-        ldg256(y8row + 16 * m, Y);         // T part, pairs of the four rotations
-        ldg256(y8row + 16 * m + 8, Z);     // U part, pairs of the four mirrored views
+        ldg256(y8row + 8 * m, Y);          // T8: pairs of the four rotations
+        ldg256(y8row + 8 * m + uoff, Z);   // U8: pairs of the four mirrored views
         const float2 wa = bp_pair_rot4<ARC, EXACT>(Qa, da, A, a);
         const float2 wb = bp_pair_rot4<ARC, EXACT>(Qb, db, A, a);
         const float2 wa0 = make_float2(wa.x, wa.x), wa1 = make_float2(wa.y, wa.y);
@@ -735,17 +739,18 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
             const TileViewS<float> T = tv[vv];
             const int J = tj[vv];
             const float *arow = ac + 8 * (long long)v * ndh;
-            const float *yrow = y8 + 16 * (long long)v * ndh, *yorow = y8 + 16 * (long long)(nk + v) * ndh;
+            const float *yrow = y8 + 8 * (long long)v * ndh, *yorow = y8 + 8 * (long long)(nk + v) * ndh;
+            const long long uoff = 16LL * nk * ndh;   // U8 after T8
             const long long ac_odd = 8LL * nv4 * ndh;
             const QuadView Q = quad_view_setup<ARC>(T, di, dr, in1, in2, in3, a);
             const BpPixel4 P0 = bp_pixel4<ARC>(Q.P0, J, a), P1 = bp_pixel4<ARC>(Q.P1, J, a);
             const BpPixel4 P2 = bp_pixel4<ARC>(Q.P2, J, a), P3 = bp_pixel4<ARC>(Q.P3, J, a);
             if (Q.col) {   // P1 is quad pixel 2, P2 quad pixel 1
-                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[0], t[2]);
-                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[1], t[3]);
+                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[0], t[2]);
+                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[1], t[3]);
             } else {
-                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[0], t[1]);
-                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, t[2], t[3]);
+                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[0], t[1]);
+                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[2], t[3]);
             }
         }
     }

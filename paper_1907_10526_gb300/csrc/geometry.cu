@@ -230,10 +230,11 @@ int build_geometry(const cnsf_geometry_desc *d, cnsf_geometry **out)
                 S[2 + h] = c.c1;
                 S[4 + h] = c.c2;
             }
-    // The quarter-turn back projector's pair table for views v < V/4 (built below when the
-    // symmetry holds): per (parity, view, pair) one 32-byte entry (q, q', 1/C, 1/C', ds/L,
-    // ds/L', c1, c1') of cells 2m + o, 2m + o + 1; p/C = q/C - 1 and -C/2 = -1/(2 (1/C)) are
-    // formed in the kernel, and the blur needs no c2 there (c2 = c1 s_j / D_ps).
+    // The symmetric back projectors' pair table for views v < V/4 (built below when the
+    // symmetry holds): per (parity, view, pair) one 32-byte entry of cells 2m + o, 2m + o + 1
+    // in units of the cell's C (q/C, q'/C', p/C, p'/C', ds/(L C), ds'/(L' C'), c1/C,
+    // c1'/C'; arc detector 1/C, 1/C' in the slope slots and zeros in the last two); the blur
+    // needs no c2 there (c2 = c1 s_j / D_ps).
     std::vector<float> ac;
     int pad = ((kc_max + 1 + 3) / 4) * 4;
     // The walk never leaves [-pad, na-1+pad]: windows that meet [0, na-1] are at most kc wide.

@@ -597,30 +597,28 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
 // pixel p, U_m(p) = sum_k sum_j y[-k + mV/4][n_det - 1 - j] a(k, j, p) over the views
 // k = 0 .. V/8 that are not their own mirror images, and
 //     (A^T y)[n] = sum_m T_m(R^-m n) + sum_m U_m(M R^-m n),   M (i, r) = (i, N-1-r).
-// Two per-call tables hold the 16 weighted values of a cell pair (2m + o, 2m + o + 1):
-// T8[o][k][m], 32 bytes, y[k + rV/4][j] w_j (r = 0..3), and after it U8[o][k][m], 32 bytes,
+// Two per-call tables hold the 16 weighted values of a cell pair (2m, 2m + 1): T8[k][m],
+// 32 bytes, y[k + rV/4][j] w_j (r = 0..3), and after it U8[k][m], 32 bytes,
 // y[-k + rV/4][n_det - 1 - j] w_j (zero for the self-mirror views k = 0 and 8k = V), each
-// the first cell's four values, then the second's; w_j = 2/B of (k, j).  (Two 32-byte
-// tables rather than one of 64-byte records: the neighbouring lanes of a warp, about two
-// pairs apart, then share 128-byte lines, and the L1 data pipe, the back projector's
-// bound, moves fewer wavefronts.)
+// the first cell's four values, then the second's; w_j = 2/B of (k, j), 0 past n_det.  Two
+// 32-byte tables rather than one of 64-byte records, and even-aligned pairs only: the
+// neighbouring lanes of a warp, about two pairs apart, then share 128-byte lines, and the
+// L1 data pipe, the back projector's bound, moves fewer wavefronts.
 __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *__restrict__ box,
                                        float4 *__restrict__ y8, int nv, int nd)
 {
     const int ndh = (nd + 1) >> 1, nk = nv / 8 + 1, v4 = nv >> 2;
-    const long long n = 2LL * nk * ndh;
+    const long long n = (long long)nk * ndh;
     y += (long long)blockIdx.y * nv * nd;   // image y of a batch
     y8 += 4 * n * blockIdx.y;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-        const int o = (int)(t / ((long long)nk * ndh));
-        const long long rem = t - (long long)o * nk * ndh;
-        const int k = (int)(rem / ndh), m = (int)(rem - (long long)k * ndh);
+        const int k = (int)(t / ndh), m = (int)(t - (long long)k * ndh);
         const bool self = k == 0 || 8 * k == nv;
         const BoxF *br = box + (long long)k * nd;
         float out[16];
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-            const int j = 2 * m + o + hh;
+            const int j = 2 * m + hh;
             const float w = j < nd ? 1.f / (br[j].q - br[j].hC) : 0.f;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -637,24 +635,24 @@ __global__ void sino_pairs_rot8_kernel(const float *__restrict__ y, const BoxF *
 }
 
 // bp_view2_rot4 with the eight values per cell pair (the merged constants and 2 x 32 bytes
-// of weighted sinogram, uoff floats apart); each pixel's two entries are applied to the pair's sixteen values as
-// packed pairs of neighbouring values (adjacent registers of the 256-bit loads): ta[i],
-// tb[i] accumulate the values 2i and 2i + 1 of T_0..3, U_0..3.
+// of weighted sinogram, uoff floats apart), over even-aligned pairs only: the pairs
+// (2m, 2m + 1) that cover the window, so a cell just outside it may be evaluated too (its
+// entry is zero, or rounding-level at the support's edge).  Each pixel's two entries are
+// applied to the pair's sixteen values as packed pairs of neighbouring values (adjacent
+// registers of the 256-bit loads): ta[i], tb[i] accumulate the values 2i and 2i + 1 of
+// T_0..3, U_0..3.  (Warp-uniform alignment halves the lines a warp's loads touch, for about
+// a fifth more pair steps: 0.231 -> 0.226 ms at 512^2 x 720; the quarter-turn kernel, with
+// two loads per step, is faster with both alignments.)
 template <bool ARC, bool EXACT>
 __device__ __forceinline__ void bp_view2_rot8(const BpPixel4 &Qa, const BpPixel4 &Qb, float hwc, int J,
                                               const BpArgs &a, int nd, const float *__restrict__ y8row,
-                                              const float *__restrict__ y8orow, const float *__restrict__ acrow,
-                                              long long ac_odd, long long uoff, float2 (&ta)[4], float2 (&tb)[4])
+                                              const float *__restrict__ acrow, long long uoff, float2 (&ta)[4],
+                                              float2 (&tb)[4])
 {
     int g0, g1;
     pair_window(Qa.P, Qb.P, hwc, J, nd, g0, g1);
-    const int odd = g0 & 1;
-    const int m0 = g0 >> 1, m1 = (g1 - odd) >> 1;   // m0 > m1 when the window misses the detector
-    if (odd) {   // pairs (2m + 1, 2m + 2)
-        acrow += ac_odd;
-        y8row = y8orow;
-    }
-    const float off = (float)(2 * m0 + odd - J);
+    const int m0 = g0 >> 1, m1 = g1 >> 1;   // m0 > m1 when the window misses the detector
+    const float off = (float)(2 * m0 - J);
     const float sa = ARC ? 1.f : Qa.P.Dn, sb = ARC ? 1.f : Qb.P.Dn;
     float2 da = make_float2(sa * (Qa.P.sig - off), sa * (Qa.P.sig - off - 1.f));
     float2 db = make_float2(sb * (Qb.P.sig - off), sb * (Qb.P.sig - off - 1.f));
@@ -699,10 +697,10 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
     const int tx = 2 * (lane & 7), ty = 8 * warp + 2 * (lane >> 3);
     const int tile = order[blockIdx.x];   // tiles with the most work first
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
-    const int nk = g.nv / 8 + 1, nv4 = g.nv >> 2;
+    const int nk = g.nv / 8 + 1;
     const int vbeg = (int)((long long)nk * blockIdx.y / nsplit), vend = (int)((long long)nk * (blockIdx.y + 1) / nsplit);
     if (BATCH) {   // image z of a batch (the single-image instantiation has no offsets)
-        y8 += 32LL * blockIdx.z * nk * ((g.nd + 1) >> 1);
+        y8 += 16LL * blockIdx.z * nk * ((g.nd + 1) >> 1);
         partial += 8LL * blockIdx.z * nsplit * g.nx * g.ny;
     }
     const int i = it + tx, r = rt + ty;
@@ -739,18 +737,17 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
             const TileViewS<float> T = tv[vv];
             const int J = tj[vv];
             const float *arow = ac + 8 * (long long)v * ndh;
-            const float *yrow = y8 + 8 * (long long)v * ndh, *yorow = y8 + 8 * (long long)(nk + v) * ndh;
-            const long long uoff = 16LL * nk * ndh;   // U8 after T8
-            const long long ac_odd = 8LL * nv4 * ndh;
+            const float *yrow = y8 + 8 * (long long)v * ndh;
+            const long long uoff = 8LL * nk * ndh;   // U8 after T8
             const QuadView Q = quad_view_setup<ARC>(T, di, dr, in1, in2, in3, a);
             const BpPixel4 P0 = bp_pixel4<ARC>(Q.P0, J, a), P1 = bp_pixel4<ARC>(Q.P1, J, a);
             const BpPixel4 P2 = bp_pixel4<ARC>(Q.P2, J, a), P3 = bp_pixel4<ARC>(Q.P3, J, a);
             if (Q.col) {   // P1 is quad pixel 2, P2 quad pixel 1
-                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[0], t[2]);
-                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[1], t[3]);
+                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, arow, uoff, t[0], t[2]);
+                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, arow, uoff, t[1], t[3]);
             } else {
-                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[0], t[1]);
-                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, yorow, arow, ac_odd, uoff, t[2], t[3]);
+                bp_view2_rot8<ARC, EXACT>(P0, P1, Q.hwc, J, a, g.nd, yrow, arow, uoff, t[0], t[1]);
+                bp_view2_rot8<ARC, EXACT>(P2, P3, Q.hwc, J, a, g.nd, yrow, arow, uoff, t[2], t[3]);
             }
         }
     }
@@ -997,7 +994,7 @@ static int bp_view_parts_rot8(const cnsf_geometry *geo)
 static size_t back_rot8_image_bytes(const cnsf_geometry *geo)
 {
     const GeomConsts &g = geo->gc;
-    const size_t y8 = 2 * (size_t)(g.nv / 8 + 1) * ((g.nd + 1) / 2) * 16 * sizeof(float);
+    const size_t y8 = (size_t)(g.nv / 8 + 1) * ((g.nd + 1) / 2) * 16 * sizeof(float);
     return y8 + (size_t)bp_view_parts_rot8(geo) * 8 * g.nx * g.ny * sizeof(float);
 }
 
@@ -1009,7 +1006,7 @@ static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *
     const GeomConsts &g = geo->gc;
     const int nk = g.nv / 8 + 1, ndh = (g.nd + 1) / 2, n = g.nx;
     const int nsplit = bp_view_parts_rot8(geo);
-    const size_t ny8 = 2 * (size_t)nk * ndh * 16;
+    const size_t ny8 = (size_t)nk * ndh * 16;   // T8 and U8 of one image, floats
     const size_t per = back_rot8_image_bytes(geo);
     const int grp = sym_batch_group(per, batch);
     char *buf = nullptr;
@@ -1022,7 +1019,7 @@ static int launch_back_rot8(const cnsf_geometry *geo, const float *sino, float *
              (float)(g.arc ? tan(0.5 * g.tau / g.dps) / (g.ds / g.dps) : 0.0), (float)(g.arc ? -0.5 * (g.ds / g.dps) * (g.ds / g.dps) : 0.0)};
     const int ntx = (g.nx + BP_T - 1) / BP_T, nty = (g.ny + BP_T - 1) / BP_T;
     float *y8 = reinterpret_cast<float *>(buf), *partial = y8 + grp * ny8;
-    const long long npair = 2LL * nk * ndh;
+    const long long npair = (long long)nk * ndh;
     auto kern1 = g.arc ? (geo->exact ? bp_rot8_f32_kernel<true, true, false> : bp_rot8_f32_kernel<true, false, false>)
                        : (geo->exact ? bp_rot8_f32_kernel<false, true, false> : bp_rot8_f32_kernel<false, false, false>);
     auto kernb = g.arc ? (geo->exact ? bp_rot8_f32_kernel<true, true, true> : bp_rot8_f32_kernel<true, false, true>)

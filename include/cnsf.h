@@ -188,11 +188,13 @@ CNSF_API int cnsf_forward_project(const cnsf_geometry *geom, const void *image, 
 /* Back projection c = A^T y, the exact adjoint of cnsf_forward_project (same
  * entries), pixel-driven gather without atomics.  sino: device
  * [batch][n_views][n_det]; image: device [batch][n_y][n_x], overwritten.  FP32
- * allocates scratch stream-ordered on `stream` (the sinogram as odd-aligned cell pairs,
- * and as even-aligned pairs too when n_det is odd or the pointer is not 8-byte aligned;
- * partial images of groups of views, summed in a fixed order; interleaved copies for
- * batch >= 2 off the symmetric path) and frees it the same way.  Batches as
- * cnsf_forward_project.  FP64 uses no scratch. */
+ * allocates scratch stream-ordered on `stream` (the sinogram as weighted cell-pair
+ * records — on a symmetric geometry the base views' records with the values of the views
+ * that share their entries, even-aligned pairs only on the eight-fold path, both
+ * alignments on the quarter-turn path; the general path an odd-aligned copy, and an
+ * even-aligned one when n_det is odd or the pointer is not 8-byte aligned; partial images of groups of views, summed in a fixed order;
+ * interleaved copies for batch >= 2 off the symmetric path) and frees it the same way.
+ * Batches as cnsf_forward_project.  FP64 uses no scratch. */
 CNSF_API int cnsf_back_project(const cnsf_geometry *geom, const void *sino, void *image, int32_t batch,
                       int32_t dtype, void *stream);
 

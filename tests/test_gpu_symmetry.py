@@ -44,10 +44,14 @@ SYMMETRIC = {
     # are their own mirror images
     "odd_odd": FanGeometry(nx=37, ny=37, n_views=32, n_det=91, d_po=200.0, d_ps=450.0),
     "odd_odd_arc": FanGeometry(nx=33, ny=33, n_views=40, n_det=77, d_po=180.0, d_ps=400.0, detector="arc"),
+    # a fan narrower than the image: windows that miss the detector on either side, and the
+    # last even-aligned pair of an odd cell count running past the detector
+    "narrow_odd": FanGeometry(nx=48, ny=48, n_views=32, n_det=41, d_po=200.0, d_ps=400.0),
+    "narrow_even_arc": FanGeometry(nx=48, ny=48, n_views=24, n_det=40, d_po=200.0, d_ps=400.0, detector="arc"),
 }
 # the order each case takes: 8 with a centred detector and views closed under reflection
 ORDER = {"flat_72": 8, "flat_odd_offset": 4, "arc": 8, "parallel": 8, "angles_offset": 4, "wide_cells": 8,
-         "views_20": 8, "views_8": 8, "odd_odd": 8, "odd_odd_arc": 8}
+         "views_20": 8, "views_8": 8, "odd_odd": 8, "odd_odd_arc": 8, "narrow_odd": 8, "narrow_even_arc": 8}
 
 NOT_SYMMETRIC = {
     "views_not_multiple_of_4": config_geometry(1),                                 # 90 views

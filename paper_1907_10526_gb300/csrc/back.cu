@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 10) bp_f32_kernel(GeomConsts 
     __shared__ TileViewS<float> tv[BP_CHUNK];
     __shared__ int tj[BP_CHUNK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = 2 * (lane & 7), ty = 8 * warp + 2 * (lane >> 3);
+    // lanes 4k .. 4k + 3 take a 2 x 2 block of quads: their cell windows lie close, so a
+    // warp's loads touch fewer 128-byte lines per group of four lanes
+    const int tx = 2 * ((lane & 1) | ((lane >> 1) & 6)), ty = 8 * warp + 2 * (((lane >> 1) & 1) | ((lane >> 3) & 2));
     const int tile = order[blockIdx.x];   // tiles with the most work first
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const long long b = blockIdx.z;
@@ -522,7 +524,9 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot4_f32_kernel(GeomCon
     __shared__ TileViewS<float> tv[BP_CHUNK];
     __shared__ int tj[BP_CHUNK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = 2 * (lane & 7), ty = 8 * warp + 2 * (lane >> 3);
+    // lanes 4k .. 4k + 3 take a 2 x 2 block of quads: their cell windows lie close, so a
+    // warp's loads touch fewer 128-byte lines per group of four lanes
+    const int tx = 2 * ((lane & 1) | ((lane >> 1) & 6)), ty = 8 * warp + 2 * (((lane >> 1) & 1) | ((lane >> 3) & 2));
     const int tile = order[blockIdx.x];   // tiles with the most work first
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const int nv4 = g.nv >> 2;
@@ -694,7 +698,9 @@ __global__ void __launch_bounds__(BP_QUAD_THREADS, 8) bp_rot8_f32_kernel(GeomCon
     __shared__ TileViewS<float> tv[BP_CHUNK];
     __shared__ int tj[BP_CHUNK];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tx = 2 * (lane & 7), ty = 8 * warp + 2 * (lane >> 3);
+    // lanes 4k .. 4k + 3 take a 2 x 2 block of quads: their cell windows lie close, so a
+    // warp's loads touch fewer 128-byte lines per group of four lanes
+    const int tx = 2 * ((lane & 1) | ((lane >> 1) & 6)), ty = 8 * warp + 2 * (((lane >> 1) & 1) | ((lane >> 3) & 2));
     const int tile = order[blockIdx.x];   // tiles with the most work first
     const int it = (tile % ntx) * BP_T, rt = (tile / ntx) * BP_T;
     const int nk = g.nv / 8 + 1;
